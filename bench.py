@@ -1,0 +1,310 @@
+"""Benchmark of the coupled LBM-DEM step (one step = one pass of Algorithm 1:
+sort, volume fraction, moments and fields, particle forces, reaction gathers,
+DEM substeps with lubrication, collide-stream) on a synthetic suspension.
+
+Default workload: 64^3 box with walls at z, 5000 spheres of d = 1 (random
+sequential insertion, seed 12345), density ratio 2.5, tau 0.65, 1 interaction
+subcycle with 10 DEM substeps, contact (e_n 0.9, T_c = 1), lubrication
+(h_c = d), FP64.  Prints one JSON line (see the contract in the README of this
+repository's design notes): value = coupled MLUPS over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1711_00336_gb300 import workloads  # noqa: E402
+
+PHASES = ["moments+fields", "force_am", "reaction_am", "force_drag", "reaction_drag", "dem_substep", "cell_sort",
+          "eps_gather", "collide_stream"]
+
+
+def closure_kw(wl):
+    # reading of the wall-suspension configuration: n_int = 1, n_DEM = 10,
+    # T_c = (d/dx) dt, h_c = d, e_n = 0.9, mu_c = 0.25
+    return dict(g=wl["g"], fb_mode=0, fb=(0, 0, 0), e_n=0.9, mu_c=0.25, T_c=1.0, h_c=1.0, h_min=1e-5,
+                C_am=0.5, n_int=1, n_dem=10, lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5)
+
+
+def algorithmic_bytes_collide(prec):
+    """K1 per cell: 19 PDF loads + 19 stores, eps_f and f_pf (3) loads."""
+    s = {"f64": 8, "f32": 4, "f16s": 2}[prec]
+    sf = 8 if prec == "f64" else 4
+    return 2 * 19 * s + 4 * sf
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_domain(dps, wl, prec, stream=None):
+    dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], prec, max_particles=len(wl["x"]), stream=stream)
+    dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+    dom.set_closure(**closure_kw(wl))
+    return dom
+
+
+def time_device(dps, wl, prec, steps, warmup, flush, timing=True):
+    """Device-timed steps: CUDA events on the domain's stream around every
+    step, L2 flushed (256 MB write) between steps outside the events."""
+    import torch
+    dom = make_domain(dps, wl, prec)
+    s = dom.stream
+    dom.step(warmup)
+    if timing:
+        dom.set_timing(True)
+        dom.step(1)  # capture the step graph with the timing events
+        dom.collect_timing()
+        dom.get_timing(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        with torch.cuda.stream(s):
+            flush.zero_()
+            ev[k][0].record(s)
+        dom.step_async(1)
+        with torch.cuda.stream(s):
+            ev[k][1].record(s)
+        if timing:
+            dom.collect_timing()
+    dom.check()
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in ev]
+    total = sum(times)
+    phase = dom.get_timing(reset=True) if timing else None
+    lps = dom.launches_per_step()
+    st = dom.stats()
+    dom.close()
+    return total, times, phase, lps, st
+
+
+def e2e_run(dps, wl, prec, steps):
+    """End to end through the public API with host buffers: create, upload the
+    particles, set the closure, then per step: step + read all particle state
+    (x, u, w, F) back to the host; destroy.  Wall clock around all of it."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dom = make_domain(dps, wl, prec)
+    for _ in range(steps):
+        dom.step(1)
+        dom.read_particles()
+    dom.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    n = len(wl["x"])
+    h2d = n * (9 + 2) * 8 / steps
+    d2h = n * 12 * 8
+    return dt, h2d, d2h
+
+
+def oracle_sample(wl, seconds=12.0, max_steps=200):
+    """Time the FP64 CPU oracle (as it stands, one host thread) on the same
+    workload: as many whole steps as fit in `seconds`."""
+    import oracle as O
+    kw = closure_kw(wl)
+    P = O.make_params(wl["n"], wl["periodic"], wl["tau"], g=kw["g"], f_b=kw["fb"], e_n=kw["e_n"], mu_c=kw["mu_c"],
+                      T_c=kw["T_c"], h_c=kw["h_c"], h_min=kw["h_min"], C_am=kw["C_am"], n_int=kw["n_int"],
+                      n_dem=kw["n_dem"], lub_limiter=1, lub_cap=kw["lub_cap"], eps_min=kw["eps_min"])
+    dom = O.Domain(P, x=wl["x"], d=wl["d"], rho_p=wl["rho_p"])
+    dom.step(1)
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps:
+        dom.step(1)
+        k += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    ncell = int(np.prod(wl["n"]))
+    return ncell * k / dt / 1e6, k, dt
+
+
+def run_reference(args, wl, ncell):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build.build()
+    mlups, k, dt = oracle_sample(wl, seconds=max(3.0, min(60.0, 1.5 * (args.steps + args.warmup))),
+                                 max_steps=args.steps + args.warmup)
+    ms = dt / k * 1e3
+    line = {"metric": "coupled MLUPS (FP64 plain method)", "value": mlups, "unit": "MLUPS", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, ncell, "f64"),
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{k} coupled steps of the same workload on one host thread"},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl, ncell, prec):
+    return {"workload": wl["name"], "cells": ncell, "particles": int(len(wl["x"])), "precision": prec,
+            "n_int": 1, "n_dem": 10, "boundaries": "periodic x,y; walls z",
+            "l2": "flushed between timed steps (256 MB write outside the step events)",
+            "parallelism": "replicas (one independent box per GPU)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--forms", default="f32,f16s", help="extra precision forms to time (comma list, '' for none)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    wl = workloads.wall_suspension()
+    ncell = int(np.prod(wl["n"]))
+    if args.impl == "reference":
+        run_reference(args, wl, ncell)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1711_00336_gb300 import build, dps
+    build.build()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    total_ms, times, phase, lps, st = time_device(dps, wl, "f64", args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_all = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_all = float(t.item())
+    value = world * ncell * args.steps / (t_all * 1e-3) / 1e6
+    ms_step = t_all / args.steps
+
+    # roofline of the dominant kernel, measured live over the timed region
+    peaks = measured_peaks()
+    dom_phase = max(phase, key=lambda k: phase[k]["ms"]) if phase else None
+    roof = None
+    if phase:
+        cs = phase["collide_stream"]
+        per_launch_ms = cs["ms"] / max(cs["launches"], 1)
+        bytes_launch = algorithmic_bytes_collide("f64") * ncell
+        achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "collide_stream (K1, FP64)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800",
+                "bytes_per_cell": algorithmic_bytes_collide("f64"), "cells_per_launch": ncell,
+                "per_launch_us": per_launch_ms * 1e3, "dominant_phase": dom_phase}
+
+    forms = {}
+    for prec in [f for f in args.forms.split(",") if f]:
+        tot, _, ph, _, st2 = time_device(dps, wl, prec, max(args.steps // 2, 10), args.warmup, flush)
+        k = max(args.steps // 2, 10)
+        cs = ph["collide_stream"]
+        per = cs["ms"] / max(cs["launches"], 1)
+        forms[prec] = {"value": ncell * k / (tot * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": tot / k,
+                       "collide_stream_GBps": algorithmic_bytes_collide(prec) * ncell / (per * 1e-3) / 1e9,
+                       "u_pS_z": float(st2["u_pS"][2])}
+
+    e2e_steps = min(args.steps, 50)
+    dt, h2d, d2h = e2e_run(dps, wl, "f64", e2e_steps)
+    e2e = {"value": ncell * e2e_steps / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+           "what": "create + upload particles + per step (step, read x/u/w/F) + destroy, wall clock"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        mlups_cpu, k, dt = oracle_sample(wl)
+        cpu = {"value": mlups_cpu, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{k} coupled steps of the same 64^3 / 5000-sphere workload, one host thread"}
+
+    if rank == 0:
+        psteps = len(wl["x"]) * args.steps / (t_all * 1e-3)
+        line = {"metric": "coupled MLUPS (FP64 plain method)", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_of(wl, ncell, "f64"),
+                "particle_steps_per_s": world * psteps,
+                "particle_substeps_per_s": world * psteps * 10,
+                "step_ms_p50": float(np.percentile(times, 50)), "step_ms_p99": float(np.percentile(times, 99)),
+                "roofline": roof, "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in phase.items()} if phase else None,
+                "forms": forms, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": int(lps * args.steps),
+                "u_pS_z": float(st["u_pS"][2]), "status": int(st["status"])}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

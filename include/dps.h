@@ -1,0 +1,244 @@
+/*
+ * dps.h -- C ABI of the GB300 (sm_103a) discrete particle simulation library:
+ * the coupled lattice Boltzmann / discrete element time step of Rettinger &
+ * Ruede, "A Coupled Lattice Boltzmann Method and Discrete Element Method for
+ * Discrete Particle Simulations of Particulate Flows", arXiv:1711.00336.
+ *
+ * Units are lattice units (Sec. 3.2.2): dx = dt = 1, c_s^2 = 1/3, rho_0 = 1.
+ * A lattice cell (ix,iy,iz) has its centre at (ix+0.5, iy+0.5, iz+0.5) and the
+ * linear index ix + nx*(iy + ny*iz) ("cell order", x fastest).  Positions of
+ * periodic axes live in [0, n); non-periodic axes have no-slip walls at the
+ * faces 0 and n (halfway bounce-back for the fluid, planar walls for the DEM).
+ *
+ * Conventions of every call:
+ *   - every function returns an int status: DPS_OK (0) or a negative DPS_ERR_*;
+ *     dps_last_error() gives a message for the last failure on a handle;
+ *   - no C++ exception crosses this boundary;
+ *   - the library owns every device buffer of a domain; the caller owns every
+ *     host buffer it passes; each transfer is a copy (host pointers are read or
+ *     written before the call returns);
+ *   - calls on one handle are not thread-safe; distinct handles are independent;
+ *   - the "op" entry points at the end work on caller-owned DEVICE buffers and
+ *     are stream-ordered on the stream they are given.
+ */
+#ifndef DPS_H
+#define DPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DPS_OK            0
+#define DPS_ERR_ARG      -1  /* invalid argument (size, pointer, parameter) */
+#define DPS_ERR_OOM      -2  /* device allocation failed */
+#define DPS_ERR_STATE    -3  /* call not valid in the current state */
+#define DPS_ERR_UNSTABLE -4  /* NaN, non-positive density, or particles moved beyond the skin */
+#define DPS_ERR_TIMEOUT  -5  /* a bounded device wait gave up */
+#define DPS_ERR_CUDA     -6  /* a CUDA runtime call failed */
+
+/* ---- precision forms --------------------------------------------------- */
+#define DPS_F64  0  /* PDFs and fields FP64, FP64 arithmetic (the plain method) */
+#define DPS_F32  1  /* PDFs stored FP32 as f_q - w_q*rho_0, fields and arithmetic FP32 */
+#define DPS_F16S 2  /* PDFs stored FP16 as f_q - w_q*rho_0, fields and arithmetic FP32 */
+
+/* ---- field masks for dps_read_fields / dps_write_fields ---------------- */
+#define DPS_FIELD_RHO    0x001u  /* density rho_f = sum_q f_q (Eq. MacVel), 1 plane */
+#define DPS_FIELD_UBAR   0x002u  /* volume-averaged velocity ubar (Eq. MacVel), 3 planes */
+#define DPS_FIELD_UF     0x004u  /* fluid-phase velocity u_f = ubar/eps_f (Sec. 3.2.3), 3 planes */
+#define DPS_FIELD_EPS    0x008u  /* fluid volume fraction eps_f (Eq. fluid_volume_fraction), 1 plane */
+#define DPS_FIELD_FEXT   0x010u  /* f_ext = f_pf + eps_f f_b applied in the last LBM step, 3 planes */
+#define DPS_FIELD_P      0x020u  /* pressure p = c_s^2 rho / eps_f (Sec. 3.2.2), 1 plane */
+#define DPS_FIELD_FPF    0x040u  /* f_pf of the last LBM step (Eq. forces_pf, subcycle average), 3 planes */
+#define DPS_FIELD_GRADP  0x080u  /* grad(eps_f p) of the current step (Sec. 3.2.3), 3 planes */
+#define DPS_FIELD_DUDT   0x100u  /* Du_f/Dt of the current step (Table 1, added mass), 3 planes */
+
+typedef struct dps_domain *dps_handle;
+
+/* Device allocator hooks.  alloc returns a device pointer (NULL on failure,
+ * which the library reports as DPS_ERR_OOM); free releases it.  Both NULL:
+ * the library uses cudaMalloc / cudaFree. */
+typedef void *(*dps_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*dps_free_fn)(void *ptr, void *ctx);
+
+/* Domain description: the box and the fluid of Sec. 3.2 (Eq. GNS). */
+typedef struct {
+    int n[3];                 /* lattice cells per axis, each >= 1 */
+    int periodic[3];          /* 1 periodic, 0 no-slip walls at both faces */
+    double tau;               /* relaxation time tau_e (Eq. visc_tau), > 0.5 */
+    double rho_f;             /* fluid density in the particle closures (rho_0 = 1) */
+    int precision;            /* DPS_F64 / DPS_F32 / DPS_F16S */
+    int64_t max_particles;    /* capacity of the particle arrays, >= 0 */
+    void *stream;             /* cudaStream_t for all work; NULL: the library creates one */
+    dps_alloc_fn alloc;       /* optional allocator hooks (see above) */
+    dps_free_fn free;
+    void *alloc_ctx;
+} dps_domain_desc;
+
+/* Closure: the models and constants of Sec. 3.1 and Algorithm 1. */
+typedef struct {
+    int drag;                 /* Table 1 drag (Tenneti et al.) */
+    int pressure;             /* Table 1 pressure-gradient force */
+    int added_mass;           /* Table 1 added-mass force */
+    int lubrication;          /* Sec. 3.1.3 (Ball & Melrose) */
+    int contact;              /* Sec. 3.1.1 spring-dashpot contact */
+    double g[3];              /* gravity, acting on the particles only (Sec. 3.1.2) */
+    int fb_mode;              /* body force on the fluid, applied as eps_f*f_b:
+                                 0 f_b = fb[3] as given,
+                                 1 f_b balances the buoyant weight of all particles
+                                   (f_b = -sum_i (rho_p,i - rho_f) V_i g / (cells - sum_i V_i)),
+                                 2 the literal Sec. 4.1 form f_b = -<eps_p> (rho_p - rho_f) g */
+    double fb[3];
+    double e_n;               /* dry restitution (Eq. damping_to_stiffness), (0, 1] */
+    double mu_c;              /* Coulomb friction coefficient */
+    double T_c;               /* collision duration (Eq. collision_time), > 0 */
+    double h_c;               /* lubrication cut-off gap, >= 0 */
+    double h_min;             /* gap floor (Sec. 3.1.3: 1e-5 dx) */
+    double C_am;              /* added-mass coefficient (Table 1: 0.5) */
+    int n_int;                /* interaction subcycles per LBM step (Algorithm 1), >= 1 */
+    int n_dem;                /* DEM substeps per subcycle, >= 1 */
+    int lub_limiter;          /* 1: cap each lubrication coefficient at lub_cap*m_ij/dt_DEM */
+    double lub_cap;
+    double eps_min;           /* floor of eps_f, in (0, 1) */
+    double skin;              /* neighbour-list skin in dx (>= 0): particles may move skin/2
+                                 within one subcycle before DPS_ERR_UNSTABLE is raised */
+} dps_closure;
+
+/* Global sums (FP64, deterministic order). */
+typedef struct {
+    double mass;              /* sum_x rho */
+    double fluid_j[3];        /* sum_x sum_q f_q c_q */
+    double fluid_ubar[3];     /* sum_x ubar (with the applied f_ext) */
+    double uf_mean[3];        /* mean over cells of u_f */
+    double particle_momentum[3]; /* sum_i m_i u_i */
+    double up_mean[3];        /* mean over particles of u_p */
+    double u_pS[3];           /* <u_pS> of Sec. 4.1: up_mean - uf_mean */
+    double eps_min_seen;      /* smallest eps_f before the floor */
+    int64_t step;             /* LBM steps done */
+    int64_t n_particles;
+    int64_t n_eps_clamp;      /* cells floored at eps_min (cumulative) */
+    int64_t n_lub_limited;    /* lubrication coefficients capped (cumulative) */
+    int status;               /* sticky status bits, 0 when healthy */
+} dps_stats;
+
+/* ---- library ----------------------------------------------------------- */
+const char *dps_version(void);
+/* message of the last failing call on h (h may be NULL for create failures) */
+const char *dps_last_error(dps_handle h);
+
+/* ---- domain API -------------------------------------------------------- */
+
+/* Create a domain: the lattice of Sec. 3.2.2 with the fluid at rest,
+ * f_q = f_q^eq(rho_0 = 1, ubar = 0) = w_q, and no particles.
+ * Errors: DPS_ERR_ARG (bad sizes, tau <= 0.5, unknown precision),
+ * DPS_ERR_OOM, DPS_ERR_CUDA.  On failure *out is NULL. */
+int dps_create_domain(const dps_domain_desc *desc, dps_handle *out);
+int dps_destroy(dps_handle h);
+
+/* Append n particles (Eq. particle_motion: position x, velocity u, angular
+ * velocity w, diameter d, density rho_p).  x3/u3/w3 hold 3 doubles per
+ * particle (x0,y0,z0,x1,...); u3 and w3 may be NULL (zero).  Positions on
+ * periodic axes are wrapped into [0, n); on wall axes they must lie in
+ * (0, n).  Errors: DPS_ERR_ARG (d <= 0, rho_p <= 0, position outside,
+ * capacity exceeded, a particle-carrying axis shorter than 3 cells). */
+int dps_add_particles(dps_handle h, int64_t n, const double *x3, const double *u3,
+                      const double *w3, const double *d, const double *rho_p);
+
+/* Overwrite the state (x, u, w) of all particles, in insertion order.  Used to
+ * couple an external particle code; NULL arrays are left unchanged. */
+int dps_write_particles(dps_handle h, int64_t n, const double *x3, const double *u3,
+                        const double *w3);
+
+/* Set the closure (all models and constants).  Must precede dps_step. */
+int dps_set_closure(dps_handle h, const dps_closure *c);
+/* The closure defaults of the paper's hindered-settling setup (Sec. 4.1):
+ * all forces on, mu_c 0.25, e_n 0.88, h_c 1, h_min 1e-5, C_am 0.5, n_int 10,
+ * n_dem 50, T_c 0.5, limiter on (cap 0.25), eps_min 0.05, skin 0.5, fb_mode 1. */
+void dps_closure_defaults(dps_closure *c);
+
+/* Algorithm 1 initialisation: sort the particles, evaluate eps_f and the
+ * body force eps_f f_b.  dps_step calls it when particles changed. */
+int dps_prepare(dps_handle h);
+
+/* Run n coupled time steps of Algorithm 1 on the domain's stream, then wait
+ * for them and check the device status word once.
+ * Errors: DPS_ERR_STATE (no closure), DPS_ERR_UNSTABLE, DPS_ERR_CUDA. */
+int dps_step(dps_handle h, int64_t n);
+/* As dps_step but returns right after enqueueing (no wait, no status check);
+ * dps_check() waits and reports the status accumulated since the last check. */
+int dps_step_async(dps_handle h, int64_t n);
+int dps_check(dps_handle h);
+/* Run n steps of the GNS-LBM collide-stream only (Eq. LBM_Equation) with the
+ * current eps_f and f_ext, without particles (fluid-only use). */
+int dps_collide_stream(dps_handle h, int64_t n);
+int dps_sync(dps_handle h);
+
+/* Copy fields to the host.  out receives the planes of the requested fields in
+ * mask-bit order, each plane ncell doubles in cell order (vectors as 3 planes
+ * x,y,z).  cap = capacity of out in doubles.  Values are at the current time
+ * (before the next step's collision), converted to FP64. */
+int dps_read_fields(dps_handle h, uint32_t mask, double *out, int64_t cap);
+/* Overwrite eps_f (DPS_FIELD_EPS) and/or f_pf (DPS_FIELD_FPF) from the host,
+ * in the same layout.  Other mask bits are DPS_ERR_ARG. */
+int dps_write_fields(dps_handle h, uint32_t mask, const double *in, int64_t count);
+/* Read / write the PDFs f_q(x,t) at the current time: 19 planes of ncell
+ * doubles in the lattice order of dps_lattice(). */
+int dps_read_pdfs(dps_handle h, double *out, int64_t cap);
+int dps_write_pdfs(dps_handle h, const double *in, int64_t count);
+/* The D3Q19 velocities (19x3 ints) and weights of the PDF planes. */
+void dps_lattice(int c[19][3], double w[19]);
+
+/* Particles in insertion order: x, u, w and the frozen fluid-particle force
+ * plus gravity F (Eq. particle_motion, F_fp + F_g) of the last subcycle.
+ * Any pointer may be NULL.  cap = capacity in particles. */
+int dps_read_particles(dps_handle h, double *x3, double *u3, double *w3, double *F3,
+                       int64_t cap);
+int dps_stats_get(dps_handle h, dps_stats *s);
+
+/* The current linked-cell sort (the neighbour search of the DEM and the
+ * gather of the coupling): cell_start[ncell+1] over cell keys, order[np] the
+ * insertion indices in sorted order.  See dps_op_cell_sort for the key. */
+int dps_read_cell_list(dps_handle h, int32_t *cell_start, int32_t *order, int64_t cap_cells,
+                       int64_t cap_particles);
+/* bin edge B (cells) chosen for the current closure */
+int dps_bin_edge(dps_handle h, int *B);
+
+/* ---- tracing: per-phase CUDA-event timing of the coupled step ---------- */
+/* Phases, in the order of Algorithm 1:
+ *   0 moments + fields (rho, j, u_f, grad P, Du_f/Dt)   1 added-mass force
+ *   2 added-mass reaction gather                          3 drag/pressure/gravity force
+ *   4 drag reaction gather                                5 DEM substeps
+ *   6 linked-cell sort                                    7 eps_f gather
+ *   8 collide-stream                                                                  */
+#define DPS_NPHASE 9
+/* enable / disable event pairs around every phase (captured into the step graph) */
+int dps_set_timing(dps_handle h, int enable);
+/* wait for the stream, then add the phase times of the last step to the totals */
+int dps_collect_timing(dps_handle h);
+/* totals since the last reset: milliseconds and kernel launches per phase */
+int dps_get_timing(dps_handle h, double ms[DPS_NPHASE], int64_t launches[DPS_NPHASE], int reset);
+/* number of kernels one coupled step launches with the current closure */
+int dps_launches_per_step(dps_handle h, int64_t *n);
+
+/* ---- op API (caller-owned device buffers) ------------------------------- */
+
+/* Linked-cell sort of np particles (device x3, 3 doubles each, interleaved;
+ * device ids[np], the tie-break).  Lattice cells are grouped in bins of B
+ * cells per axis (the last bin of an axis takes the remainder); the key of a
+ * cell orders cells bin-major (bz,by,bx), then (z,y,x) inside the bin, so
+ * that every bin and every cell is one contiguous key range.  Particles are
+ * sorted by (key of the cell containing them, ids).  Outputs (device):
+ * cell_start[ncell+1] (exclusive prefix of the counts per key) and
+ * order[np] (input index of each sorted slot).  Scratch is allocated on the
+ * stream (stream-ordered).  Errors: DPS_ERR_ARG, DPS_ERR_OOM, DPS_ERR_CUDA. */
+int dps_op_cell_sort(const int n[3], const int periodic[3], int B, int64_t np,
+                     const double *x3, const int32_t *ids, int32_t *cell_start, int32_t *order,
+                     void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPS_H */

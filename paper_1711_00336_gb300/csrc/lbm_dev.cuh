@@ -1,0 +1,109 @@
+// lbm_dev.cuh -- device helpers of the AA-pattern PDF storage: neighbour
+// index deltas with periodic wrap / wall detection, parity-aware loads and
+// stores of the 19 populations, and their first two moments (Eq. MacVel).
+#pragma once
+#include "dps_internal.cuh"
+
+namespace dps {
+
+// linear-index deltas to the -1/+1 neighbour along each axis; INV marks a
+// neighbour beyond a wall.
+constexpr long long INV = (1LL << 62);
+
+struct NbDelta {
+    long long d[3][3];  // [axis][offset+1]
+};
+
+__device__ __forceinline__ void cell_coords(const Geom &g, long long c, int &ix, int &iy, int &iz) {
+    long long nxy = (long long)g.n[0] * g.n[1];
+    iz = (int)(c / nxy);
+    long long r = c - (long long)iz * nxy;
+    iy = (int)(r / g.n[0]);
+    ix = (int)(r - (long long)iy * g.n[0]);
+}
+
+__device__ __forceinline__ NbDelta neighbour_deltas(const Geom &g, int ix, int iy, int iz) {
+    NbDelta D;
+    const int ii[3] = {ix, iy, iz};
+    long long stride[3] = {1, g.n[0], (long long)g.n[0] * g.n[1]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int L = g.n[a];
+        D.d[a][1] = 0;
+        D.d[a][0] = ii[a] > 0 ? -stride[a] : (g.per[a] ? (long long)(L - 1) * stride[a] : INV);
+        D.d[a][2] = ii[a] < L - 1 ? stride[a] : (g.per[a] ? -(long long)(L - 1) * stride[a] : INV);
+    }
+    return D;
+}
+
+__device__ __forceinline__ long long nb_delta(const NbDelta &D, int q) {
+    long long dx = D.d[0][CX(q) + 1], dy = D.d[1][CY(q) + 1], dz = D.d[2][CZ(q) + 1];
+    if (dx == INV || dy == INV || dz == INV) return INV;
+    return dx + dy + dz;
+}
+
+// Load f_q(x,t) for all q at cell c under the AA parity.
+template <typename ST, typename CT, int PAR>
+__device__ __forceinline__ void load_pdfs(const ST *__restrict__ pdf, long long N, long long c,
+                                          const NbDelta &D, CT f[Q]) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const CT w = (CT)WQ(q);
+        if (PAR == 0 || q == 0) {
+            f[q] = Store<ST>::load(pdf + (long long)q * N + c, w);
+        } else {
+            // f_q(x) was written by the upstream cell x - c_q into plane opp(q);
+            // across a wall it is the own cell's bounced value in plane q.
+            long long dm;
+            {
+                long long dx = D.d[0][-CX(q) + 1], dy = D.d[1][-CY(q) + 1], dz = D.d[2][-CZ(q) + 1];
+                dm = (dx == INV || dy == INV || dz == INV) ? INV : dx + dy + dz;
+            }
+            if (dm != INV)
+                f[q] = Store<ST>::load(pdf + (long long)OPP(q) * N + c + dm, w);
+            else
+                f[q] = Store<ST>::load(pdf + (long long)q * N + c, w);
+        }
+    }
+}
+
+template <typename ST, typename CT, int PAR>
+__device__ __forceinline__ void store_pdfs(ST *__restrict__ pdf, long long N, long long c,
+                                           const NbDelta &D, const CT f[Q]) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const CT w = (CT)WQ(q);
+        if (q == 0) {
+            Store<ST>::store(pdf + c, f[0], w);
+        } else if (PAR == 0) {
+            Store<ST>::store(pdf + (long long)OPP(q) * N + c, f[q], (CT)WQ(OPP(q)));
+        } else {
+            long long dp = nb_delta(D, q);
+            if (dp != INV)
+                Store<ST>::store(pdf + (long long)q * N + c + dp, f[q], w);
+            else  // bounce back: returns to this cell with velocity -c_q
+                Store<ST>::store(pdf + (long long)OPP(q) * N + c, f[q], (CT)WQ(OPP(q)));
+        }
+    }
+}
+
+template <typename CT>
+__device__ __forceinline__ void moments(const CT f[Q], CT &rho, CT &jx, CT &jy, CT &jz) {
+    // pair sums: direction q and its opposite q+9
+    CT r = f[0];
+    CT x = 0, y = 0, z = 0;
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+        r += f[k] + f[k + 9];
+        CT d = f[k] - f[k + 9];
+        if (CX(k) != 0) x += CX(k) * d;
+        if (CY(k) != 0) y += CY(k) * d;
+        if (CZ(k) != 0) z += CZ(k) * d;
+    }
+    rho = r;
+    jx = x;
+    jy = y;
+    jz = z;
+}
+
+}  // namespace dps

@@ -1,0 +1,104 @@
+"""Precision forms against the FP64 oracle: PDFs stored FP32 or FP16 as
+shifted populations f_q - w_q rho_0 with FP32 arithmetic; particles FP64.
+
+Stated tolerances (velocity field, relative L2 over the box):
+  FP32 form       1e-4 after 100 steps
+  FP16-shifted    5e-3 after 100 steps
+and the settling velocity of the single-sphere workload within 1 % of the
+FP64 oracle in every form."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1711_00336_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL_FIELD = {"f32": 1e-4, "f16s": 5e-3}
+
+
+def _dps():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_00336_gb300 import build, dps
+    build.build()
+    return dps
+
+
+def _perm():
+    from paper_1711_00336_gb300 import dps
+    cl, _ = dps.lattice()
+    co, _, _ = O.lattice()
+    return np.array([next(q for q in range(19) if (co[q] == cl[k]).all()) for k in range(19)])
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16s"])
+def test_collide_stream_forms(prec):
+    dps = _dps()
+    n, per = (16, 12, 10), (1, 1, 0)
+    nc = int(np.prod(n))
+    _, w, _ = O.lattice()
+    # a smooth shear-wave initial state (velocity 1e-2) and a uniform force
+    idx = np.arange(nc)
+    iy = (idx // n[0]) % n[1]
+    u = 0.01 * np.sin(2 * np.pi * iy / n[1])
+    f0 = np.stack([O.equilibrium(1.0, np.array([u[c], 0.0, 0.0]), 1.0) for c in range(nc)], 1)
+    eps = np.full(nc, 0.9)
+    fpf = np.zeros((3, nc))
+    fpf[0] = 1e-6
+    dom = dps.Domain(n, per, 0.65, prec)
+    dom.write_pdfs(f0[_perm()])
+    dom.write_fields(eps_f=eps, f_pf=fpf)
+    dom.collide_stream(100)
+    got = dom.read_fields(("ubar",))["ubar"]
+    P = O.make_params(n, per, 0.65)
+    ref = f0
+    for _ in range(100):
+        ref = O.collide_stream(P, ref, eps, fpf)
+    rho, j = O.moments(P, ref)
+    ub = (j + 0.5 * fpf) / rho
+    assert rel_l2(got, ub) < TOL_FIELD[prec]
+    dom.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16s"])
+def test_single_sphere_settling_velocity_forms(prec):
+    """Terminal settling velocity of the single sphere within 1 % of FP64."""
+    dps = _dps()
+    wl = workloads.single_sphere()
+    kw = dict(e_n=0.9, mu_c=0.25, T_c=1.0, h_c=0.8, h_min=1e-5, C_am=0.5, n_int=1, n_dem=1, lub_limiter=1,
+              lub_cap=0.25, eps_min=0.05)
+    res = {}
+    for p in ("f64", prec):
+        dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], p, max_particles=1)
+        dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+        dom.set_closure(g=wl["g"], fb_mode=0, fb=(0, 0, 0), skin=0.5, **kw)
+        dom.step(600)
+        res[p] = (dom.read_particles()["u"][0, 2], dom.read_fields(("u_f",))["u_f"])
+        dom.close()
+    assert abs(res[prec][0] - res["f64"][0]) / abs(res["f64"][0]) < 1e-2
+    assert rel_l2(res[prec][1], res["f64"][1]) < 10 * TOL_FIELD[prec]
+
+
+def test_f64_gpu_single_sphere_matches_oracle_terminal_velocity():
+    """The FP64 GPU path and the oracle agree on the terminal velocity over
+    the first 600 steps of the single-sphere workload."""
+    dps = _dps()
+    wl = workloads.single_sphere()
+    kw = dict(e_n=0.9, mu_c=0.25, T_c=1.0, h_c=0.8, h_min=1e-5, C_am=0.5, n_int=1, n_dem=1, lub_limiter=1,
+              lub_cap=0.25, eps_min=0.05)
+    dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=1)
+    dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+    dom.set_closure(g=wl["g"], fb_mode=0, fb=(0, 0, 0), skin=0.5, **kw)
+    dom.step(600)
+    u = dom.read_particles()["u"][0, 2]
+    P = O.make_params(wl["n"], wl["periodic"], wl["tau"], g=wl["g"], **kw)
+    ref = O.Domain(P, x=wl["x"], d=wl["d"], rho_p=wl["rho_p"])
+    ref.step(600)
+    assert abs(u - ref.u[0, 2]) / abs(ref.u[0, 2]) < 1e-10
+    dom.close()
