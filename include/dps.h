@@ -223,6 +223,114 @@ int dps_get_timing(dps_handle h, double ms[DPS_NPHASE], int64_t launches[DPS_NPH
 /* number of kernels one coupled step launches with the current closure */
 int dps_launches_per_step(dps_handle h, int64_t *n);
 
+/* ---- batch API: many independent boxes advanced by one launch per phase --- */
+/* A batch holds boxes of different sizes (each its own lattice, particles and
+ * closure; n_int and n_dem must agree across the batch).  Every phase kernel
+ * of the coupled step runs once for all boxes over a list of tiles (cells or
+ * particles of one box), and the whole step is one CUDA graph replay.  Box ids
+ * stay valid until the box is removed.  Results of a box do not depend on the
+ * other boxes in the batch.  Errors as for the domain API. */
+typedef struct dps_batch_s *dps_batch;
+typedef struct {
+    int precision;            /* DPS_F64 / DPS_F32 / DPS_F16S for every box */
+    void *stream;             /* cudaStream_t; NULL: the library creates one */
+    dps_alloc_fn alloc;       /* optional allocator hooks */
+    dps_free_fn free;
+    void *alloc_ctx;
+} dps_batch_desc;
+
+int dps_batch_create(const dps_batch_desc *desc, dps_batch *out);
+int dps_batch_destroy(dps_batch b);
+/* add a box (fluid at rest, no particles); *box receives its id */
+int dps_batch_add_box(dps_batch b, const int n[3], const int periodic[3], double tau, double rho_f,
+                      int64_t max_particles, int *box);
+int dps_batch_remove_box(dps_batch b, int box);
+int dps_batch_add_particles(dps_batch b, int box, int64_t n, const double *x3, const double *u3,
+                            const double *w3, const double *d, const double *rho_p);
+int dps_batch_set_closure(dps_batch b, int box, const dps_closure *c);
+int dps_batch_step(dps_batch b, int64_t n);
+int dps_batch_step_async(dps_batch b, int64_t n);
+int dps_batch_check(dps_batch b);
+int dps_batch_read_particles(dps_batch b, int box, double *x3, double *u3, double *w3, double *F3, int64_t cap);
+int dps_batch_read_fields(dps_batch b, int box, uint32_t mask, double *out, int64_t cap);
+int dps_batch_stats(dps_batch b, int box, dps_stats *s);
+/* mean particle velocity of a box (FP64, fixed summation order) */
+int dps_batch_particle_mean(dps_batch b, int box, double u[3]);
+int dps_batch_num_boxes(dps_batch b, int *n);
+/* launch shape: cfg = {cell threads/block, cells/tile, particle threads/block, particles/tile} */
+int dps_batch_set_tuning(dps_batch b, const int cfg[4]);
+int dps_batch_get_tuning(dps_batch b, int cfg[4]);
+/* autotuner: time every candidate launch shape for `steps` steps on the
+ * current boxes (their state advances) and keep the fastest; ms[0] receives
+ * the best time per step */
+int dps_batch_autotune(dps_batch b, int steps, double *best_ms);
+int dps_batch_set_timing(dps_batch b, int enable);
+int dps_batch_collect_timing(dps_batch b);
+int dps_batch_get_timing(dps_batch b, double ms[DPS_NPHASE], int64_t launches[DPS_NPHASE], int reset);
+int dps_batch_launches_per_step(dps_batch b, int64_t *n);
+/* device bytes one box needs (for admission by free HBM) */
+int dps_box_bytes(int precision, const int n[3], int64_t max_particles, size_t *bytes);
+
+/* ---- serving: continuous batching of settling-suspension runs ----------- */
+/* A server owns a batch and a worker thread.  Requests (one periodic or walled
+ * box with its particles and closure) queue on submit; the worker admits a
+ * queued request when a batch slot is free and cudaMemGetInfo shows room for
+ * the box (dps_box_bytes) plus the reserve, steps all running boxes together
+ * in chunks, samples each box's mean particle velocity every chunk and
+ * retires a box once the mean over its last `window` steps changed by less
+ * than rel_tol (relative, along g) from the window before, or after max_steps.
+ * A box's result does not depend on which other requests shared the GPU. */
+typedef struct dps_server_s *dps_server;
+typedef struct {
+    int precision;            /* form of every box */
+    int device;               /* CUDA device of the worker thread */
+    int max_boxes;            /* batch slots */
+    size_t hbm_reserve_bytes; /* free HBM kept aside when admitting */
+    int64_t chunk_steps;      /* steps between scheduling rounds (also the sampling period) */
+} dps_serve_desc;
+typedef struct {
+    int n[3];
+    int periodic[3];
+    double tau, rho_f;
+    int64_t np;                     /* particles; x3/d/rho_p are copied at submit */
+    const double *x3, *d, *rho_p;
+    dps_closure closure;
+    int64_t max_steps;              /* cap (e.g. 20000) */
+    int64_t window;                 /* steps per averaging window (a multiple of chunk_steps) */
+    double rel_tol;                 /* convergence threshold on the windowed mean (e.g. 1e-3) */
+} dps_request;
+#define DPS_REQ_QUEUED 0
+#define DPS_REQ_RUNNING 1
+#define DPS_REQ_DONE 2
+#define DPS_REQ_FAILED 3
+#define DPS_REQ_CANCELLED 4
+typedef struct {
+    int state;                /* DPS_REQ_* */
+    int capped;               /* 1 if stopped by max_steps */
+    int status;               /* DPS_OK or the error of a failed run */
+    int64_t steps;
+    double up_mean[3];        /* windowed mean particle velocity at the end */
+    double u_pS[3];           /* <u_pS> (Sec. 4.1) at the end */
+    double t_submit, t_start, t_end;  /* seconds since the server started */
+} dps_result;
+typedef struct {
+    int64_t submitted, admitted, completed, failed, running, queued;
+    int peak_boxes;
+    double cell_updates;      /* sum over boxes of cells x steps */
+    double busy_s;            /* time with at least one running box */
+    double wall_s;            /* since the server started */
+} dps_serve_stats;
+
+int dps_serve_create(const dps_serve_desc *desc, dps_server *out);
+int dps_serve_submit(dps_server s, const dps_request *r, int64_t *id);
+int dps_serve_poll(dps_server s, int64_t id, dps_result *res);
+int dps_serve_cancel(dps_server s, int64_t id);
+/* wait until nothing is queued or running (timeout in seconds, <0: forever);
+ * DPS_ERR_TIMEOUT when the time runs out */
+int dps_serve_wait_idle(dps_server s, double timeout_s);
+int dps_serve_stats_get(dps_server s, dps_serve_stats *st);
+int dps_serve_destroy(dps_server s);
+
 /* ---- op API (caller-owned device buffers) ------------------------------- */
 
 /* Linked-cell sort of np particles (device x3, 3 doubles each, interleaved;

@@ -1,25 +1,29 @@
-// abi.cu -- the C ABI of include/dps.h: domain lifetime, Algorithm 1 driver
-// (one coupled step = a fixed sequence of kernel launches on the domain's
-// stream, replayed as a CUDA graph once the history flags are set), status
-// handling and host<->device copies.
+// abi.cu -- the C ABI of include/dps.h.
+//
+// Everything runs through one host object, the Batch: a device table of boxes
+// (BoxDev) and tile lists over their cells and particles.  A coupled step of
+// Algorithm 1 is a fixed sequence of launches, each covering every box of the
+// batch; the per-box step state (AA parity, current particle set, history
+// flags) is advanced on the device, so the sequence is captured once as a CUDA
+// graph and replayed for every step until the set of boxes changes.  A domain
+// (dps_handle) is a batch of one box.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
 
-#include "dps_internal.cuh"
+#include "box.cuh"
 
 namespace dps {
 // launchers (lbm.cu, coupling.cu, dem.cu, scan.cu, io.cu)
 template <typename ST, typename FT, typename CT>
-void launch_collide_stream(void *, const void *, const void *, const Geom &, const double *, double, int, int, int *,
-                           cudaStream_t);
+void launch_collide_stream(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename ST, typename FT, typename CT>
-void launch_moments(const void *, const void *, const void *, const Geom &, const double *, int, void *, void *, void *,
-                    cudaStream_t);
+void launch_moments(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT, typename CT>
-void launch_fields(const void *, const void *, void *, const Geom &, int, void *, void *, cudaStream_t);
+void launch_fields(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename ST>
 void launch_pdf_export(const void *, const Geom &, int, double *, cudaStream_t);
 template <typename ST>
@@ -28,24 +32,26 @@ void launch_sort_count(const double *, const double *, const double *, long long
                        int *, cudaStream_t);
 void launch_sort_scatter(const int *, long long, const int *, int *, int *, cudaStream_t);
 void launch_sort_rank(const int *, const int *, long long, const int *, const int *, int *, cudaStream_t);
-void launch_sort_gather(const double *, const double *, const int *, long long, long long, const int *, const int *,
-                        const Geom &, double *, int *, cudaStream_t);
+void launch_bsort_count(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
+void launch_bsort_scatter(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+void launch_bsort_rank(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+void launch_bsort_gather(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
+void launch_bsort_flip(BoxDev *, int, int, cudaStream_t);
+void launch_end_step(BoxDev *, int, cudaStream_t);
+void launch_flip_parity(BoxDev *, int, cudaStream_t);
+void launch_bscan(const BoxDev *, int, const Tile *, int, cudaStream_t);
+int scan_tile_cells();
 template <typename FT>
-void launch_eps(const Geom &, const int *, const double *, long long, double, void *, unsigned long long *, int *,
-                cudaStream_t);
+void launch_eps(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
-void launch_force_am(const Geom &, double *, const double *, long long, long long, const void *, const Phys &, int,
-                     cudaStream_t);
+void launch_force_am(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
-void launch_force_drag(const Geom &, double *, const double *, long long, long long, const void *, const void *,
-                       const void *, const void *, const void *, const Phys &, cudaStream_t);
+void launch_force_drag(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
-void launch_reaction_am(const Geom &, const int *, const double *, long long, void *, cudaStream_t);
+void launch_reaction_am(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
-void launch_reaction_drag(const Geom &, const int *, const double *, long long, const void *, void *, void *, int, int,
-                          double, cudaStream_t);
-void launch_dem_substep(const double *, double *, const double *, const int *, long long, long long, int, const Geom &,
-                        const Phys &, int *, unsigned long long *, cudaStream_t);
+void launch_reaction_drag(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
+void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 long long scan_scratch_words(long long);
 void exclusive_scan(const int *, long long, int *, int *, cudaStream_t);
 template <typename ST>
@@ -72,312 +78,165 @@ using namespace dps;
 
 static const double PI_H = 3.14159265358979323846;
 
-struct dps_domain {
-    dps_domain_desc desc{};
-    Geom g{};
+// ---------------------------------------------------------------------------
+// host objects
+// ---------------------------------------------------------------------------
+struct BoxHost {
+    BoxDev d{};                   // table entry (state fields authoritative on the device)
+    std::vector<void *> allocs;
+    dps_closure cl{};
+    bool have_closure = false;
+    double sumV = 0, sumWb = 0, dmax = 0;
+    long long max_particles = 0;
+    double tau = 0.65, rho_f = 1.0;
+    bool prepared = false;
+    long long steps = 0;
+    int sticky = 0;
+    double *d_red = nullptr, *d_redout = nullptr;
+    int64_t user_id = -1;
+};
+
+enum { PH_MOM = 0, PH_FAM, PH_RAM, PH_FDRAG, PH_RDRAG, PH_DEM, PH_SORT, PH_EPS, PH_COLLIDE, NPH };
+
+struct Tuning {
+    int cell_block = 128, cell_tile = 1024;   // threads per block, cells per tile
+    int part_block = 128, part_tile = 256;    // threads per block, particles per tile
+};
+
+struct Batch {
     int prec = DPS_F64;
     size_t pdf_elem = 8, fel = 8;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    dps_alloc_fn alloc = nullptr;
+    dps_free_fn free = nullptr;
+    void *ctx = nullptr;
     std::string err;
-    std::vector<void *> allocs;
-
-    // fluid
-    void *pdf = nullptr;
-    void *eps = nullptr, *fpf = nullptr, *fam = nullptr, *acc = nullptr, *rho = nullptr, *j = nullptr,
-         *uD = nullptr, *uprev = nullptr, *gradP = nullptr, *DuDt = nullptr;
-    int parity = 0;
-    int have_uprev = 0;
-
-    // particles
-    long long cap = 0, np = 0;
-    double *pf[2] = {nullptr, nullptr};
-    int *pi[2] = {nullptr, nullptr};
-    double *xtmp = nullptr;
-    int cur = 0;
-    int have_usub = 0;
-    double sumV = 0.0, sumWb = 0.0, dmax = 0.0;  // sum V, sum (rho_p - rho_f) V, max d
-
-    // sort
-    int *cell_start = nullptr, *count = nullptr, *fill = nullptr, *key = nullptr, *tmp = nullptr, *perm = nullptr,
-        *scan_scratch = nullptr;
-
-    // status
-    int *d_status = nullptr;
-    unsigned long long *d_counters = nullptr;
-    double *d_red = nullptr, *d_redout = nullptr;
-    int sticky = 0;
-
-    // closure
-    dps_closure cl{};
-    bool have_closure = false;
-    Phys ph{};
-    int R = 1;
-    bool prepared = false;
-    long long step = 0;
-
-    // graphs keyed by (parity, cur)
-    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<BoxHost *> boxes;
+    int table_cap = 0;
+    BoxDev *d_table = nullptr;
+    std::vector<void *> allocs;  // batch-level buffers (table, tiles)
+    Tile *d_cell = nullptr, *d_part = nullptr, *d_scan = nullptr;
+    int n_cell = 0, n_part = 0, n_scan = 0;
+    size_t cap_cell = 0, cap_part = 0, cap_scan = 0;
+    Tuning tune;
+    bool tuned = false;
+    int n_int = 0, n_dem = 0;
+    bool layout_dirty = true;     // table/tiles must be rebuilt and uploaded
+    cudaGraphExec_t gexec = nullptr;
     bool use_graphs = true;
-
-    // tracing: event pairs around each phase of a step, in launch order
+    long long launches_step = 0, launch_count = 0;
+    // tracing
     bool timing = false;
-    std::vector<cudaEvent_t> ev;     // 2 per phase instance
-    std::vector<int> ev_phase, ev_nl;  // phase and kernel launches of each instance
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_phase, ev_nl;
     size_t ev_used = 0;
-    double ph_ms[DPS_NPHASE] = {0};
-    long long ph_nl[DPS_NPHASE] = {0};
-    long long launches_step = 0;     // kernels per step (counted while enqueueing)
-    long long launch_count = 0;
+    double ph_ms[NPH] = {0};
+    long long ph_nl[NPH] = {0};
 };
-
-enum { PH_MOM = 0, PH_FAM, PH_RAM, PH_FDRAG, PH_RDRAG, PH_DEM, PH_SORT, PH_EPS, PH_COLLIDE };
-
-static void tbegin(dps_domain *h) {
-    if (!h->timing) return;
-    if (h->ev_used * 2 + 2 > h->ev.size()) {
-        cudaEvent_t a, b;
-        cudaEventCreate(&a);
-        cudaEventCreate(&b);
-        h->ev.push_back(a);
-        h->ev.push_back(b);
-        h->ev_phase.push_back(0);
-        h->ev_nl.push_back(0);
-    }
-    cudaEventRecord(h->ev[2 * h->ev_used], h->stream);
-}
-static void tend(dps_domain *h, int phase, int nlaunch) {
-    h->launch_count += nlaunch;
-    if (!h->timing) return;
-    cudaEventRecord(h->ev[2 * h->ev_used + 1], h->stream);
-    h->ev_phase[h->ev_used] = phase;
-    h->ev_nl[h->ev_used] = nlaunch;
-    h->ev_used++;
-}
 
 static thread_local std::string g_create_err;
 
-#define FAIL(h, code, ...)                                   \
-    do {                                                     \
-        char _b[512];                                        \
-        snprintf(_b, sizeof(_b), __VA_ARGS__);               \
-        (h)->err = _b;                                       \
-        return code;                                         \
+#define FAILB(b, code, ...)                      \
+    do {                                         \
+        char _m[512];                            \
+        snprintf(_m, sizeof(_m), __VA_ARGS__);   \
+        (b)->err = _m;                           \
+        return code;                             \
     } while (0)
 
-#define CK(h, call)                                                                         \
-    do {                                                                                    \
-        cudaError_t _e = (call);                                                            \
-        if (_e != cudaSuccess) FAIL(h, DPS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
+#define CKB(b, call)                                                                           \
+    do {                                                                                       \
+        cudaError_t _e = (call);                                                               \
+        if (_e != cudaSuccess) FAILB(b, DPS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
     } while (0)
 
-static void *dalloc(dps_domain *h, size_t bytes) {
+static void *dalloc_raw(Batch *B, size_t bytes) {
     if (bytes == 0) bytes = 16;
     void *p = nullptr;
-    if (h->desc.alloc) {
-        p = h->desc.alloc(bytes, h->desc.alloc_ctx);
-    } else {
-        if (cudaMalloc(&p, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-        }
+    if (B->alloc) {
+        p = B->alloc(bytes, B->ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
     }
+    return p;
+}
+static void dfree_raw(Batch *B, void *p) {
+    if (!p) return;
+    if (B->free)
+        B->free(p, B->ctx);
+    else
+        cudaFree(p);
+}
+static void *box_alloc(Batch *B, BoxHost *h, size_t bytes) {
+    void *p = dalloc_raw(B, bytes);
     if (p) h->allocs.push_back(p);
     return p;
 }
-
-static void free_all(dps_domain *h) {
-    for (int k = 0; k < 4; ++k)
-        if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
-    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
-    h->ev.clear();
-    for (void *p : h->allocs) {
-        if (h->desc.free)
-            h->desc.free(p, h->desc.alloc_ctx);
-        else
-            cudaFree(p);
-    }
+static void box_free(Batch *B, BoxHost *h) {
+    for (void *p : h->allocs) dfree_raw(B, p);
     h->allocs.clear();
-    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
-static void invalidate_graphs(dps_domain *h) {
-    for (int k = 0; k < 4; ++k)
-        if (h->gexec[k]) {
-            cudaGraphExecDestroy(h->gexec[k]);
-            h->gexec[k] = nullptr;
-        }
-}
-
-// ---- precision dispatch ------------------------------------------------------------------
-#define DISPATCH_PREC(h, F64CALL, F32CALL, F16CALL) \
-    do {                                            \
-        if ((h)->prec == DPS_F64) {                 \
-            F64CALL;                                \
-        } else if ((h)->prec == DPS_F32) {          \
-            F32CALL;                                \
-        } else {                                    \
-            F16CALL;                                \
-        }                                           \
-    } while (0)
-
-static void k1(dps_domain *h, const double fb[3], int n_avg) {
-    DISPATCH_PREC(h,
-                  (launch_collide_stream<double, double, double>(h->pdf, h->eps, h->fpf, h->g, fb, h->desc.tau, n_avg,
-                                                                 h->parity, h->d_status, h->stream)),
-                  (launch_collide_stream<float, float, float>(h->pdf, h->eps, h->fpf, h->g, fb, h->desc.tau, n_avg,
-                                                              h->parity, h->d_status, h->stream)),
-                  (launch_collide_stream<__half, float, float>(h->pdf, h->eps, h->fpf, h->g, fb, h->desc.tau, n_avg,
-                                                               h->parity, h->d_status, h->stream)));
-}
-
-static void k2(dps_domain *h) {
-    const double *fb = h->ph.fb;
-    DISPATCH_PREC(h,
-                  (launch_moments<double, double, double>(h->pdf, h->eps, h->fpf, h->g, fb, h->parity, h->rho, h->j,
-                                                          h->uD, h->stream)),
-                  (launch_moments<float, float, float>(h->pdf, h->eps, h->fpf, h->g, fb, h->parity, h->rho, h->j, h->uD,
-                                                       h->stream)),
-                  (launch_moments<__half, float, float>(h->pdf, h->eps, h->fpf, h->g, fb, h->parity, h->rho, h->j,
-                                                        h->uD, h->stream)));
-    if (h->prec == DPS_F64)
-        launch_fields<double, double>(h->rho, h->uD, h->uprev, h->g, h->have_uprev, h->gradP, h->DuDt, h->stream);
-    else
-        launch_fields<float, float>(h->rho, h->uD, h->uprev, h->g, h->have_uprev, h->gradP, h->DuDt, h->stream);
-}
-
-static int scan_launches(long long n) {
-    const long long tile = 8192;
-    if (n <= tile) return 1;
-    return 2 + scan_launches((n + tile - 1) / tile);
-}
-
-static double *main_f(dps_domain *h) { return h->pf[h->cur]; }
-static int *main_i(dps_domain *h) { return h->pi[h->cur]; }
-
-// S1: sort by (containing cell, id), reorder into the other set, swap
-static void do_sort(dps_domain *h, const double *xuw) {
-    const long long N = h->g.ncell, cap = h->cap, np = h->np;
-    cudaMemsetAsync(h->count, 0, sizeof(int) * N, h->stream);
-    launch_sort_count(xuw, xuw + cap, xuw + 2 * cap, 1, np, h->g, h->count, h->key, h->d_status, h->stream);
-    exclusive_scan(h->count, N, h->cell_start, h->scan_scratch, h->stream);
-    cudaMemsetAsync(h->fill, 0, sizeof(int) * N, h->stream);
-    launch_sort_scatter(h->key, np, h->cell_start, h->fill, h->tmp, h->stream);
-    launch_sort_rank(h->key, main_i(h) + IID * cap, np, h->cell_start, h->tmp, h->perm, h->stream);
-    int other = 1 - h->cur;
-    launch_sort_gather(main_f(h), xuw, main_i(h), cap, np, h->perm, h->key, h->g, h->pf[other], h->pi[other],
-                       h->stream);
-    h->cur = other;
-}
-
-static void eps_eval(dps_domain *h) {
-    if (h->prec == DPS_F64)
-        launch_eps<double>(h->g, h->cell_start, main_f(h), h->cap, h->ph.eps_min, h->eps, h->d_counters, h->d_status,
-                           h->stream);
-    else
-        launch_eps<float>(h->g, h->cell_start, main_f(h), h->cap, h->ph.eps_min, h->eps, h->d_counters, h->d_status,
-                          h->stream);
-}
-
-// one coupled LBM step (Algorithm 1), enqueued on h->stream
-static void enqueue_step(dps_domain *h) {
-    const long long cap = h->cap, np = h->np;
-    const Phys &ph = h->ph;
-    const int pl = np > 0 ? 1 : 0;  // particle kernels are skipped without particles
-    h->ev_used = 0;
-    h->launch_count = 0;
-    // Du_f/Dt and grad P once per step
-    tbegin(h);
-    k2(h);
-    tend(h, PH_MOM, 2);
-    h->have_uprev = 1;
-    for (int k = 0; k < ph.n_int; ++k) {
-        double *pf = main_f(h);
-        const double *xuw = pf;  // x,u,w are in planes 0..8 of the main set after every sort
-        const bool f64 = h->prec == DPS_F64;
-        tbegin(h);
-        if (f64) launch_force_am<double>(h->g, pf, xuw, cap, np, h->DuDt, ph, h->have_usub, h->stream);
-        else launch_force_am<float>(h->g, pf, xuw, cap, np, h->DuDt, ph, h->have_usub, h->stream);
-        tend(h, PH_FAM, pl);
-        tbegin(h);
-        if (f64) launch_reaction_am<double>(h->g, h->cell_start, pf, cap, h->fam, h->stream);
-        else launch_reaction_am<float>(h->g, h->cell_start, pf, cap, h->fam, h->stream);
-        tend(h, PH_RAM, 1);
-        tbegin(h);
-        if (f64) launch_force_drag<double>(h->g, pf, xuw, cap, np, h->rho, h->j, h->eps, h->fam, h->gradP, ph, h->stream);
-        else launch_force_drag<float>(h->g, pf, xuw, cap, np, h->rho, h->j, h->eps, h->fam, h->gradP, ph, h->stream);
-        tend(h, PH_FDRAG, pl);
-        tbegin(h);
-        if (f64)
-            launch_reaction_drag<double>(h->g, h->cell_start, pf, cap, h->fam, h->acc, h->fpf, k == 0,
-                                         k == ph.n_int - 1, 1.0 / ph.n_int, h->stream);
-        else
-            launch_reaction_drag<float>(h->g, h->cell_start, pf, cap, h->fam, h->acc, h->fpf, k == 0,
-                                        k == ph.n_int - 1, 1.0 / ph.n_int, h->stream);
-        tend(h, PH_RDRAG, 1);
-        h->have_usub = 1;
-        // DEM substeps: ping-pong between the main set's planes 0..8 and xtmp
-        const double *xin = pf;
-        double *xout = h->xtmp;
-        tbegin(h);
-        for (int s = 0; s < ph.n_dem; ++s) {
-            launch_dem_substep(xin, xout, pf, h->cell_start, cap, np, h->R, h->g, ph, h->d_status, h->d_counters,
-                               h->stream);
-            const double *t = xin;
-            xin = xout;
-            xout = (double *)t;
-        }
-        tend(h, PH_DEM, pl * ph.n_dem);
-        // re-sort with the new positions, then re-evaluate eps_f
-        tbegin(h);
-        do_sort(h, xin);
-        tend(h, PH_SORT, scan_launches(h->g.ncell) + 4 * pl);
-        tbegin(h);
-        eps_eval(h);
-        tend(h, PH_EPS, 1);
+static void invalidate_graph(Batch *B) {
+    if (B->gexec) {
+        cudaGraphExecDestroy(B->gexec);
+        B->gexec = nullptr;
     }
-    tbegin(h);
-    k1(h, ph.fb, 1);
-    tend(h, PH_COLLIDE, 1);
-    h->launches_step = h->launch_count;
-    h->parity ^= 1;
-    h->step++;
 }
 
-static int check_status(dps_domain *h) {
-    int st = 0;
-    CK(h, cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    if (st) {
-        CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
-        CK(h, cudaStreamSynchronize(h->stream));
-        h->sticky |= st;
-        std::string m;
-        if (st & ST_NAN) m += "non-finite or non-positive state; ";
-        if (st & ST_SKIN) m += "a particle moved more than skin/2 within one subcycle (increase skin or n_int); ";
-        if (st & ST_EPS_NEG) m += "eps_f < 0 before the floor; ";
-        if (st & ST_BAD_CELL) m += "a particle left the box through a wall; ";
-        FAIL(h, DPS_ERR_UNSTABLE, "unstable: %s", m.c_str());
+// ---- phase timing -----------------------------------------------------------
+static void tbegin(Batch *B) {
+    if (!B->timing) return;
+    if (B->ev_used * 2 + 2 > B->ev.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        B->ev.push_back(a);
+        B->ev.push_back(b);
+        B->ev_phase.push_back(0);
+        B->ev_nl.push_back(0);
     }
-    return DPS_OK;
+    // external record nodes: the events stay readable after graph replays
+    cudaEventRecordWithFlags(B->ev[2 * B->ev_used], B->stream, cudaEventRecordExternal);
+}
+static void tend(Batch *B, int phase, int nl) {
+    B->launch_count += nl;
+    if (!B->timing) return;
+    cudaEventRecordWithFlags(B->ev[2 * B->ev_used + 1], B->stream, cudaEventRecordExternal);
+    B->ev_phase[B->ev_used] = phase;
+    B->ev_nl[B->ev_used] = nl;
+    B->ev_used++;
 }
 
-static void compute_phys(dps_domain *h) {
+// ---- physics constants of a box ---------------------------------------------
+static void compute_phys(BoxHost *h) {
     const dps_closure &c = h->cl;
-    Phys &p = h->ph;
-    p.tau = h->desc.tau;
-    p.omega = 1.0 / h->desc.tau;
-    p.rho_f = h->desc.rho_f;
-    p.mu = h->desc.rho_f * (h->desc.tau - 0.5) / 3.0;  // Eq. visc_tau
-    for (int a = 0; a < 3; ++a) p.g[a] = c.g[a];
-    const double cells = (double)h->g.ncell;
+    Phys &p = h->d.ph;
+    p.tau = h->tau;
+    p.omega = 1.0 / h->tau;
+    p.rho_f = h->rho_f;
+    p.mu = h->rho_f * (h->tau - 0.5) / 3.0;  // Eq. visc_tau
+    const double cells = (double)h->d.g.ncell;
     for (int a = 0; a < 3; ++a) {
-        if (c.fb_mode == 1)
+        p.g[a] = h->have_closure ? c.g[a] : 0.0;
+        if (!h->have_closure)
+            p.fb[a] = 0.0;
+        else if (c.fb_mode == 1)
             p.fb[a] = (cells - h->sumV) > 0 ? -h->sumWb * c.g[a] / (cells - h->sumV) : 0.0;
         else if (c.fb_mode == 2)
-            p.fb[a] = h->np > 0 ? -(h->sumV / cells) * (h->sumWb / h->sumV) * c.g[a] : 0.0;
+            p.fb[a] = h->sumV > 0 ? -(h->sumV / cells) * (h->sumWb / h->sumV) * c.g[a] : 0.0;
         else
             p.fb[a] = c.fb[a];
+    }
+    if (!h->have_closure) {
+        p.eps_min = 0.05;
+        p.n_int = p.n_dem = 1;
+        p.dt_sub = p.dt_dem = 1.0;
+        h->d.R = 1;
+        p.skin_half2 = 0.25;
+        return;
     }
     p.e_n = c.e_n;
     p.mu_c = c.mu_c;
@@ -398,27 +257,618 @@ static void compute_phys(dps_domain *h) {
     p.contact = c.contact;
     p.lub_limiter = c.lub_limiter;
     const double cutoff = h->dmax + (c.lubrication ? std::fmax(c.h_c, 0.0) : 0.0);
-    h->R = (int)std::floor(cutoff + c.skin) + 1;
-    const double slack = h->R - cutoff;
+    h->d.R = (int)std::floor(cutoff + c.skin) + 1;
+    const double slack = h->d.R - cutoff;
     p.skin_half2 = 0.25 * slack * slack;
 }
 
-static int prepare(dps_domain *h) {
-    if (!h->have_closure) FAIL(h, DPS_ERR_STATE, "dps_set_closure must be called first");
+// ---- table and tiles ------------------------------------------------------------
+// copy the device-side step state of every box into the host entries
+static int pull_state(Batch *B) {
+    if (B->boxes.empty() || !B->d_table) return DPS_OK;
+    CKB(B, cudaStreamSynchronize(B->stream));
+    std::vector<BoxDev> t(B->boxes.size());
+    CKB(B, cudaMemcpy(t.data(), B->d_table, sizeof(BoxDev) * t.size(), cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < B->boxes.size(); ++k) {
+        BoxDev &d = B->boxes[k]->d;
+        d.parity = t[k].parity;
+        d.cur = t[k].cur;
+        d.have_uprev = t[k].have_uprev;
+        d.have_usub = t[k].have_usub;
+    }
+    return DPS_OK;
+}
+
+static int ensure_buf(Batch *B, Tile **p, size_t *cap, size_t need) {
+    if (need <= *cap && *p) return DPS_OK;
+    size_t n = std::max<size_t>(need, 64);
+    Tile *q = (Tile *)dalloc_raw(B, n * sizeof(Tile));
+    if (!q) FAILB(B, DPS_ERR_OOM, "tile list allocation failed");
+    if (*p) {
+        dfree_raw(B, *p);
+        B->allocs.erase(std::remove(B->allocs.begin(), B->allocs.end(), (void *)*p), B->allocs.end());
+    }
+    B->allocs.push_back(q);
+    *p = q;
+    *cap = n;
+    return DPS_OK;
+}
+
+// rebuild the device table and the tile lists from the host boxes (the
+// device step state must have been pulled first)
+static int push_layout(Batch *B) {
+    const int nb = (int)B->boxes.size();
+    if (nb > B->table_cap) {
+        int cap = std::max(nb, std::max(2 * B->table_cap, 4));
+        BoxDev *t = (BoxDev *)dalloc_raw(B, sizeof(BoxDev) * cap);
+        if (!t) FAILB(B, DPS_ERR_OOM, "box table allocation failed");
+        if (B->d_table) {
+            dfree_raw(B, B->d_table);
+            B->allocs.erase(std::remove(B->allocs.begin(), B->allocs.end(), (void *)B->d_table), B->allocs.end());
+        }
+        B->allocs.push_back(t);
+        B->d_table = t;
+        B->table_cap = cap;
+    }
+    std::vector<BoxDev> tab(nb);
+    std::vector<Tile> cell, part, scan;
+    const long long ST = scan_tile_cells();
+    for (int k = 0; k < nb; ++k) {
+        BoxHost *h = B->boxes[k];
+        compute_phys(h);
+        tab[k] = h->d;
+        const long long N = h->d.g.ncell, np = h->d.np;
+        for (long long c = 0; c < N; c += B->tune.cell_tile)
+            cell.push_back(Tile{k, 0, c, std::min(N, c + B->tune.cell_tile)});
+        for (long long p = 0; p < np; p += B->tune.part_tile)
+            part.push_back(Tile{k, 0, p, std::min(np, p + B->tune.part_tile)});
+        int idx = 0;
+        for (long long c = 0; c < N; c += ST) scan.push_back(Tile{k, idx++, c, std::min(N, c + ST)});
+    }
+    int rc;
+    if ((rc = ensure_buf(B, &B->d_cell, &B->cap_cell, cell.size()))) return rc;
+    if ((rc = ensure_buf(B, &B->d_part, &B->cap_part, part.size()))) return rc;
+    if ((rc = ensure_buf(B, &B->d_scan, &B->cap_scan, scan.size()))) return rc;
+    if (nb) CKB(B, cudaMemcpyAsync(B->d_table, tab.data(), sizeof(BoxDev) * nb, cudaMemcpyHostToDevice, B->stream));
+    if (!cell.empty())
+        CKB(B, cudaMemcpyAsync(B->d_cell, cell.data(), sizeof(Tile) * cell.size(), cudaMemcpyHostToDevice, B->stream));
+    if (!part.empty())
+        CKB(B, cudaMemcpyAsync(B->d_part, part.data(), sizeof(Tile) * part.size(), cudaMemcpyHostToDevice, B->stream));
+    if (!scan.empty())
+        CKB(B, cudaMemcpyAsync(B->d_scan, scan.data(), sizeof(Tile) * scan.size(), cudaMemcpyHostToDevice, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
+    B->n_cell = (int)cell.size();
+    B->n_part = (int)part.size();
+    B->n_scan = (int)scan.size();
+    B->layout_dirty = false;
+    invalidate_graph(B);
+    return DPS_OK;
+}
+
+static int grid_of(int ntiles) { return std::max(1, std::min(ntiles, 152 * 8)); }
+
+// ---- the coupled step --------------------------------------------------------------
+#define PREC_CALL(B, F64CALL, F32CALL, F16CALL) \
+    do {                                        \
+        if ((B)->prec == DPS_F64) {             \
+            F64CALL;                            \
+        } else if ((B)->prec == DPS_F32) {      \
+            F32CALL;                            \
+        } else {                                \
+            F16CALL;                            \
+        }                                       \
+    } while (0)
+
+static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub) {
+    const BoxDev *T = B->d_table;
+    const int nb = (int)B->boxes.size();
+    const Tuning &u = B->tune;
+    const int pl = B->n_part > 0;
+    tbegin(B);
+    if (pl) launch_bsort_count(T, B->d_part, B->n_part, xsel, grid_of(B->n_part), u.part_block, B->stream);
+    launch_bscan(T, nb, B->d_scan, B->n_scan, B->stream);
+    if (pl) {
+        launch_bsort_scatter(T, B->d_part, B->n_part, grid_of(B->n_part), u.part_block, B->stream);
+        launch_bsort_rank(T, B->d_part, B->n_part, grid_of(B->n_part), u.part_block, B->stream);
+        launch_bsort_gather(T, B->d_part, B->n_part, xsel, grid_of(B->n_part), u.part_block, B->stream);
+    }
+    launch_bsort_flip(B->d_table, nb, mark_usub, B->stream);
+    tend(B, PH_SORT, 3 + 4 * pl + 1);
+    tbegin(B);
+    if (B->fel == 8)
+        launch_eps<double>(T, B->d_cell, B->n_cell, grid_of(B->n_cell), u.cell_block, B->stream);
+    else
+        launch_eps<float>(T, B->d_cell, B->n_cell, grid_of(B->n_cell), u.cell_block, B->stream);
+    tend(B, PH_EPS, 1);
+}
+
+static void enqueue_step(Batch *B) {
+    const BoxDev *T = B->d_table;
+    const Tuning &u = B->tune;
+    const int gc = grid_of(B->n_cell), gp = grid_of(B->n_part);
+    const int pl = B->n_part > 0;
+    const bool f64 = B->fel == 8;
+    cudaStream_t s = B->stream;
+    B->ev_used = 0;
+    B->launch_count = 0;
+    // Du_f/Dt and grad P, once per step
+    tbegin(B);
+    PREC_CALL(B, (launch_moments<double, double, double>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)),
+              (launch_moments<float, float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)),
+              (launch_moments<__half, float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)));
+    if (f64)
+        launch_fields<double, double>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
+    else
+        launch_fields<float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
+    tend(B, PH_MOM, 2);
+    for (int k = 0; k < B->n_int; ++k) {
+        tbegin(B);
+        if (pl) {
+            if (f64) launch_force_am<double>(T, B->d_part, B->n_part, gp, u.part_block, s);
+            else launch_force_am<float>(T, B->d_part, B->n_part, gp, u.part_block, s);
+        }
+        tend(B, PH_FAM, pl);
+        tbegin(B);
+        if (f64) launch_reaction_am<double>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
+        else launch_reaction_am<float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
+        tend(B, PH_RAM, 1);
+        tbegin(B);
+        if (pl) {
+            if (f64) launch_force_drag<double>(T, B->d_part, B->n_part, gp, u.part_block, s);
+            else launch_force_drag<float>(T, B->d_part, B->n_part, gp, u.part_block, s);
+        }
+        tend(B, PH_FDRAG, pl);
+        tbegin(B);
+        if (f64)
+            launch_reaction_drag<double>(T, B->d_cell, B->n_cell, k == 0, k == B->n_int - 1, gc, u.cell_block, s);
+        else
+            launch_reaction_drag<float>(T, B->d_cell, B->n_cell, k == 0, k == B->n_int - 1, gc, u.cell_block, s);
+        tend(B, PH_RDRAG, 1);
+        tbegin(B);
+        if (pl)
+            for (int sd = 0; sd < B->n_dem; ++sd) launch_dem_substep(T, B->d_part, B->n_part, sd & 1, gp, u.part_block, s);
+        tend(B, PH_DEM, pl * B->n_dem);
+        enqueue_sort_eps(B, B->n_dem & 1, 1);
+    }
+    tbegin(B);
+    PREC_CALL(B, (launch_collide_stream<double, double, double>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)),
+              (launch_collide_stream<float, float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)),
+              (launch_collide_stream<__half, float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)));
+    launch_end_step(B->d_table, (int)B->boxes.size(), s);
+    tend(B, PH_COLLIDE, 2);
+    B->launches_step = B->launch_count;
+}
+
+static int check_boxes(Batch *B) {
+    CKB(B, cudaStreamSynchronize(B->stream));
+    std::string m;
+    int bad = 0;
+    for (BoxHost *h : B->boxes) {
+        int st = 0;
+        CKB(B, cudaMemcpy(&st, h->d.status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st) {
+            CKB(B, cudaMemset(h->d.status, 0, sizeof(int)));
+            h->sticky |= st;
+            bad |= st;
+        }
+    }
+    if (bad) {
+        if (bad & ST_NAN) m += "non-finite or non-positive state; ";
+        if (bad & ST_SKIN) m += "a particle moved more than skin/2 within one subcycle (increase skin or n_int); ";
+        if (bad & ST_EPS_NEG) m += "eps_f < 0 before the floor; ";
+        if (bad & ST_BAD_CELL) m += "a particle left the box through a wall; ";
+        FAILB(B, DPS_ERR_UNSTABLE, "unstable: %s", m.c_str());
+    }
+    return DPS_OK;
+}
+
+// uniform subcycle counts over the batch; layout upload; prepare new boxes
+static int ready(Batch *B) {
+    for (BoxHost *h : B->boxes)
+        if (!h->have_closure) FAILB(B, DPS_ERR_STATE, "dps_set_closure must be called for every box first");
+    if (B->boxes.empty()) return DPS_OK;
+    B->n_int = B->boxes[0]->cl.n_int;
+    B->n_dem = B->boxes[0]->cl.n_dem;
+    for (BoxHost *h : B->boxes)
+        if (h->cl.n_int != B->n_int || h->cl.n_dem != B->n_dem)
+            FAILB(B, DPS_ERR_ARG, "all boxes of a batch need the same n_int and n_dem");
+    bool need_prep = false;
+    for (BoxHost *h : B->boxes) need_prep |= !h->prepared;
+    if (B->layout_dirty || need_prep) {
+        int rc = pull_state(B);
+        if (rc) return rc;
+        if ((rc = push_layout(B))) return rc;
+    }
+    if (need_prep) {
+        // Algorithm 1 initialisation: sort and eps_f for every box (idempotent
+        // for boxes already prepared: their particles did not move)
+        B->ev_used = 0;
+        bool t = B->timing;
+        B->timing = false;
+        enqueue_sort_eps(B, 0, 0);
+        B->timing = t;
+        for (BoxHost *h : B->boxes) h->prepared = true;
+        int rc = check_boxes(B);
+        if (rc) return rc;
+    }
+    return DPS_OK;
+}
+
+static int run_steps(Batch *B, long long n) {
+    int rc = ready(B);
+    if (rc) return rc;
+    if (B->boxes.empty()) return DPS_OK;
+    for (long long s = 0; s < n; ++s) {
+        if (!B->use_graphs) {
+            enqueue_step(B);
+        } else {
+            if (!B->gexec) {
+                cudaGraph_t g;
+                CKB(B, cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+                enqueue_step(B);
+                CKB(B, cudaStreamEndCapture(B->stream, &g));
+                cudaError_t e = cudaGraphInstantiate(&B->gexec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) FAILB(B, DPS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            }
+            CKB(B, cudaGraphLaunch(B->gexec, B->stream));
+        }
+        for (BoxHost *h : B->boxes) h->steps++;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) FAILB(B, DPS_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+    return DPS_OK;
+}
+
+// ---- boxes ------------------------------------------------------------------------------
+static int batch_init(Batch *B, int precision, void *stream, dps_alloc_fn a, dps_free_fn f, void *ctx) {
+    B->prec = precision;
+    B->pdf_elem = precision == DPS_F64 ? 8 : (precision == DPS_F32 ? 4 : 2);
+    B->fel = precision == DPS_F64 ? 8 : 4;
+    B->alloc = a;
+    B->free = f;
+    B->ctx = ctx;
+    const char *env = getenv("DPS_NO_GRAPH");
+    B->use_graphs = !(env && env[0] == '1');
+    B->stream = (cudaStream_t)stream;  // NULL: created with the first box
+    return DPS_OK;
+}
+
+static int ensure_stream(Batch *B) {
+    if (B->stream) return DPS_OK;
+    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        FAILB(B, DPS_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    B->own_stream = true;
+    return DPS_OK;
+}
+
+static void batch_release(Batch *B) {
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    invalidate_graph(B);
+    for (BoxHost *h : B->boxes) {
+        box_free(B, h);
+        delete h;
+    }
+    B->boxes.clear();
+    for (void *p : B->allocs) dfree_raw(B, p);
+    B->allocs.clear();
+    for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
+    B->ev.clear();
+    if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
+    B->stream = nullptr;
+}
+
+// bytes of device memory a box of n cells and cap particles needs
+static size_t box_bytes(int prec, long long ncell, long long cap) {
+    size_t pe = prec == DPS_F64 ? 8 : (prec == DPS_F32 ? 4 : 2), fe = prec == DPS_F64 ? 8 : 4;
+    size_t N = (size_t)ncell, C = (size_t)(cap > 0 ? cap : 1);
+    size_t b = 19 * N * pe + 26 * N * fe;
+    b += 2 * (size_t)NPF * C * 8 + 2 * (size_t)NPI * C * 4 + 9 * C * 8;
+    b += (3 * N + 1) * 4 + 3 * C * 4 + ((N + 8191) / 8192 + 1) * 4;
+    b += 4096 + (size_t)reduce_partials_doubles() * 8;
+    return b;
+}
+
+// allocate and initialise one box (fluid at rest, eps_f = 1, no particles)
+static int box_create(Batch *B, const int n[3], const int per[3], double tau, double rho_f, long long max_particles,
+                      BoxHost **out) {
+    *out = nullptr;
+    for (int a = 0; a < 3; ++a)
+        if (n[a] < 1) FAILB(B, DPS_ERR_ARG, "lattice size must be >= 1 per axis");
+    long long ncell = (long long)n[0] * n[1] * n[2];
+    if (ncell >= (1LL << 31) - 1) FAILB(B, DPS_ERR_ARG, "lattice too large for 32-bit cell indices");
+    if (!(tau > 0.5) || !(rho_f > 0.0) || max_particles < 0 || max_particles >= (1LL << 31))
+        FAILB(B, DPS_ERR_ARG, "invalid box (tau > 0.5, rho_f > 0, particle capacity)");
+    BoxHost *h = new BoxHost();
+    h->tau = tau;
+    h->rho_f = rho_f;
+    h->max_particles = max_particles;
+    BoxDev &d = h->d;
+    for (int a = 0; a < 3; ++a) {
+        d.g.n[a] = n[a];
+        d.g.per[a] = per[a] ? 1 : 0;
+        d.g.nb[a] = n[a];
+    }
+    d.g.B = 1;
+    d.g.ncell = ncell;
+    d.cap = max_particles > 0 ? max_particles : 1;
+    d.np = 0;
+    const size_t N = (size_t)ncell, cap = (size_t)d.cap;
+    bool ok = true;
+    auto A = [&](size_t bytes) {
+        void *p = box_alloc(B, h, bytes);
+        ok = ok && p;
+        return p;
+    };
+    d.pdf = A(19 * N * B->pdf_elem);
+    d.eps = A(N * B->fel);
+    d.rho = A(N * B->fel);
+    void **vec[] = {&d.fpf, &d.fam, &d.acc, &d.j, &d.uD, &d.uprev, &d.gradP, &d.DuDt};
+    for (void **v : vec) *v = A(3 * N * B->fel);
+    for (int s = 0; s < 2; ++s) {
+        d.pf[s] = (double *)A((size_t)NPF * cap * 8);
+        d.pi[s] = (int *)A((size_t)NPI * cap * 4);
+    }
+    d.xtmp = (double *)A(9 * cap * 8);
+    d.cell_start = (int *)A((N + 1) * 4);
+    d.count = (int *)A(N * 4);
+    d.fill = (int *)A(N * 4);
+    d.key = (int *)A(cap * 4);
+    d.tmp = (int *)A(cap * 4);
+    d.perm = (int *)A(cap * 4);
+    d.scan_part = (int *)A(((N + 8191) / 8192 + 1) * 4);
+    d.status = (int *)A(64);
+    d.counters = (unsigned long long *)A(8 * CNT_N);
+    h->d_red = (double *)A((size_t)reduce_partials_doubles() * 8);
+    h->d_redout = (double *)A(32 * 8);
+    if (!ok) {
+        box_free(B, h);
+        delete h;
+        FAILB(B, DPS_ERR_OOM, "device allocation failed");
+    }
+    if (ensure_stream(B)) {
+        box_free(B, h);
+        delete h;
+        return DPS_ERR_CUDA;
+    }
+    cudaStream_t s = B->stream;
+    PREC_CALL(B, launch_pdf_rest<double>(d.pdf, ncell, s), launch_pdf_rest<float>(d.pdf, ncell, s),
+              launch_pdf_rest<__half>(d.pdf, ncell, s));
+    if (B->fel == 8)
+        launch_fill<double>(d.eps, ncell, 1.0, s);
+    else
+        launch_fill<float>(d.eps, ncell, 1.0, s);
+    for (void *p : {d.fpf, d.fam, d.acc, d.j, d.uD, d.uprev, d.gradP, d.DuDt}) cudaMemsetAsync(p, 0, 3 * N * B->fel, s);
+    cudaMemsetAsync(d.rho, 0, N * B->fel, s);
+    for (int k = 0; k < 2; ++k) {
+        cudaMemsetAsync(d.pf[k], 0, (size_t)NPF * cap * 8, s);
+        cudaMemsetAsync(d.pi[k], 0, (size_t)NPI * cap * 4, s);
+    }
+    cudaMemsetAsync(d.cell_start, 0, (N + 1) * 4, s);
+    cudaMemsetAsync(d.count, 0, N * 4, s);
+    cudaMemsetAsync(d.fill, 0, N * 4, s);
+    cudaMemsetAsync(d.status, 0, 64, s);
+    cudaMemsetAsync(d.counters, 0, 8 * CNT_N, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        box_free(B, h);
+        delete h;
+        FAILB(B, DPS_ERR_CUDA, "initialisation kernels failed");
+    }
+    d.parity = d.cur = d.have_uprev = d.have_usub = 0;
     compute_phys(h);
-    do_sort(h, main_f(h));
-    eps_eval(h);
-    invalidate_graphs(h);
-    h->prepared = true;
-    return check_status(h);
+    *out = h;
+    return DPS_OK;
+}
+
+static int box_add_particles(Batch *B, BoxHost *h, long long n, const double *x3, const double *u3, const double *w3,
+                             const double *dd, const double *rp) {
+    if (n < 0 || (n > 0 && (!x3 || !dd || !rp))) FAILB(B, DPS_ERR_ARG, "bad particle arrays");
+    if (n == 0) return DPS_OK;
+    if (h->d.np + n > h->max_particles)
+        FAILB(B, DPS_ERR_ARG, "capacity exceeded (%lld + %lld > %lld)", h->d.np, n, h->max_particles);
+    for (int a = 0; a < 3; ++a)
+        if (h->d.g.n[a] < 3) FAILB(B, DPS_ERR_ARG, "particles need at least 3 cells per axis");
+    int rc = pull_state(B);
+    if (rc) return rc;
+    const long long cap = h->d.cap;
+    std::vector<double> st((size_t)11 * n);
+    std::vector<int> ids((size_t)n);
+    double sV = 0, sW = 0, dm = h->dmax;
+    for (long long i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            double x = x3[3 * i + a];
+            if (!std::isfinite(x)) FAILB(B, DPS_ERR_ARG, "non-finite position");
+            const int L = h->d.g.n[a];
+            if (h->d.g.per[a]) {
+                x -= L * std::floor(x / L);
+                if (x >= L) x -= L;
+            } else if (!(x > 0.0 && x < L)) {
+                FAILB(B, DPS_ERR_ARG, "particle %lld outside the walls on axis %d", i, a);
+            }
+            st[(size_t)a * n + i] = x;
+            st[(size_t)(3 + a) * n + i] = u3 ? u3[3 * i + a] : 0.0;
+            st[(size_t)(6 + a) * n + i] = w3 ? w3[3 * i + a] : 0.0;
+        }
+        if (!(dd[i] > 0.0) || !(rp[i] > 0.0)) FAILB(B, DPS_ERR_ARG, "d and rho_p must be > 0");
+        st[(size_t)9 * n + i] = dd[i];
+        st[(size_t)10 * n + i] = rp[i];
+        ids[i] = (int)(h->d.np + i);
+        double V = PI_H / 6.0 * dd[i] * dd[i] * dd[i];
+        sV += V;
+        sW += (rp[i] - h->rho_f) * V;
+        dm = std::fmax(dm, dd[i]);
+    }
+    double *pf = h->d.pf[h->d.cur];
+    const long long off = h->d.np;
+    for (int f = 0; f < 11; ++f)
+        CKB(B, cudaMemcpyAsync(pf + (size_t)f * cap + off, st.data() + (size_t)f * n, 8 * n, cudaMemcpyHostToDevice,
+                               B->stream));
+    for (int a = 0; a < 3; ++a)
+        CKB(B, cudaMemcpyAsync(pf + (size_t)(PUS0 + a) * cap + off, st.data() + (size_t)(3 + a) * n, 8 * n,
+                               cudaMemcpyHostToDevice, B->stream));
+    CKB(B, cudaMemcpyAsync(h->d.pi[h->d.cur] + IID * cap + off, ids.data(), 4 * n, cudaMemcpyHostToDevice, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
+    h->d.np += n;
+    h->sumV += sV;
+    h->sumWb += sW;
+    h->dmax = dm;
+    h->prepared = false;
+    B->layout_dirty = true;
+    return DPS_OK;
+}
+
+static int check_closure(Batch *B, const dps_closure *c) {
+    if (!c) FAILB(B, DPS_ERR_ARG, "null closure");
+    if (c->n_int < 1 || c->n_dem < 1 || !(c->e_n > 0.0 && c->e_n <= 1.0) || !(c->T_c > 0.0) || !(c->h_c >= 0.0) ||
+        !(c->h_min > 0.0) || !(c->mu_c >= 0.0) || !(c->eps_min > 0.0 && c->eps_min < 1.0) || !(c->skin >= 0.0) ||
+        !(c->lub_cap > 0.0) || c->fb_mode < 0 || c->fb_mode > 2)
+        FAILB(B, DPS_ERR_ARG, "invalid closure parameter");
+    return DPS_OK;
+}
+
+// ---- per-box host views -------------------------------------------------------------------
+static int box_read_fields(Batch *B, BoxHost *h, uint32_t mask, double *out, long long cap) {
+    if (mask & ~0x1FFu) FAILB(B, DPS_ERR_ARG, "unknown field bits");
+    const long long N = h->d.g.ncell;
+    static const int planes[9] = {1, 3, 3, 1, 3, 1, 3, 3, 3};
+    long long need = 0;
+    for (int b = 0; b < 9; ++b)
+        if (mask & (1u << b)) need += planes[b] * N;
+    if (!out && need) FAILB(B, DPS_ERR_ARG, "null output");
+    if (cap < need) FAILB(B, DPS_ERR_ARG, "output capacity %lld < %lld", cap, need);
+    int rc = h->have_closure && !h->prepared ? ready(B) : pull_state(B);
+    if (rc) return rc;
+    compute_phys(h);
+    const double *fb = h->d.ph.fb;
+    const BoxDev &d = h->d;
+    double *buf = nullptr;
+    CKB(B, cudaMallocAsync((void **)&buf, 8 * 3 * N, B->stream));
+    long long off = 0;
+    for (int b = 0; b < 9; ++b) {
+        if (!(mask & (1u << b))) continue;
+        const uint32_t bit = 1u << b;
+        if (bit == DPS_FIELD_RHO || bit == DPS_FIELD_UBAR || bit == DPS_FIELD_UF || bit == DPS_FIELD_P ||
+            bit == DPS_FIELD_FEXT) {
+            int what = bit == DPS_FIELD_RHO ? 0 : bit == DPS_FIELD_UBAR ? 1 : bit == DPS_FIELD_UF ? 2 : bit == DPS_FIELD_P ? 3 : 4;
+            PREC_CALL(B, (launch_fluid_export<double, double>(d.pdf, d.eps, d.fpf, d.g, fb, d.parity, what, buf, B->stream)),
+                      (launch_fluid_export<float, float>(d.pdf, d.eps, d.fpf, d.g, fb, d.parity, what, buf, B->stream)),
+                      (launch_fluid_export<__half, float>(d.pdf, d.eps, d.fpf, d.g, fb, d.parity, what, buf, B->stream)));
+        } else {
+            const void *src = bit == DPS_FIELD_EPS ? d.eps : bit == DPS_FIELD_FPF ? d.fpf : bit == DPS_FIELD_GRADP ? d.gradP : d.DuDt;
+            if (B->fel == 8)
+                launch_to_double<double>(src, planes[b] * N, buf, B->stream);
+            else
+                launch_to_double<float>(src, planes[b] * N, buf, B->stream);
+        }
+        CKB(B, cudaMemcpyAsync(out + off, buf, 8 * planes[b] * N, cudaMemcpyDeviceToHost, B->stream));
+        off += planes[b] * N;
+    }
+    CKB(B, cudaFreeAsync(buf, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
+    return DPS_OK;
+}
+
+static int box_read_particles(Batch *B, BoxHost *h, double *x3, double *u3, double *w3, double *F3, long long cap) {
+    const long long np = h->d.np;
+    if (cap < np) FAILB(B, DPS_ERR_ARG, "capacity %lld < %lld particles", cap, np);
+    if (np == 0) return DPS_OK;
+    int rc = pull_state(B);
+    if (rc) return rc;
+    double *buf = nullptr;
+    CKB(B, cudaMallocAsync((void **)&buf, 8 * 3 * np, B->stream));
+    double *dst[4] = {x3, u3, w3, F3};
+    const int plane[4] = {PX, PU, POX, PFH0};
+    const double *pf = h->d.pf[h->d.cur];
+    const int *ids = h->d.pi[h->d.cur] + IID * h->d.cap;
+    for (int k = 0; k < 4; ++k) {
+        if (!dst[k]) continue;
+        launch_particles_export(pf, plane[k], h->d.cap, np, ids, buf, B->stream);
+        CKB(B, cudaMemcpyAsync(dst[k], buf, 8 * 3 * np, cudaMemcpyDeviceToHost, B->stream));
+    }
+    CKB(B, cudaFreeAsync(buf, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
+    return DPS_OK;
+}
+
+static int box_write_particles(Batch *B, BoxHost *h, long long n, const double *x3, const double *u3, const double *w3) {
+    if (n != h->d.np) FAILB(B, DPS_ERR_ARG, "n must equal the number of particles (%lld)", h->d.np);
+    if (n == 0) return DPS_OK;
+    if (x3)
+        for (long long i = 0; i < 3 * n; ++i)
+            if (!std::isfinite(x3[i])) FAILB(B, DPS_ERR_ARG, "non-finite position");
+    int rc = pull_state(B);
+    if (rc) return rc;
+    double *buf = nullptr;
+    CKB(B, cudaMallocAsync((void **)&buf, 8 * 3 * n, B->stream));
+    const double *src[3] = {x3, u3, w3};
+    double *pf = h->d.pf[h->d.cur];
+    const int *ids = h->d.pi[h->d.cur] + IID * h->d.cap;
+    for (int k = 0; k < 3; ++k) {
+        if (!src[k]) continue;
+        CKB(B, cudaMemcpyAsync(buf, src[k], 8 * 3 * n, cudaMemcpyHostToDevice, B->stream));
+        launch_particles_import(pf, 3 * k, h->d.cap, n, ids, buf, B->stream);
+    }
+    CKB(B, cudaFreeAsync(buf, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
+    if (x3) h->prepared = false;
+    return DPS_OK;
+}
+
+static int box_stats(Batch *B, BoxHost *h, dps_stats *s) {
+    std::memset(s, 0, sizeof(*s));
+    int rc = pull_state(B);
+    if (rc) return rc;
+    compute_phys(h);
+    const BoxDev &d = h->d;
+    double fl[12], pt[6];
+    PREC_CALL(B, (launch_fluid_sums<double, double>(d.pdf, d.eps, d.fpf, d.g, d.ph.fb, d.parity, h->d_red, h->d_redout, B->stream)),
+              (launch_fluid_sums<float, float>(d.pdf, d.eps, d.fpf, d.g, d.ph.fb, d.parity, h->d_red, h->d_redout, B->stream)),
+              (launch_fluid_sums<__half, float>(d.pdf, d.eps, d.fpf, d.g, d.ph.fb, d.parity, h->d_red, h->d_redout, B->stream)));
+    CKB(B, cudaMemcpyAsync(fl, h->d_redout, sizeof(fl), cudaMemcpyDeviceToHost, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
+    launch_particle_sums(d.pf[d.cur], d.pf[d.cur], d.cap, d.np, h->d_red, h->d_redout, B->stream);
+    CKB(B, cudaMemcpyAsync(pt, h->d_redout, sizeof(pt), cudaMemcpyDeviceToHost, B->stream));
+    unsigned long long cnt[CNT_N];
+    CKB(B, cudaMemcpyAsync(cnt, d.counters, sizeof(cnt), cudaMemcpyDeviceToHost, B->stream));
+    int st = 0;
+    CKB(B, cudaMemcpyAsync(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
+    const double N = (double)d.g.ncell;
+    s->mass = fl[0];
+    for (int a = 0; a < 3; ++a) {
+        s->fluid_j[a] = fl[1 + a];
+        s->fluid_ubar[a] = fl[4 + a];
+        s->uf_mean[a] = fl[7 + a] / N;
+        s->particle_momentum[a] = pt[a];
+        s->up_mean[a] = d.np ? pt[3 + a] / d.np : 0.0;
+        s->u_pS[a] = s->up_mean[a] - s->uf_mean[a];
+    }
+    s->eps_min_seen = fl[10];
+    s->step = h->steps;
+    s->n_particles = d.np;
+    s->n_eps_clamp = (int64_t)cnt[CNT_EPS_CLAMP];
+    s->n_lub_limited = (int64_t)cnt[CNT_LUB_LIMITED];
+    s->status = h->sticky | st;
+    return DPS_OK;
 }
 
 // ===============================================================================================
+// domain = batch of one box
+// ===============================================================================================
+struct dps_domain {
+    Batch B;
+    BoxHost *box = nullptr;
+};
+
+#define DOM_ERR(h) (h)->B.err
+
 extern "C" {
 
-const char *dps_version(void) { return "dps-gb300 0.1 (sm_103a)"; }
+const char *dps_version(void) { return "dps-gb300 0.2 (sm_103a)"; }
 
-const char *dps_last_error(dps_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+const char *dps_last_error(dps_handle h) { return h ? h->B.err.c_str() : g_create_err.c_str(); }
 
 void dps_lattice(int c[19][3], double w[19]) {
     for (int q = 0; q < Q; ++q) {
@@ -453,110 +903,43 @@ int dps_create_domain(const dps_domain_desc *desc, dps_handle *out) {
         g_create_err = "null argument";
         return DPS_ERR_ARG;
     }
+    if (desc->precision < DPS_F64 || desc->precision > DPS_F16S || ((desc->alloc == nullptr) != (desc->free == nullptr))) {
+        g_create_err = "invalid domain description (precision, allocator pair)";
+        return DPS_ERR_ARG;
+    }
     for (int a = 0; a < 3; ++a)
         if (desc->n[a] < 1) {
             g_create_err = "lattice size must be >= 1 per axis";
             return DPS_ERR_ARG;
         }
-    long long ncell = (long long)desc->n[0] * desc->n[1] * desc->n[2];
-    if (ncell >= (1LL << 31) - 1) {
-        g_create_err = "lattice too large for 32-bit cell indices";
-        return DPS_ERR_ARG;
-    }
-    if (!(desc->tau > 0.5) || !(desc->rho_f > 0.0) || desc->max_particles < 0 || desc->max_particles >= (1LL << 31) ||
-        desc->precision < DPS_F64 || desc->precision > DPS_F16S || ((desc->alloc == nullptr) != (desc->free == nullptr))) {
-        g_create_err = "invalid domain description (tau > 0.5, rho_f > 0, precision, particles, allocator pair)";
+    if (!(desc->tau > 0.5) || !(desc->rho_f > 0.0) || desc->max_particles < 0 || desc->max_particles >= (1LL << 31)) {
+        g_create_err = "invalid domain description (tau > 0.5, rho_f > 0, particle capacity)";
         return DPS_ERR_ARG;
     }
     dps_domain *h = new dps_domain();
-    h->desc = *desc;
-    h->prec = desc->precision;
-    h->pdf_elem = desc->precision == DPS_F64 ? 8 : (desc->precision == DPS_F32 ? 4 : 2);
-    h->fel = desc->precision == DPS_F64 ? 8 : 4;
-    for (int a = 0; a < 3; ++a) {
-        h->g.n[a] = desc->n[a];
-        h->g.per[a] = desc->periodic[a] ? 1 : 0;
-    }
-    h->g.ncell = ncell;
-    h->g.B = 1;
-    for (int a = 0; a < 3; ++a) h->g.nb[a] = desc->n[a];
-    h->cap = desc->max_particles > 0 ? desc->max_particles : 1;
-    const char *env = getenv("DPS_NO_GRAPH");
-    h->use_graphs = !(env && env[0] == '1');
-
-    auto bail = [&](int code, const char *msg) {
-        g_create_err = msg;
-        free_all(h);
+    if (batch_init(&h->B, desc->precision, desc->stream, desc->alloc, desc->free, desc->alloc_ctx)) {
+        g_create_err = "cudaStreamCreate failed";
         delete h;
-        return code;
-    };
-    const size_t N = (size_t)ncell, cap = (size_t)h->cap;
-    // allocations (fluid, particles, sort, status)
-    h->pdf = dalloc(h, (size_t)Q * N * h->pdf_elem);
-    void **fields[] = {&h->eps, &h->rho};
-    for (void **f : fields) *f = dalloc(h, N * h->fel);
-    void **vec[] = {&h->fpf, &h->fam, &h->acc, &h->j, &h->uD, &h->uprev, &h->gradP, &h->DuDt};
-    for (void **f : vec) *f = dalloc(h, 3 * N * h->fel);
-    for (int s = 0; s < 2; ++s) {
-        h->pf[s] = (double *)dalloc(h, (size_t)NPF * cap * sizeof(double));
-        h->pi[s] = (int *)dalloc(h, (size_t)NPI * cap * sizeof(int));
+        return DPS_ERR_CUDA;
     }
-    h->xtmp = (double *)dalloc(h, 9 * cap * sizeof(double));
-    h->cell_start = (int *)dalloc(h, (N + 1) * sizeof(int));
-    h->count = (int *)dalloc(h, N * sizeof(int));
-    h->fill = (int *)dalloc(h, N * sizeof(int));
-    h->key = (int *)dalloc(h, cap * sizeof(int));
-    h->tmp = (int *)dalloc(h, cap * sizeof(int));
-    h->perm = (int *)dalloc(h, cap * sizeof(int));
-    h->scan_scratch = (int *)dalloc(h, (size_t)scan_scratch_words((long long)N) * sizeof(int));
-    h->d_status = (int *)dalloc(h, sizeof(int) * 4);
-    h->d_counters = (unsigned long long *)dalloc(h, sizeof(unsigned long long) * CNT_N);
-    h->d_red = (double *)dalloc(h, (size_t)reduce_partials_doubles() * sizeof(double));
-    h->d_redout = (double *)dalloc(h, 32 * sizeof(double));
-    for (void *p : {(void *)h->pdf, h->eps, h->rho, h->fpf, h->fam, h->acc, h->j, h->uD, h->uprev, h->gradP, h->DuDt,
-                    (void *)h->pf[0], (void *)h->pf[1], (void *)h->pi[0], (void *)h->pi[1], (void *)h->xtmp,
-                    (void *)h->cell_start, (void *)h->count, (void *)h->fill, (void *)h->key, (void *)h->tmp,
-                    (void *)h->perm, (void *)h->scan_scratch, (void *)h->d_status, (void *)h->d_counters,
-                    (void *)h->d_red, (void *)h->d_redout})
-        if (!p) return bail(DPS_ERR_OOM, "device allocation failed");
-
-    if (desc->stream) {
-        h->stream = (cudaStream_t)desc->stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            return bail(DPS_ERR_CUDA, "cudaStreamCreate failed");
-        }
-        h->own_stream = true;
+    BoxHost *bx = nullptr;
+    int rc = box_create(&h->B, desc->n, desc->periodic, desc->tau, desc->rho_f, desc->max_particles, &bx);
+    if (rc) {
+        g_create_err = h->B.err;
+        batch_release(&h->B);
+        delete h;
+        return rc;
     }
-    // fluid at rest: f = w_q, eps_f = 1, all force fields zero
-    cudaStream_t s = h->stream;
-    DISPATCH_PREC(h, launch_pdf_rest<double>(h->pdf, ncell, s), launch_pdf_rest<float>(h->pdf, ncell, s),
-                  launch_pdf_rest<__half>(h->pdf, ncell, s));
-    if (h->prec == DPS_F64)
-        launch_fill<double>(h->eps, ncell, 1.0, s);
-    else
-        launch_fill<float>(h->eps, ncell, 1.0, s);
-    for (void *p : {h->fpf, h->fam, h->acc, h->j, h->uD, h->uprev, h->gradP, h->DuDt})
-        cudaMemsetAsync(p, 0, 3 * N * h->fel, s);
-    cudaMemsetAsync(h->rho, 0, N * h->fel, s);
-    for (int k = 0; k < 2; ++k) {
-        cudaMemsetAsync(h->pf[k], 0, (size_t)NPF * cap * sizeof(double), s);
-        cudaMemsetAsync(h->pi[k], 0, (size_t)NPI * cap * sizeof(int), s);
-    }
-    cudaMemsetAsync(h->cell_start, 0, (N + 1) * sizeof(int), s);
-    cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, s);
-    cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long) * CNT_N, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-        return bail(DPS_ERR_CUDA, "initialisation kernels failed");
+    h->box = bx;
+    h->B.boxes.push_back(bx);
+    h->B.layout_dirty = true;
     *out = h;
     return DPS_OK;
 }
 
 int dps_destroy(dps_handle h) {
     if (!h) return DPS_ERR_ARG;
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    free_all(h);
+    batch_release(&h->B);
     delete h;
     return DPS_OK;
 }
@@ -564,407 +947,458 @@ int dps_destroy(dps_handle h) {
 int dps_add_particles(dps_handle h, int64_t n, const double *x3, const double *u3, const double *w3, const double *d,
                       const double *rho_p) {
     if (!h) return DPS_ERR_ARG;
-    if (n < 0 || (n > 0 && (!x3 || !d || !rho_p))) FAIL(h, DPS_ERR_ARG, "bad particle arrays");
-    if (n == 0) return DPS_OK;
-    if (h->np + n > h->desc.max_particles) FAIL(h, DPS_ERR_ARG, "capacity exceeded (%lld + %lld > %lld)",
-                                                (long long)h->np, (long long)n, (long long)h->desc.max_particles);
-    for (int a = 0; a < 3; ++a)
-        if (h->g.n[a] < 3) FAIL(h, DPS_ERR_ARG, "particles need at least 3 cells per axis");
-    const long long cap = h->cap;
-    std::vector<double> st((size_t)11 * n);  // planes x,y,z,u,v,w,ox,oy,oz,d,rho
-    std::vector<int> ids((size_t)n);
-    double sV = 0, sW = 0, dm = h->dmax;
-    for (long long i = 0; i < n; ++i) {
-        for (int a = 0; a < 3; ++a) {
-            double x = x3[3 * i + a];
-            if (!std::isfinite(x)) FAIL(h, DPS_ERR_ARG, "non-finite position");
-            const int L = h->g.n[a];
-            if (h->g.per[a]) {
-                x -= L * std::floor(x / L);
-                if (x >= L) x -= L;
-            } else if (!(x > 0.0 && x < L)) {
-                FAIL(h, DPS_ERR_ARG, "particle %lld outside the walls on axis %d", i, a);
-            }
-            st[(size_t)a * n + i] = x;
-            st[(size_t)(3 + a) * n + i] = u3 ? u3[3 * i + a] : 0.0;
-            st[(size_t)(6 + a) * n + i] = w3 ? w3[3 * i + a] : 0.0;
-        }
-        if (!(d[i] > 0.0) || !(rho_p[i] > 0.0)) FAIL(h, DPS_ERR_ARG, "d and rho_p must be > 0");
-        st[(size_t)9 * n + i] = d[i];
-        st[(size_t)10 * n + i] = rho_p[i];
-        ids[i] = (int)(h->np + i);
-        double V = PI_H / 6.0 * d[i] * d[i] * d[i];
-        sV += V;
-        sW += (rho_p[i] - h->desc.rho_f) * V;
-        dm = std::fmax(dm, d[i]);
-    }
-    double *pf = main_f(h);
-    const long long off = h->np;
-    for (int f = 0; f < 11; ++f)
-        CK(h, cudaMemcpyAsync(pf + (size_t)f * cap + off, st.data() + (size_t)f * n, sizeof(double) * n,
-                              cudaMemcpyHostToDevice, h->stream));
-    // u at the start of the previous subcycle := u (no acceleration history yet)
-    for (int a = 0; a < 3; ++a)
-        CK(h, cudaMemcpyAsync(pf + (size_t)(PUS0 + a) * cap + off, st.data() + (size_t)(3 + a) * n, sizeof(double) * n,
-                              cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(main_i(h) + IID * cap + off, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    h->np += n;
-    h->sumV += sV;
-    h->sumWb += sW;
-    h->dmax = dm;
-    h->prepared = false;
-    return DPS_OK;
+    return box_add_particles(&h->B, h->box, n, x3, u3, w3, d, rho_p);
 }
 
 int dps_write_particles(dps_handle h, int64_t n, const double *x3, const double *u3, const double *w3) {
     if (!h) return DPS_ERR_ARG;
-    if (n != h->np) FAIL(h, DPS_ERR_ARG, "n must equal the number of particles (%lld)", (long long)h->np);
-    if (n == 0) return DPS_OK;
-    double *buf = nullptr;
-    CK(h, cudaMallocAsync((void **)&buf, sizeof(double) * 3 * n, h->stream));
-    const double *src[3] = {x3, u3, w3};
-    for (int k = 0; k < 3; ++k) {
-        if (!src[k]) continue;
-        if (k == 0)
-            for (long long i = 0; i < 3 * n; ++i)
-                if (!std::isfinite(x3[i])) {
-                    cudaFreeAsync(buf, h->stream);
-                    FAIL(h, DPS_ERR_ARG, "non-finite position");
-                }
-        CK(h, cudaMemcpyAsync(buf, src[k], sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
-        launch_particles_import(main_f(h), 3 * k, h->cap, n, main_i(h) + IID * h->cap, buf, h->stream);
-    }
-    CK(h, cudaFreeAsync(buf, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    if (x3) h->prepared = false;
-    return DPS_OK;
+    return box_write_particles(&h->B, h->box, n, x3, u3, w3);
 }
 
 int dps_set_closure(dps_handle h, const dps_closure *c) {
-    if (!h || !c) return DPS_ERR_ARG;
-    if (c->n_int < 1 || c->n_dem < 1 || !(c->e_n > 0.0 && c->e_n <= 1.0) || !(c->T_c > 0.0) || !(c->h_c >= 0.0) ||
-        !(c->h_min > 0.0) || !(c->mu_c >= 0.0) || !(c->eps_min > 0.0 && c->eps_min < 1.0) || !(c->skin >= 0.0) ||
-        !(c->lub_cap > 0.0) || c->fb_mode < 0 || c->fb_mode > 2)
-        FAIL(h, DPS_ERR_ARG, "invalid closure parameter");
-    h->cl = *c;
-    h->have_closure = true;
-    h->prepared = false;
+    if (!h) return DPS_ERR_ARG;
+    int rc = check_closure(&h->B, c);
+    if (rc) return rc;
+    h->box->cl = *c;
+    h->box->have_closure = true;
+    h->box->prepared = false;
+    h->B.layout_dirty = true;
     return DPS_OK;
 }
 
 int dps_prepare(dps_handle h) {
     if (!h) return DPS_ERR_ARG;
-    return prepare(h);
-}
-
-static int run_steps(dps_handle h, int64_t n) {
-    if (!h->have_closure) FAIL(h, DPS_ERR_STATE, "dps_set_closure must be called first");
-    if (!h->prepared) {
-        int rc = prepare(h);
-        if (rc) return rc;
-    }
-    for (int64_t s = 0; s < n; ++s) {
-        if (!h->use_graphs || !h->have_uprev || !h->have_usub) {
-            enqueue_step(h);
-            continue;
-        }
-        const int key = h->parity * 2 + h->cur;
-        if (!h->gexec[key]) {
-            const int p0 = h->parity, c0 = h->cur;
-            const long long st0 = h->step;
-            cudaGraph_t graph;
-            CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            enqueue_step(h);
-            CK(h, cudaStreamEndCapture(h->stream, &graph));
-            cudaError_t e = cudaGraphInstantiate(&h->gexec[key], graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) FAIL(h, DPS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-            // the capture only recorded the step: restore the host state
-            h->parity = p0;
-            h->cur = c0;
-            h->step = st0;
-        }
-        CK(h, cudaGraphLaunch(h->gexec[key], h->stream));
-        // advance the host-side state exactly as the step would
-        h->parity ^= 1;
-        if (h->ph.n_int & 1) h->cur ^= 1;
-        h->step++;
-    }
-    return DPS_OK;
+    h->box->prepared = false;
+    return ready(&h->B);
 }
 
 int dps_step_async(dps_handle h, int64_t n) {
     if (!h || n < 0) return DPS_ERR_ARG;
-    int rc = run_steps(h, n);
-    if (rc) return rc;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) FAIL(h, DPS_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
-    return DPS_OK;
+    return run_steps(&h->B, n);
 }
 
 int dps_check(dps_handle h) {
     if (!h) return DPS_ERR_ARG;
-    return check_status(h);
+    return check_boxes(&h->B);
 }
 
 int dps_step(dps_handle h, int64_t n) {
     int rc = dps_step_async(h, n);
     if (rc) return rc;
-    return check_status(h);
+    return check_boxes(&h->B);
 }
 
 int dps_collide_stream(dps_handle h, int64_t n) {
     if (!h || n < 0) return DPS_ERR_ARG;
-    double fb[3] = {0, 0, 0};
-    if (h->have_closure) {
-        compute_phys(h);
-        for (int a = 0; a < 3; ++a) fb[a] = h->ph.fb[a];
-    }
+    Batch *B = &h->B;
+    int rc = pull_state(B);
+    if (rc) return rc;
+    if ((rc = push_layout(B))) return rc;
     for (int64_t s = 0; s < n; ++s) {
-        k1(h, fb, 1);
-        h->parity ^= 1;
+        PREC_CALL(B, (launch_collide_stream<double, double, double>(B->d_table, B->d_cell, B->n_cell, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
+                  (launch_collide_stream<float, float, float>(B->d_table, B->d_cell, B->n_cell, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
+                  (launch_collide_stream<__half, float, float>(B->d_table, B->d_cell, B->n_cell, grid_of(B->n_cell), B->tune.cell_block, B->stream)));
+        launch_flip_parity(B->d_table, (int)B->boxes.size(), B->stream);
     }
-    return check_status(h);
+    return check_boxes(B);
 }
 
 int dps_sync(dps_handle h) {
     if (!h) return DPS_ERR_ARG;
-    CK(h, cudaStreamSynchronize(h->stream));
+    CKB(&h->B, cudaStreamSynchronize(h->B.stream));
     return DPS_OK;
-}
-
-static const double *current_fb(dps_handle h) {
-    static thread_local double zero[3] = {0, 0, 0};
-    if (!h->have_closure) return zero;
-    compute_phys(h);
-    return h->ph.fb;
 }
 
 int dps_read_fields(dps_handle h, uint32_t mask, double *out, int64_t cap) {
-    if (!h || (!out && mask)) return DPS_ERR_ARG;
-    if (mask & ~0x1FFu) FAIL(h, DPS_ERR_ARG, "unknown field bits");
-    const long long N = h->g.ncell;
-    static const int planes[9] = {1, 3, 3, 1, 3, 1, 3, 3, 3};
-    long long need = 0;
-    for (int b = 0; b < 9; ++b)
-        if (mask & (1u << b)) need += planes[b] * N;
-    if (cap < need) FAIL(h, DPS_ERR_ARG, "output capacity %lld < %lld", (long long)cap, need);
-    if (h->have_closure && !h->prepared) {
-        int rc = prepare(h);
-        if (rc) return rc;
-    }
-    const double *fb = current_fb(h);
-    double *buf = nullptr;
-    CK(h, cudaMallocAsync((void **)&buf, sizeof(double) * 3 * N, h->stream));
-    long long off = 0;
-    for (int b = 0; b < 9; ++b) {
-        if (!(mask & (1u << b))) continue;
-        const uint32_t bit = 1u << b;
-        if (bit == DPS_FIELD_RHO || bit == DPS_FIELD_UBAR || bit == DPS_FIELD_UF || bit == DPS_FIELD_P ||
-            bit == DPS_FIELD_FEXT) {
-            int what = bit == DPS_FIELD_RHO ? 0 : bit == DPS_FIELD_UBAR ? 1 : bit == DPS_FIELD_UF ? 2 : bit == DPS_FIELD_P ? 3 : 4;
-            DISPATCH_PREC(h, (launch_fluid_export<double, double>(h->pdf, h->eps, h->fpf, h->g, fb, h->parity, what, buf, h->stream)),
-                          (launch_fluid_export<float, float>(h->pdf, h->eps, h->fpf, h->g, fb, h->parity, what, buf, h->stream)),
-                          (launch_fluid_export<__half, float>(h->pdf, h->eps, h->fpf, h->g, fb, h->parity, what, buf, h->stream)));
-        } else {
-            const void *src = bit == DPS_FIELD_EPS ? h->eps : bit == DPS_FIELD_FPF ? h->fpf : bit == DPS_FIELD_GRADP ? h->gradP : h->DuDt;
-            if (h->fel == 8)
-                launch_to_double<double>(src, planes[b] * N, buf, h->stream);
-            else
-                launch_to_double<float>(src, planes[b] * N, buf, h->stream);
-        }
-        CK(h, cudaMemcpyAsync(out + off, buf, sizeof(double) * planes[b] * N, cudaMemcpyDeviceToHost, h->stream));
-        off += planes[b] * N;
-    }
-    CK(h, cudaFreeAsync(buf, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    return DPS_OK;
+    if (!h) return DPS_ERR_ARG;
+    return box_read_fields(&h->B, h->box, mask, out, cap);
 }
 
 int dps_write_fields(dps_handle h, uint32_t mask, const double *in, int64_t count) {
     if (!h || !in) return DPS_ERR_ARG;
-    if (mask & ~(DPS_FIELD_EPS | DPS_FIELD_FPF)) FAIL(h, DPS_ERR_ARG, "only eps_f and f_pf can be written");
-    const long long N = h->g.ncell;
+    Batch *B = &h->B;
+    BoxDev &d = h->box->d;
+    if (mask & ~(DPS_FIELD_EPS | DPS_FIELD_FPF)) FAILB(B, DPS_ERR_ARG, "only eps_f and f_pf can be written");
+    const long long N = d.g.ncell;
     long long need = ((mask & DPS_FIELD_EPS) ? N : 0) + ((mask & DPS_FIELD_FPF) ? 3 * N : 0);
-    if (count < need) FAIL(h, DPS_ERR_ARG, "input has %lld values, %lld needed", (long long)count, need);
+    if (count < need) FAILB(B, DPS_ERR_ARG, "input has %lld values, %lld needed", (long long)count, need);
+    if (mask & DPS_FIELD_EPS)
+        for (long long c = 0; c < N; ++c)
+            if (!(in[c] > 0.0 && in[c] <= 1.0)) FAILB(B, DPS_ERR_ARG, "eps_f must lie in (0, 1]");
     double *buf = nullptr;
-    CK(h, cudaMallocAsync((void **)&buf, sizeof(double) * 3 * N, h->stream));
+    CKB(B, cudaMallocAsync((void **)&buf, 8 * 3 * N, B->stream));
     long long off = 0;
     if (mask & DPS_FIELD_EPS) {
-        for (long long c = 0; c < N; ++c)
-            if (!(in[c] > 0.0 && in[c] <= 1.0)) {
-                cudaFreeAsync(buf, h->stream);
-                FAIL(h, DPS_ERR_ARG, "eps_f must lie in (0, 1]");
-            }
-        CK(h, cudaMemcpyAsync(buf, in, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
-        if (h->fel == 8) launch_from_double<double>(buf, N, h->eps, h->stream);
-        else launch_from_double<float>(buf, N, h->eps, h->stream);
+        CKB(B, cudaMemcpyAsync(buf, in, 8 * N, cudaMemcpyHostToDevice, B->stream));
+        if (B->fel == 8) launch_from_double<double>(buf, N, d.eps, B->stream);
+        else launch_from_double<float>(buf, N, d.eps, B->stream);
         off += N;
     }
     if (mask & DPS_FIELD_FPF) {
-        CK(h, cudaMemcpyAsync(buf, in + off, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
-        if (h->fel == 8) launch_from_double<double>(buf, 3 * N, h->fpf, h->stream);
-        else launch_from_double<float>(buf, 3 * N, h->fpf, h->stream);
+        CKB(B, cudaMemcpyAsync(buf, in + off, 8 * 3 * N, cudaMemcpyHostToDevice, B->stream));
+        if (B->fel == 8) launch_from_double<double>(buf, 3 * N, d.fpf, B->stream);
+        else launch_from_double<float>(buf, 3 * N, d.fpf, B->stream);
     }
-    CK(h, cudaFreeAsync(buf, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+    CKB(B, cudaFreeAsync(buf, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
     return DPS_OK;
 }
 
 int dps_read_pdfs(dps_handle h, double *out, int64_t cap) {
     if (!h || !out) return DPS_ERR_ARG;
-    const long long N = h->g.ncell;
-    if (cap < (long long)Q * N) FAIL(h, DPS_ERR_ARG, "output capacity too small");
+    Batch *B = &h->B;
+    int rc = pull_state(B);
+    if (rc) return rc;
+    const BoxDev &d = h->box->d;
+    const long long N = d.g.ncell;
+    if (cap < (long long)Q * N) FAILB(B, DPS_ERR_ARG, "output capacity too small");
     double *buf = nullptr;
-    CK(h, cudaMallocAsync((void **)&buf, sizeof(double) * Q * N, h->stream));
-    DISPATCH_PREC(h, launch_pdf_export<double>(h->pdf, h->g, h->parity, buf, h->stream),
-                  launch_pdf_export<float>(h->pdf, h->g, h->parity, buf, h->stream),
-                  launch_pdf_export<__half>(h->pdf, h->g, h->parity, buf, h->stream));
-    CK(h, cudaMemcpyAsync(out, buf, sizeof(double) * Q * N, cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaFreeAsync(buf, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+    CKB(B, cudaMallocAsync((void **)&buf, 8 * Q * N, B->stream));
+    PREC_CALL(B, launch_pdf_export<double>(d.pdf, d.g, d.parity, buf, B->stream),
+              launch_pdf_export<float>(d.pdf, d.g, d.parity, buf, B->stream),
+              launch_pdf_export<__half>(d.pdf, d.g, d.parity, buf, B->stream));
+    CKB(B, cudaMemcpyAsync(out, buf, 8 * Q * N, cudaMemcpyDeviceToHost, B->stream));
+    CKB(B, cudaFreeAsync(buf, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
     return DPS_OK;
 }
 
 int dps_write_pdfs(dps_handle h, const double *in, int64_t count) {
     if (!h || !in) return DPS_ERR_ARG;
-    const long long N = h->g.ncell;
-    if (count < (long long)Q * N) FAIL(h, DPS_ERR_ARG, "input too small");
+    Batch *B = &h->B;
+    int rc = pull_state(B);
+    if (rc) return rc;
+    BoxDev &d = h->box->d;
+    const long long N = d.g.ncell;
+    if (count < (long long)Q * N) FAILB(B, DPS_ERR_ARG, "input too small");
     double *buf = nullptr;
-    CK(h, cudaMallocAsync((void **)&buf, sizeof(double) * Q * N, h->stream));
-    CK(h, cudaMemcpyAsync(buf, in, sizeof(double) * Q * N, cudaMemcpyHostToDevice, h->stream));
-    DISPATCH_PREC(h, launch_pdf_import<double>(h->pdf, N, buf, h->stream), launch_pdf_import<float>(h->pdf, N, buf, h->stream),
-                  launch_pdf_import<__half>(h->pdf, N, buf, h->stream));
-    CK(h, cudaFreeAsync(buf, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    h->parity = 0;
-    invalidate_graphs(h);
-    return DPS_OK;
+    CKB(B, cudaMallocAsync((void **)&buf, 8 * Q * N, B->stream));
+    CKB(B, cudaMemcpyAsync(buf, in, 8 * Q * N, cudaMemcpyHostToDevice, B->stream));
+    PREC_CALL(B, launch_pdf_import<double>(d.pdf, N, buf, B->stream), launch_pdf_import<float>(d.pdf, N, buf, B->stream),
+              launch_pdf_import<__half>(d.pdf, N, buf, B->stream));
+    CKB(B, cudaFreeAsync(buf, B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
+    d.parity = 0;
+    return push_layout(B);
 }
 
 int dps_read_particles(dps_handle h, double *x3, double *u3, double *w3, double *F3, int64_t cap) {
     if (!h) return DPS_ERR_ARG;
-    const long long np = h->np;
-    if (cap < np) FAIL(h, DPS_ERR_ARG, "capacity %lld < %lld particles", (long long)cap, np);
-    if (np == 0) return DPS_OK;
-    double *buf = nullptr;
-    CK(h, cudaMallocAsync((void **)&buf, sizeof(double) * 3 * np, h->stream));
-    double *dst[4] = {x3, u3, w3, F3};
-    const int plane[4] = {PX, PU, POX, PFH0};
-    for (int k = 0; k < 4; ++k) {
-        if (!dst[k]) continue;
-        launch_particles_export(main_f(h), plane[k], h->cap, np, main_i(h) + IID * h->cap, buf, h->stream);
-        CK(h, cudaMemcpyAsync(dst[k], buf, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, h->stream));
-    }
-    CK(h, cudaFreeAsync(buf, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    return DPS_OK;
+    return box_read_particles(&h->B, h->box, x3, u3, w3, F3, cap);
 }
 
 int dps_stats_get(dps_handle h, dps_stats *s) {
     if (!h || !s) return DPS_ERR_ARG;
-    std::memset(s, 0, sizeof(*s));
-    const double *fb = current_fb(h);
-    double fl[12], pt[6];
-    DISPATCH_PREC(h, (launch_fluid_sums<double, double>(h->pdf, h->eps, h->fpf, h->g, fb, h->parity, h->d_red, h->d_redout, h->stream)),
-                  (launch_fluid_sums<float, float>(h->pdf, h->eps, h->fpf, h->g, fb, h->parity, h->d_red, h->d_redout, h->stream)),
-                  (launch_fluid_sums<__half, float>(h->pdf, h->eps, h->fpf, h->g, fb, h->parity, h->d_red, h->d_redout, h->stream)));
-    CK(h, cudaMemcpyAsync(fl, h->d_redout, sizeof(fl), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    launch_particle_sums(main_f(h), main_f(h), h->cap, h->np, h->d_red, h->d_redout, h->stream);
-    CK(h, cudaMemcpyAsync(pt, h->d_redout, sizeof(pt), cudaMemcpyDeviceToHost, h->stream));
-    unsigned long long cnt[CNT_N];
-    CK(h, cudaMemcpyAsync(cnt, h->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
-    int st = 0;
-    CK(h, cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    const double N = (double)h->g.ncell;
-    s->mass = fl[0];
-    for (int a = 0; a < 3; ++a) {
-        s->fluid_j[a] = fl[1 + a];
-        s->fluid_ubar[a] = fl[4 + a];
-        s->uf_mean[a] = fl[7 + a] / N;
-        s->particle_momentum[a] = pt[a];
-        s->up_mean[a] = h->np ? pt[3 + a] / h->np : 0.0;
-        s->u_pS[a] = s->up_mean[a] - s->uf_mean[a];
-    }
-    s->eps_min_seen = fl[10];
-    s->step = h->step;
-    s->n_particles = h->np;
-    s->n_eps_clamp = (int64_t)cnt[CNT_EPS_CLAMP];
-    s->n_lub_limited = (int64_t)cnt[CNT_LUB_LIMITED];
-    s->status = h->sticky | st;
-    return DPS_OK;
+    return box_stats(&h->B, h->box, s);
 }
 
 int dps_read_cell_list(dps_handle h, int32_t *cell_start, int32_t *order, int64_t cap_cells, int64_t cap_particles) {
     if (!h || !cell_start || !order) return DPS_ERR_ARG;
-    if (cap_cells < h->g.ncell + 1 || cap_particles < h->np) FAIL(h, DPS_ERR_ARG, "capacity too small");
-    if (h->have_closure && !h->prepared) {
-        int rc = prepare(h);
-        if (rc) return rc;
+    Batch *B = &h->B;
+    const BoxDev &d0 = h->box->d;
+    if (cap_cells < d0.g.ncell + 1 || cap_particles < d0.np) FAILB(B, DPS_ERR_ARG, "capacity too small");
+    int rc = h->box->have_closure && !h->box->prepared ? ready(B) : pull_state(B);
+    if (rc) return rc;
+    const BoxDev &d = h->box->d;
+    CKB(B, cudaMemcpy(cell_start, d.cell_start, 4 * (d.g.ncell + 1), cudaMemcpyDeviceToHost));
+    if (d.np) CKB(B, cudaMemcpy(order, d.pi[d.cur] + IID * d.cap, 4 * d.np, cudaMemcpyDeviceToHost));
+    return DPS_OK;
+}
+
+int dps_bin_edge(dps_handle h, int *R) {
+    if (!h || !R) return DPS_ERR_ARG;
+    if (!h->box->have_closure) FAILB(&h->B, DPS_ERR_STATE, "no closure");
+    compute_phys(h->box);
+    *R = h->box->d.R;
+    return DPS_OK;
+}
+
+// ---- tracing -------------------------------------------------------------------------------
+static int b_set_timing(Batch *B, int enable) {
+    if ((enable != 0) != B->timing) {
+        CKB(B, cudaStreamSynchronize(B->stream));
+        B->timing = enable != 0;
+        invalidate_graph(B);
     }
-    CK(h, cudaMemcpyAsync(cell_start, h->cell_start, sizeof(int) * (h->g.ncell + 1), cudaMemcpyDeviceToHost, h->stream));
-    if (h->np)
-        CK(h, cudaMemcpyAsync(order, main_i(h) + IID * h->cap, sizeof(int) * h->np, cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
     return DPS_OK;
 }
-
-int dps_bin_edge(dps_handle h, int *B) {
-    if (!h || !B) return DPS_ERR_ARG;
-    if (!h->have_closure) FAIL(h, DPS_ERR_STATE, "no closure");
-    compute_phys(h);
-    *B = h->R;
-    return DPS_OK;
-}
-
-int dps_set_timing(dps_handle h, int enable) {
-    if (!h) return DPS_ERR_ARG;
-    if ((enable != 0) != h->timing) {
-        CK(h, cudaStreamSynchronize(h->stream));
-        h->timing = enable != 0;
-        invalidate_graphs(h);
-    }
-    return DPS_OK;
-}
-
-int dps_collect_timing(dps_handle h) {
-    if (!h) return DPS_ERR_ARG;
-    CK(h, cudaStreamSynchronize(h->stream));
-    if (!h->timing) return DPS_OK;
-    for (size_t k = 0; k < h->ev_used; ++k) {
+static int b_collect_timing(Batch *B) {
+    CKB(B, cudaStreamSynchronize(B->stream));
+    if (!B->timing) return DPS_OK;
+    for (size_t k = 0; k < B->ev_used; ++k) {
         float ms = 0.f;
-        CK(h, cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]));
-        h->ph_ms[h->ev_phase[k]] += ms;
-        h->ph_nl[h->ev_phase[k]] += h->ev_nl[k];
+        CKB(B, cudaEventElapsedTime(&ms, B->ev[2 * k], B->ev[2 * k + 1]));
+        B->ph_ms[B->ev_phase[k]] += ms;
+        B->ph_nl[B->ev_phase[k]] += B->ev_nl[k];
     }
     return DPS_OK;
 }
-
-int dps_get_timing(dps_handle h, double ms[DPS_NPHASE], int64_t launches[DPS_NPHASE], int reset) {
-    if (!h) return DPS_ERR_ARG;
-    for (int k = 0; k < DPS_NPHASE; ++k) {
-        if (ms) ms[k] = h->ph_ms[k];
-        if (launches) launches[k] = h->ph_nl[k];
+static void b_get_timing(Batch *B, double *ms, int64_t *nl, int reset) {
+    for (int k = 0; k < NPH; ++k) {
+        if (ms) ms[k] = B->ph_ms[k];
+        if (nl) nl[k] = B->ph_nl[k];
         if (reset) {
-            h->ph_ms[k] = 0;
-            h->ph_nl[k] = 0;
+            B->ph_ms[k] = 0;
+            B->ph_nl[k] = 0;
         }
     }
-    return DPS_OK;
+}
+static long long b_launches_per_step(Batch *B) {
+    long long np = 0;
+    for (BoxHost *h : B->boxes) np += h->d.np;
+    const int pl = np > 0;
+    const int n_int = B->boxes.empty() ? 1 : B->boxes[0]->cl.n_int;
+    const int n_dem = B->boxes.empty() ? 1 : B->boxes[0]->cl.n_dem;
+    return 2 + 2 + (long long)n_int * (2 * pl + 2 + pl * n_dem + 3 + 4 * pl + 1 + 1);
 }
 
+int dps_set_timing(dps_handle h, int enable) { return h ? b_set_timing(&h->B, enable) : DPS_ERR_ARG; }
+int dps_collect_timing(dps_handle h) { return h ? b_collect_timing(&h->B) : DPS_ERR_ARG; }
+int dps_get_timing(dps_handle h, double ms[DPS_NPHASE], int64_t launches[DPS_NPHASE], int reset) {
+    if (!h) return DPS_ERR_ARG;
+    b_get_timing(&h->B, ms, launches, reset);
+    return DPS_OK;
+}
 int dps_launches_per_step(dps_handle h, int64_t *n) {
     if (!h || !n) return DPS_ERR_ARG;
-    if (!h->have_closure) FAIL(h, DPS_ERR_STATE, "no closure");
-    compute_phys(h);
-    const int pl = h->np > 0 ? 1 : 0;
-    *n = 2 + 1 + (long long)h->ph.n_int * (pl * 2 + 2 + pl * h->ph.n_dem + scan_launches(h->g.ncell) + 4 * pl + 1);
+    if (!h->box->have_closure) FAILB(&h->B, DPS_ERR_STATE, "no closure");
+    *n = b_launches_per_step(&h->B);
     return DPS_OK;
 }
 
+// ===============================================================================================
+// batch API
+// ===============================================================================================
+struct dps_batch_s {
+    Batch B;
+    std::vector<std::pair<int, BoxHost *>> ids;  // id -> box
+    int next_id = 0;
+};
+
+static BoxHost *find_box(dps_batch b, int id) {
+    for (auto &p : b->ids)
+        if (p.first == id) return p.second;
+    return nullptr;
+}
+
+#define BOX_OR_FAIL(b, id, h)                                              \
+    BoxHost *h = find_box(b, id);                                          \
+    if (!h) FAILB(&(b)->B, DPS_ERR_ARG, "unknown box id %d", (int)(id));
+
+int dps_batch_create(const dps_batch_desc *desc, dps_batch *out) {
+    if (out) *out = nullptr;
+    if (!desc || !out || desc->precision < DPS_F64 || desc->precision > DPS_F16S ||
+        ((desc->alloc == nullptr) != (desc->free == nullptr))) {
+        g_create_err = "invalid batch description";
+        return DPS_ERR_ARG;
+    }
+    dps_batch b = new dps_batch_s();
+    batch_init(&b->B, desc->precision, desc->stream, desc->alloc, desc->free, desc->alloc_ctx);
+    *out = b;
+    return DPS_OK;
+}
+
+int dps_batch_destroy(dps_batch b) {
+    if (!b) return DPS_ERR_ARG;
+    batch_release(&b->B);
+    delete b;
+    return DPS_OK;
+}
+
+int dps_batch_add_box(dps_batch b, const int n[3], const int periodic[3], double tau, double rho_f,
+                      int64_t max_particles, int *box) {
+    if (!b || !n || !periodic || !box) return DPS_ERR_ARG;
+    int rc = pull_state(&b->B);
+    if (rc) return rc;
+    BoxHost *h = nullptr;
+    rc = box_create(&b->B, n, periodic, tau, rho_f, max_particles, &h);
+    if (rc) return rc;
+    h->user_id = b->next_id;
+    b->B.boxes.push_back(h);
+    b->ids.push_back({b->next_id, h});
+    *box = b->next_id++;
+    b->B.layout_dirty = true;
+    return DPS_OK;
+}
+
+int dps_batch_remove_box(dps_batch b, int id) {
+    if (!b) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    int rc = pull_state(&b->B);
+    if (rc) return rc;
+    auto &v = b->B.boxes;
+    v.erase(std::remove(v.begin(), v.end(), h), v.end());
+    b->ids.erase(std::remove_if(b->ids.begin(), b->ids.end(), [&](const std::pair<int, BoxHost *> &p) { return p.first == id; }),
+                 b->ids.end());
+    box_free(&b->B, h);
+    delete h;
+    b->B.layout_dirty = true;
+    invalidate_graph(&b->B);
+    return DPS_OK;
+}
+
+int dps_batch_add_particles(dps_batch b, int id, int64_t n, const double *x3, const double *u3, const double *w3,
+                            const double *d, const double *rho_p) {
+    if (!b) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    return box_add_particles(&b->B, h, n, x3, u3, w3, d, rho_p);
+}
+
+int dps_batch_set_closure(dps_batch b, int id, const dps_closure *c) {
+    if (!b) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    int rc = check_closure(&b->B, c);
+    if (rc) return rc;
+    h->cl = *c;
+    h->have_closure = true;
+    h->prepared = false;
+    b->B.layout_dirty = true;
+    return DPS_OK;
+}
+
+int dps_batch_step_async(dps_batch b, int64_t n) {
+    if (!b || n < 0) return DPS_ERR_ARG;
+    return run_steps(&b->B, n);
+}
+int dps_batch_check(dps_batch b) { return b ? check_boxes(&b->B) : DPS_ERR_ARG; }
+int dps_batch_step(dps_batch b, int64_t n) {
+    int rc = dps_batch_step_async(b, n);
+    return rc ? rc : check_boxes(&b->B);
+}
+
+int dps_batch_read_particles(dps_batch b, int id, double *x3, double *u3, double *w3, double *F3, int64_t cap) {
+    if (!b) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    return box_read_particles(&b->B, h, x3, u3, w3, F3, cap);
+}
+int dps_batch_read_fields(dps_batch b, int id, uint32_t mask, double *out, int64_t cap) {
+    if (!b) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    return box_read_fields(&b->B, h, mask, out, cap);
+}
+int dps_batch_stats(dps_batch b, int id, dps_stats *s) {
+    if (!b || !s) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    return box_stats(&b->B, h, s);
+}
+int dps_batch_particle_mean(dps_batch b, int id, double u[3]) {
+    if (!b || !u) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    Batch *B = &b->B;
+    int rc = pull_state(B);
+    if (rc) return rc;
+    const BoxDev &d = h->d;
+    double pt[6] = {0, 0, 0, 0, 0, 0};
+    if (d.np) {
+        launch_particle_sums(d.pf[d.cur], d.pf[d.cur], d.cap, d.np, h->d_red, h->d_redout, B->stream);
+        CKB(B, cudaMemcpyAsync(pt, h->d_redout, sizeof(pt), cudaMemcpyDeviceToHost, B->stream));
+        CKB(B, cudaStreamSynchronize(B->stream));
+    }
+    for (int a = 0; a < 3; ++a) u[a] = d.np ? pt[3 + a] / d.np : 0.0;
+    return DPS_OK;
+}
+int dps_batch_num_boxes(dps_batch b, int *n) {
+    if (!b || !n) return DPS_ERR_ARG;
+    *n = (int)b->B.boxes.size();
+    return DPS_OK;
+}
+int dps_batch_set_tuning(dps_batch b, const int cfg[4]) {
+    if (!b || !cfg) return DPS_ERR_ARG;
+    for (int k = 0; k < 4; ++k)
+        if (cfg[k] < 32 || cfg[k] > (1 << 20)) FAILB(&b->B, DPS_ERR_ARG, "invalid launch shape");
+    if (cfg[0] > 256 || cfg[2] > 256 || (cfg[0] & 31) || (cfg[2] & 31))
+        FAILB(&b->B, DPS_ERR_ARG, "threads per block must be a multiple of 32, at most 256");
+    int rc = pull_state(&b->B);
+    if (rc) return rc;
+    b->B.tune = Tuning{cfg[0], cfg[1], cfg[2], cfg[3]};
+    b->B.layout_dirty = true;
+    return DPS_OK;
+}
+int dps_batch_get_tuning(dps_batch b, int cfg[4]) {
+    if (!b || !cfg) return DPS_ERR_ARG;
+    cfg[0] = b->B.tune.cell_block;
+    cfg[1] = b->B.tune.cell_tile;
+    cfg[2] = b->B.tune.part_block;
+    cfg[3] = b->B.tune.part_tile;
+    return DPS_OK;
+}
+
+// autotuner: candidate launch shapes for the cell kernels and the particle
+// kernels, each timed over `steps` replays of the step graph
+static int autotune(Batch *B, int steps, double *best_ms) {
+    static const int cell_c[][2] = {{128, 512}, {128, 2048}, {256, 1024}, {256, 4096}, {64, 256}, {128, 8192}};
+    static const int part_c[][2] = {{128, 128}, {128, 512}, {256, 256}, {64, 64}};
+    if (steps < 1) steps = 1;
+    int rc = ready(B);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_cfg = [&](const Tuning &t, double *ms) -> int {
+        int r = pull_state(B);
+        if (r) return r;
+        B->tune = t;
+        if ((r = push_layout(B))) return r;
+        if ((r = run_steps(B, 1))) return r;  // capture
+        cudaEventRecord(e0, B->stream);
+        if ((r = run_steps(B, steps))) return r;
+        cudaEventRecord(e1, B->stream);
+        CKB(B, cudaEventSynchronize(e1));
+        float f = 0;
+        cudaEventElapsedTime(&f, e0, e1);
+        *ms = f / steps;
+        return check_boxes(B);
+    };
+    Tuning best = B->tune;
+    double bms = 1e30;
+    for (auto &c : cell_c) {
+        Tuning t = best;
+        t.cell_block = c[0];
+        t.cell_tile = c[1];
+        double ms;
+        if ((rc = time_cfg(t, &ms))) break;
+        if (ms < bms) { bms = ms; best = t; }
+    }
+    if (!rc)
+        for (auto &c : part_c) {
+            Tuning t = best;
+            t.part_block = c[0];
+            t.part_tile = c[1];
+            double ms;
+            if ((rc = time_cfg(t, &ms))) break;
+            if (ms < bms) { bms = ms; best = t; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if ((rc = pull_state(B))) return rc;
+    B->tune = best;
+    B->tuned = true;
+    if ((rc = push_layout(B))) return rc;
+    if (best_ms) *best_ms = bms;
+    return DPS_OK;
+}
+
+int dps_batch_autotune(dps_batch b, int steps, double *best_ms) { return b ? autotune(&b->B, steps, best_ms) : DPS_ERR_ARG; }
+int dps_batch_set_timing(dps_batch b, int enable) { return b ? b_set_timing(&b->B, enable) : DPS_ERR_ARG; }
+int dps_batch_collect_timing(dps_batch b) { return b ? b_collect_timing(&b->B) : DPS_ERR_ARG; }
+int dps_batch_get_timing(dps_batch b, double ms[DPS_NPHASE], int64_t launches[DPS_NPHASE], int reset) {
+    if (!b) return DPS_ERR_ARG;
+    b_get_timing(&b->B, ms, launches, reset);
+    return DPS_OK;
+}
+int dps_batch_launches_per_step(dps_batch b, int64_t *n) {
+    if (!b || !n) return DPS_ERR_ARG;
+    *n = b_launches_per_step(&b->B);
+    return DPS_OK;
+}
+int dps_box_bytes(int precision, const int n[3], int64_t max_particles, size_t *bytes) {
+    if (!n || !bytes || precision < DPS_F64 || precision > DPS_F16S) return DPS_ERR_ARG;
+    *bytes = box_bytes(precision, (long long)n[0] * n[1] * n[2], max_particles);
+    return DPS_OK;
+}
+
+// ---- stateless op -------------------------------------------------------------------------
 int dps_op_cell_sort(const int n[3], const int periodic[3], int B, int64_t np, const double *x3, const int32_t *ids,
                      int32_t *cell_start, int32_t *order, void *stream) {
     if (!n || !periodic || np < 0 || (np > 0 && (!x3 || !ids || !order)) || !cell_start) return DPS_ERR_ARG;

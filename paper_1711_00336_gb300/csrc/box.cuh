@@ -1,0 +1,44 @@
+// box.cuh -- the device box table.  Every kernel of the coupled step works on
+// a list of tiles, each a contiguous range of cells or particles of one box;
+// one launch therefore advances any number of boxes of different sizes (the
+// single domain is a batch of one box).  Kernels read the box's geometry,
+// physics and buffer pointers from the table; per-launch state common to all
+// boxes (AA parity, which particle set is current) is passed by value.
+#pragma once
+#include "dps_internal.cuh"
+
+namespace dps {
+
+struct BoxDev {
+    Geom g;
+    Phys ph;
+    int R;             // neighbour search radius (cells)
+    // step state, advanced on the device so that one captured graph serves
+    // every step: AA parity, current particle set, history flags
+    int parity, cur, have_uprev, have_usub;
+    long long np, cap;
+    // fluid
+    void *pdf;
+    void *eps, *fpf, *fam, *acc, *rho, *j, *uD, *uprev, *gradP, *DuDt;
+    // particles: two SoA sets and the DEM ping-pong planes
+    double *pf[2];
+    int *pi[2];
+    double *xtmp;
+    // linked cells
+    int *cell_start, *count, *fill, *key, *tmp, *perm;
+    int *scan_part;    // per scan tile partial sums of this box
+    // status
+    int *status;
+    unsigned long long *counters;
+};
+
+struct Tile {
+    int box;
+    int first;         // index of this tile within its box (scan tiles)
+    long long begin, end;
+};
+
+// iterate the tiles of a launch: one block per tile, blocks stride over tiles
+#define DPS_FOR_TILES(tiles, ntiles, t) for (int t = blockIdx.x; t < (ntiles); t += gridDim.x)
+
+}  // namespace dps

@@ -9,7 +9,7 @@
 //     each lattice cell: no atomics, a fixed summation order.
 //  S4 particle forces (Table 1): added mass; pressure gradient, drag, gravity.
 //  S5 reaction force density (Eq. forces_pf) as the same 27-cell gather.
-#include "dps_internal.cuh"
+#include "box.cuh"
 
 namespace dps {
 
@@ -96,35 +96,116 @@ __global__ void k_sort_rank(const int *__restrict__ key, const int *__restrict__
     }
 }
 
-// reorder every particle field from (src, with x/u/w at xuw) into dst in the
-// sorted order; record the sort position and the coupling weights.
-__global__ void k_sort_gather(const double *__restrict__ srcf, const double *__restrict__ xuw, const int *__restrict__ srci,
-                              long long cap, long long np, const int *__restrict__ perm, const int *__restrict__ key,
-                              Geom g, double *__restrict__ dstf, int *__restrict__ dsti) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < np;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long i = perm[k];
-        double x[3];
-#pragma unroll
-        for (int f = 0; f < 9; ++f) {
-            double v = xuw[f * cap + i];
-            dstf[f * cap + k] = v;
-            if (f < 3) x[f] = v;
+// ---- S1 on the box table ----------------------------------------------------
+// x/u/w of box B: planes 0..8 of the current set, or the DEM ping-pong planes
+__device__ __forceinline__ const double *xuw_of(const BoxDev &B, int xsel) {
+    return xsel ? B.xtmp : B.pf[B.cur];
+}
+
+__global__ void k_bsort_count(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles,
+                              int xsel) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        const Geom g = B.g;
+        const double *x = xuw_of(B, xsel);
+        const long long cap = B.cap;
+        for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            long long c = particle_cell(g, x[i], x[cap + i], x[2 * cap + i], B.status);
+            B.key[i] = (int)c;
+            atomicAdd(&B.count[c], 1);
         }
-#pragma unroll
-        for (int f = 9; f < PXS0; ++f) dstf[f * cap + k] = srcf[f * cap + i];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            dstf[(PXS0 + a) * cap + k] = x[a];
-            double w[3];
-            axis_weights(x[a], g.n[a], g.per[a], w);
-            dstf[(PW0 + 3 * a + 0) * cap + k] = w[0];
-            dstf[(PW0 + 3 * a + 1) * cap + k] = w[1];
-            dstf[(PW0 + 3 * a + 2) * cap + k] = w[2];
+    }
+}
+
+__global__ void k_bsort_scatter(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            int k = B.key[i];
+            B.tmp[B.cell_start[k] + atomicAdd(&B.fill[k], 1)] = (int)i;
         }
-        dsti[IID * cap + k] = srci[IID * cap + i];
-        dsti[ICELL * cap + k] = key[i];
-        dsti[IKEY * cap + k] = key[i];
+    }
+}
+
+__global__ void k_bsort_rank(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        const int *ids = B.pi[B.cur] + IID * B.cap;
+        for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            int k = B.key[i];
+            int s = B.cell_start[k], e = B.cell_start[k + 1];
+            int my = ids[i], r = 0;
+            for (int q = s; q < e; ++q) r += ids[B.tmp[q]] < my;
+            B.perm[s + r] = (int)i;
+        }
+    }
+}
+
+// reorder every particle field into the other set in the sorted order;
+// record the sort position and the kernel weights (Eq. filter_def) per axis
+__global__ void k_bsort_gather(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles,
+                               int xsel) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        const Geom g = B.g;
+        const long long cap = B.cap;
+        const double *srcf = B.pf[B.cur], *xuw = xuw_of(B, xsel);
+        const int *srci = B.pi[B.cur];
+        double *dstf = B.pf[1 - B.cur];
+        int *dsti = B.pi[1 - B.cur];
+        for (long long k = tl.begin + threadIdx.x; k < tl.end; k += blockDim.x) {
+            const long long i = B.perm[k];
+            double x[3];
+#pragma unroll
+            for (int f = 0; f < 9; ++f) {
+                double v = xuw[f * cap + i];
+                dstf[f * cap + k] = v;
+                if (f < 3) x[f] = v;
+            }
+#pragma unroll
+            for (int f = 9; f < PXS0; ++f) dstf[f * cap + k] = srcf[f * cap + i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                dstf[(PXS0 + a) * cap + k] = x[a];
+                double w[3];
+                axis_weights(x[a], g.n[a], g.per[a], w);
+                dstf[(PW0 + 3 * a + 0) * cap + k] = w[0];
+                dstf[(PW0 + 3 * a + 1) * cap + k] = w[1];
+                dstf[(PW0 + 3 * a + 2) * cap + k] = w[2];
+            }
+            dsti[IID * cap + k] = srci[IID * cap + i];
+            dsti[ICELL * cap + k] = B.key[i];
+            dsti[IKEY * cap + k] = B.key[i];
+        }
+    }
+}
+
+// after the gather: the other set becomes current; after a subcycle (not the
+// initial sort) the particles' u at the subcycle start exists
+__global__ void k_bsort_flip(BoxDev *boxes, int nboxes, int mark_usub) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nboxes) {
+        boxes[b].cur ^= 1;
+        if (mark_usub) boxes[b].have_usub = 1;
+    }
+}
+
+// fluid-only collide-stream step: only the AA parity flips
+__global__ void k_flip_parity(BoxDev *boxes, int nboxes) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nboxes) boxes[b].parity ^= 1;
+}
+
+// end of an LBM step: the AA parity flips, the previous-step velocity exists
+__global__ void k_end_step(BoxDev *boxes, int nboxes) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nboxes) {
+        boxes[b].parity ^= 1;
+        boxes[b].have_uprev = 1;
     }
 }
 
@@ -181,24 +262,34 @@ __device__ __forceinline__ void gather27(const Geom &g, long long c, const int *
 }
 
 // ---- S2: eps_f ------------------------------------------------------------------
+// also clears the sort counts for the next sort (every cell visited once)
 template <typename FT>
-__global__ void k_eps_gather(Geom g, const int *__restrict__ cell_start, const double *__restrict__ pf,
-                             long long cap, double eps_min, FT *__restrict__ eps, unsigned long long *counters,
-                             int *status) {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
-         c += (long long)gridDim.x * blockDim.x) {
-        double ep = 0.0;
-        gather27(g, c, cell_start, pf, cap, [&](int p, double W) {
-            double d = pf[PD * cap + p];
-            ep += W * (PI_D / 6.0 * d * d * d);
-        });
-        double e = 1.0 - ep;
-        if (e < eps_min) {
-            if (e < 0.0) atomicOr(status, ST_EPS_NEG);
-            atomicAdd(&counters[CNT_EPS_CLAMP], 1ULL);
-            e = eps_min;
+__global__ void k_eps_gather(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        const Geom g = B.g;
+        const double *pf = B.pf[B.cur];
+        const long long cap = B.cap;
+        FT *eps = (FT *)B.eps;
+        const double eps_min = B.ph.eps_min;
+        unsigned nclamp = 0;
+        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
+            double ep = 0.0;
+            gather27(g, c, B.cell_start, pf, cap, [&](int p, double W) {
+                double d = pf[PD * cap + p];
+                ep += W * (PI_D / 6.0 * d * d * d);
+            });
+            double e = 1.0 - ep;
+            if (e < eps_min) {
+                if (e < 0.0) atomicOr(B.status, ST_EPS_NEG);
+                ++nclamp;
+                e = eps_min;
+            }
+            eps[c] = (FT)e;
+            B.count[c] = 0;
         }
-        eps[c] = (FT)e;
+        if (nclamp) atomicAdd(&B.counters[CNT_EPS_CLAMP], (unsigned long long)nclamp);
     }
 }
 
@@ -242,20 +333,28 @@ __device__ __forceinline__ void interp(const Geom &g, const double *__restrict__
 // K5a: added mass, F_am = C_am rho_f V (Du_f/Dt|p - du_p/dt) (Table 1);
 // du_p/dt is the change of u_p over the previous subcycle.
 template <typename FT>
-__global__ void k_force_am(Geom g, double *__restrict__ pf, const double *__restrict__ xuw, long long cap,
-                           long long np, const FT *__restrict__ DuDt, Phys ph, int have_usub) {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
-         p += (long long)gridDim.x * blockDim.x) {
-        double Du[3];
-        interp<FT, 3>(g, pf, cap, p, DuDt, Du);
-        double d = pf[PD * cap + p];
-        double V = PI_D / 6.0 * d * d * d;
+__global__ void k_force_am(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        const Geom g = B.g;
+        const Phys &ph = B.ph;
+        double *pf = B.pf[B.cur];
+        const long long cap = B.cap;
+        const FT *DuDt = (const FT *)B.DuDt;
+        const int have_usub = B.have_usub;
+        for (long long p = tl.begin + threadIdx.x; p < tl.end; p += blockDim.x) {
+            double Du[3];
+            interp<FT, 3>(g, pf, cap, p, DuDt, Du);
+            double d = pf[PD * cap + p];
+            double V = PI_D / 6.0 * d * d * d;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double u = xuw[(3 + a) * cap + p];
-            double dudt = have_usub ? (u - pf[(PUS0 + a) * cap + p]) / ph.dt_sub : 0.0;
-            pf[(PUS0 + a) * cap + p] = u;
-            pf[(PFA0 + a) * cap + p] = ph.added_mass ? ph.C_am * ph.rho_f * V * (Du[a] - dudt) : 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double u = pf[(PU + a) * cap + p];
+                double dudt = have_usub ? (u - pf[(PUS0 + a) * cap + p]) / ph.dt_sub : 0.0;
+                pf[(PUS0 + a) * cap + p] = u;
+                pf[(PFA0 + a) * cap + p] = ph.added_mass ? ph.C_am * ph.rho_f * V * (Du[a] - dudt) : 0.0;
+            }
         }
     }
 }
@@ -275,67 +374,72 @@ __device__ __forceinline__ double drag_cd(double Re, double e) {
 // 27 cells is evaluated on the fly from rho, j and the force density of this
 // subcycle: u_f = (j + (eps f_b + f_pf,am)/2)/(rho eps).
 template <typename FT>
-__global__ void k_force_drag(Geom g, double *__restrict__ pf, const double *__restrict__ xuw, long long cap,
-                             long long np, const FT *__restrict__ rho, const FT *__restrict__ j,
-                             const FT *__restrict__ eps, const FT *__restrict__ fam, const FT *__restrict__ gradP,
-                             Phys ph) {
-    const long long N = g.ncell;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
-         p += (long long)gridDim.x * blockDim.x) {
-        double wx[3], wy[3], wz[3];
+__global__ void k_force_drag(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &Bx = boxes[tl.box];
+        const Geom g = Bx.g;
+        const Phys &ph = Bx.ph;
+        const long long N = g.ncell, cap = Bx.cap;
+        double *pf = Bx.pf[Bx.cur];
+        const FT *rho = (const FT *)Bx.rho, *j = (const FT *)Bx.j, *eps = (const FT *)Bx.eps;
+        const FT *fam = (const FT *)Bx.fam, *gradP = (const FT *)Bx.gradP;
+        for (long long p = tl.begin + threadIdx.x; p < tl.end; p += blockDim.x) {
+            double wx[3], wy[3], wz[3];
 #pragma unroll
-        for (int o = 0; o < 3; ++o) {
-            wx[o] = pf[(PW0 + o) * cap + p];
-            wy[o] = pf[(PW0 + 3 + o) * cap + p];
-            wz[o] = pf[(PW0 + 6 + o) * cap + p];
-        }
-        int bx = containing_cell(pf[PXS0 * cap + p], g.n[0]);
-        int by = containing_cell(pf[(PXS0 + 1) * cap + p], g.n[1]);
-        int bz = containing_cell(pf[(PXS0 + 2) * cap + p], g.n[2]);
-        double uf[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, ef = 0.0;
+            for (int o = 0; o < 3; ++o) {
+                wx[o] = pf[(PW0 + o) * cap + p];
+                wy[o] = pf[(PW0 + 3 + o) * cap + p];
+                wz[o] = pf[(PW0 + 6 + o) * cap + p];
+            }
+            int bx = containing_cell(pf[PXS0 * cap + p], g.n[0]);
+            int by = containing_cell(pf[(PXS0 + 1) * cap + p], g.n[1]);
+            int bz = containing_cell(pf[(PXS0 + 2) * cap + p], g.n[2]);
+            double uf[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, ef = 0.0;
 #pragma unroll 1
-        for (int oz = 0; oz < 3; ++oz) {
-            int z = wrap_axis(bz + oz - 1, g.n[2], g.per[2]);
-            if (z < 0) continue;
-            for (int oy = 0; oy < 3; ++oy) {
-                int y = wrap_axis(by + oy - 1, g.n[1], g.per[1]);
-                if (y < 0) continue;
-                for (int ox = 0; ox < 3; ++ox) {
-                    int x = wrap_axis(bx + ox - 1, g.n[0], g.per[0]);
-                    if (x < 0) continue;
-                    long long c = cell_index(g, x, y, z);
-                    double W = wx[ox] * wy[oy] * wz[oz];
-                    double e = (double)eps[c], r = (double)rho[c];
-                    double s = 1.0 / (r * e);
+            for (int oz = 0; oz < 3; ++oz) {
+                int z = wrap_axis(bz + oz - 1, g.n[2], g.per[2]);
+                if (z < 0) continue;
+                for (int oy = 0; oy < 3; ++oy) {
+                    int y = wrap_axis(by + oy - 1, g.n[1], g.per[1]);
+                    if (y < 0) continue;
+                    for (int ox = 0; ox < 3; ++ox) {
+                        int x = wrap_axis(bx + ox - 1, g.n[0], g.per[0]);
+                        if (x < 0) continue;
+                        long long c = cell_index(g, x, y, z);
+                        double W = wx[ox] * wy[oy] * wz[oz];
+                        double e = (double)eps[c], r = (double)rho[c];
+                        double s = 1.0 / (r * e);
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        double F = e * ph.fb[a] + (double)fam[a * N + c];
-                        uf[a] += W * ((double)j[a * N + c] + 0.5 * F) * s;
-                        gp[a] += W * (double)gradP[a * N + c];
+                        for (int a = 0; a < 3; ++a) {
+                            double F = e * ph.fb[a] + (double)fam[a * N + c];
+                            uf[a] += W * ((double)j[a * N + c] + 0.5 * F) * s;
+                            gp[a] += W * (double)gradP[a * N + c];
+                        }
+                        ef += W * e;
                     }
-                    ef += W * e;
                 }
             }
-        }
-        double d = pf[PD * cap + p], rp = pf[PRHO * cap + p];
-        double V = PI_D / 6.0 * d * d * d;
-        double ep = 1.0 - ef;
-        double du[3], dun = 0.0;
+            double d = pf[PD * cap + p], rp = pf[PRHO * cap + p];
+            double V = PI_D / 6.0 * d * d * d;
+            double ep = 1.0 - ef;
+            double du[3], dun = 0.0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            du[a] = uf[a] - xuw[(3 + a) * cap + p];
-            dun += du[a] * du[a];
-        }
-        dun = sqrt(dun);
-        double Re = ef * ph.rho_f * d * dun / ph.mu;
-        double coef = ph.drag ? 3.0 * PI_D * d * ph.mu * (1.0 - ep) * drag_cd(Re, ep) : 0.0;
+            for (int a = 0; a < 3; ++a) {
+                du[a] = uf[a] - pf[(PU + a) * cap + p];
+                dun += du[a] * du[a];
+            }
+            dun = sqrt(dun);
+            double Re = ef * ph.rho_f * d * dun / ph.mu;
+            double coef = ph.drag ? 3.0 * PI_D * d * ph.mu * (1.0 - ep) * drag_cd(Re, ep) : 0.0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double Fd = coef * du[a];
-            double Fpr = ph.pressure ? -V * gp[a] : 0.0;
-            double Fg = (rp - ph.rho_f) * V * ph.g[a];  // gravity + buoyancy
-            pf[(PFD0 + a) * cap + p] = Fd;
-            pf[(PFH0 + a) * cap + p] = Fd + Fpr + pf[(PFA0 + a) * cap + p] + Fg;
+            for (int a = 0; a < 3; ++a) {
+                double Fd = coef * du[a];
+                double Fpr = ph.pressure ? -V * gp[a] : 0.0;
+                double Fg = (rp - ph.rho_f) * V * ph.g[a];  // gravity + buoyancy
+                pf[(PFD0 + a) * cap + p] = Fd;
+                pf[(PFH0 + a) * cap + p] = Fd + Fpr + pf[(PFA0 + a) * cap + p] + Fg;
+            }
         }
     }
 }
@@ -343,46 +447,58 @@ __global__ void k_force_drag(Geom g, double *__restrict__ pf, const double *__re
 // ---- S5: reaction force density (Eq. forces_pf) -----------------------------------
 // K6a: f_pf,am(c) = -sum_p W F_am
 template <typename FT>
-__global__ void k_reaction_am(Geom g, const int *__restrict__ cell_start, const double *__restrict__ pf,
-                              long long cap, FT *__restrict__ fam) {
-    const long long N = g.ncell;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-         c += (long long)gridDim.x * blockDim.x) {
-        double s[3] = {0, 0, 0};
-        gather27(g, c, cell_start, pf, cap, [&](int p, double W) {
-            s[0] += W * pf[PFA0 * cap + p];
-            s[1] += W * pf[(PFA0 + 1) * cap + p];
-            s[2] += W * pf[(PFA0 + 2) * cap + p];
-        });
-        fam[c] = (FT)(-s[0]);
-        fam[N + c] = (FT)(-s[1]);
-        fam[2 * N + c] = (FT)(-s[2]);
+__global__ void k_reaction_am(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        const Geom g = B.g;
+        const long long N = g.ncell, cap = B.cap;
+        const double *pf = B.pf[B.cur];
+        FT *fam = (FT *)B.fam;
+        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
+            double s[3] = {0, 0, 0};
+            gather27(g, c, B.cell_start, pf, cap, [&](int p, double W) {
+                s[0] += W * pf[PFA0 * cap + p];
+                s[1] += W * pf[(PFA0 + 1) * cap + p];
+                s[2] += W * pf[(PFA0 + 2) * cap + p];
+            });
+            fam[c] = (FT)(-s[0]);
+            fam[N + c] = (FT)(-s[1]);
+            fam[2 * N + c] = (FT)(-s[2]);
+        }
     }
 }
 
 // K6b: acc = (first ? 0 : acc) + f_pf,am - sum_p W F_d; after the last subcycle
 // the applied f_pf is the subcycle average.
 template <typename FT>
-__global__ void k_reaction_drag(Geom g, const int *__restrict__ cell_start, const double *__restrict__ pf,
-                                long long cap, const FT *__restrict__ fam, FT *__restrict__ acc,
-                                FT *__restrict__ fpf, int first, int last, double inv_nint) {
-    const long long N = g.ncell;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-         c += (long long)gridDim.x * blockDim.x) {
-        double s[3] = {0, 0, 0};
-        gather27(g, c, cell_start, pf, cap, [&](int p, double W) {
-            s[0] += W * pf[PFD0 * cap + p];
-            s[1] += W * pf[(PFD0 + 1) * cap + p];
-            s[2] += W * pf[(PFD0 + 2) * cap + p];
-        });
+__global__ void k_reaction_drag(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles,
+                                int first, int last) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        const Geom g = B.g;
+        const long long N = g.ncell, cap = B.cap;
+        const double *pf = B.pf[B.cur];
+        const FT *fam = (const FT *)B.fam;
+        FT *acc = (FT *)B.acc, *fpf = (FT *)B.fpf;
+        const double inv_nint = B.ph.dt_sub;
+        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
+            double s[3] = {0, 0, 0};
+            gather27(g, c, B.cell_start, pf, cap, [&](int p, double W) {
+                s[0] += W * pf[PFD0 * cap + p];
+                s[1] += W * pf[(PFD0 + 1) * cap + p];
+                s[2] += W * pf[(PFD0 + 2) * cap + p];
+            });
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double k = (double)fam[a * N + c] - s[a];
-            double v = first ? k : (double)acc[a * N + c] + k;
-            if (last)
-                fpf[a * N + c] = (FT)(v * inv_nint);
-            else
-                acc[a * N + c] = (FT)v;
+            for (int a = 0; a < 3; ++a) {
+                double k = (double)fam[a * N + c] - s[a];
+                double v = first ? k : (double)acc[a * N + c] + k;
+                if (last)
+                    fpf[a * N + c] = (FT)(v * inv_nint);
+                else
+                    acc[a * N + c] = (FT)v;
+            }
         }
     }
 }
@@ -394,7 +510,7 @@ static int grid_for(long long n, int block) {
     return (int)(g < 1 ? 1 : g);
 }
 
-// positions: x of particle i at px[i*stride], y at py[i*stride], z at pz[i*stride]
+// stateless sort op (device buffers): x of particle i at px[i*stride]...
 void launch_sort_count(const double *px, const double *py, const double *pz, long long stride, long long np,
                        const Geom &g, int *count, int *key, int *status, cudaStream_t s) {
     if (np <= 0) return;
@@ -410,56 +526,54 @@ void launch_sort_rank(const int *key, const int *ids, long long np, const int *c
     if (np <= 0) return;
     k_sort_rank<<<grid_for(np, 256), 256, 0, s>>>(key, ids, np, cell_start, tmp, perm);
 }
-void launch_sort_gather(const double *srcf, const double *xuw, const int *srci, long long cap, long long np,
-                        const int *perm, const int *key, const Geom &g, double *dstf, int *dsti, cudaStream_t s) {
-    if (np <= 0) return;
-    k_sort_gather<<<grid_for(np, 128), 128, 0, s>>>(srcf, xuw, srci, cap, np, perm, key, g, dstf, dsti);
+
+// box-table launchers: (grid, block) chosen by the caller
+void launch_bsort_count(const BoxDev *b, const Tile *t, int nt, int xsel, int grid, int block, cudaStream_t s) {
+    k_bsort_count<<<grid, block, 0, s>>>(b, t, nt, xsel);
 }
+void launch_bsort_scatter(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
+    k_bsort_scatter<<<grid, block, 0, s>>>(b, t, nt);
+}
+void launch_bsort_rank(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
+    k_bsort_rank<<<grid, block, 0, s>>>(b, t, nt);
+}
+void launch_bsort_gather(const BoxDev *b, const Tile *t, int nt, int xsel, int grid, int block, cudaStream_t s) {
+    k_bsort_gather<<<grid, block, 0, s>>>(b, t, nt, xsel);
+}
+void launch_bsort_flip(BoxDev *b, int nb, int mark_usub, cudaStream_t s) {
+    k_bsort_flip<<<(nb + 127) / 128, 128, 0, s>>>(b, nb, mark_usub);
+}
+void launch_end_step(BoxDev *b, int nb, cudaStream_t s) { k_end_step<<<(nb + 127) / 128, 128, 0, s>>>(b, nb); }
+void launch_flip_parity(BoxDev *b, int nb, cudaStream_t s) { k_flip_parity<<<(nb + 127) / 128, 128, 0, s>>>(b, nb); }
 
 template <typename FT>
-void launch_eps(const Geom &g, const int *cell_start, const double *pf, long long cap, double eps_min, void *eps,
-                unsigned long long *counters, int *status, cudaStream_t s) {
-    k_eps_gather<FT><<<grid_for(g.ncell, 128), 128, 0, s>>>(g, cell_start, pf, cap, eps_min, (FT *)eps, counters,
-                                                           status);
+void launch_eps(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
+    k_eps_gather<FT><<<grid, block, 0, s>>>(b, t, nt);
 }
 template <typename FT>
-void launch_force_am(const Geom &g, double *pf, const double *xuw, long long cap, long long np, const void *DuDt,
-                     const Phys &ph, int have_usub, cudaStream_t s) {
-    if (np <= 0) return;
-    k_force_am<FT><<<grid_for(np, 128), 128, 0, s>>>(g, pf, xuw, cap, np, (const FT *)DuDt, ph, have_usub);
+void launch_force_am(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
+    k_force_am<FT><<<grid, block, 0, s>>>(b, t, nt);
 }
 template <typename FT>
-void launch_force_drag(const Geom &g, double *pf, const double *xuw, long long cap, long long np, const void *rho,
-                       const void *j, const void *eps, const void *fam, const void *gradP, const Phys &ph,
-                       cudaStream_t s) {
-    if (np <= 0) return;
-    k_force_drag<FT><<<grid_for(np, 128), 128, 0, s>>>(g, pf, xuw, cap, np, (const FT *)rho, (const FT *)j,
-                                                      (const FT *)eps, (const FT *)fam, (const FT *)gradP, ph);
+void launch_force_drag(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
+    k_force_drag<FT><<<grid, block, 0, s>>>(b, t, nt);
 }
 template <typename FT>
-void launch_reaction_am(const Geom &g, const int *cell_start, const double *pf, long long cap, void *fam,
-                        cudaStream_t s) {
-    k_reaction_am<FT><<<grid_for(g.ncell, 128), 128, 0, s>>>(g, cell_start, pf, cap, (FT *)fam);
+void launch_reaction_am(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
+    k_reaction_am<FT><<<grid, block, 0, s>>>(b, t, nt);
 }
 template <typename FT>
-void launch_reaction_drag(const Geom &g, const int *cell_start, const double *pf, long long cap, const void *fam,
-                          void *acc, void *fpf, int first, int last, double inv_nint, cudaStream_t s) {
-    k_reaction_drag<FT><<<grid_for(g.ncell, 128), 128, 0, s>>>(g, cell_start, pf, cap, (const FT *)fam, (FT *)acc,
-                                                              (FT *)fpf, first, last, inv_nint);
+void launch_reaction_drag(const BoxDev *b, const Tile *t, int nt, int first, int last, int grid, int block,
+                          cudaStream_t s) {
+    k_reaction_drag<FT><<<grid, block, 0, s>>>(b, t, nt, first, last);
 }
 
-#define DPS_CPL_INST(FT)                                                                                         \
-    template void launch_eps<FT>(const Geom &, const int *, const double *, long long, double, void *,           \
-                                 unsigned long long *, int *, cudaStream_t);                                     \
-    template void launch_force_am<FT>(const Geom &, double *, const double *, long long, long long, const void *, \
-                                      const Phys &, int, cudaStream_t);                                          \
-    template void launch_force_drag<FT>(const Geom &, double *, const double *, long long, long long,            \
-                                        const void *, const void *, const void *, const void *, const void *,    \
-                                        const Phys &, cudaStream_t);                                             \
-    template void launch_reaction_am<FT>(const Geom &, const int *, const double *, long long, void *,           \
-                                         cudaStream_t);                                                          \
-    template void launch_reaction_drag<FT>(const Geom &, const int *, const double *, long long, const void *,   \
-                                           void *, void *, int, int, double, cudaStream_t);
+#define DPS_CPL_INST(FT)                                                                                  \
+    template void launch_eps<FT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);              \
+    template void launch_force_am<FT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);         \
+    template void launch_force_drag<FT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);       \
+    template void launch_reaction_am<FT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);      \
+    template void launch_reaction_drag<FT>(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
 DPS_CPL_INST(double)
 DPS_CPL_INST(float)
 

@@ -10,24 +10,11 @@
 // kernel flags a particle that moved more than skin/2 since the sort.
 // Positions/velocities are read from one buffer and written to the other
 // (ping-pong), so all pair forces see the state at the start of the substep.
-#include "dps_internal.cuh"
+#include "box.cuh"
 
 namespace dps {
 
 static constexpr double PI_D = 3.14159265358979323846;
-
-struct DemArgs {
-    const double *xin;    // 9 planes (x,u,w) of the current state, stride cap
-    double *xout;         // 9 planes of the next state
-    const double *pf;     // particle SoA (d, rho_p, F_hyd, xs)
-    const int *cell_start;
-    long long cap, np;
-    int R;                // search radius in cells
-    Geom g;
-    Phys ph;
-    int *status;
-    unsigned long long *counters;
-};
 
 __device__ __forceinline__ double min_image(double dx, int L, int per) {
     return per ? dx - L * rint(dx / L) : dx;
@@ -103,13 +90,28 @@ __device__ __forceinline__ void partner(const Phys &ph, const double n[3], doubl
     }
 }
 
-__global__ void __launch_bounds__(128) k_dem_substep(DemArgs A) {
-    const long long cap = A.cap;
-    const Geom &g = A.g;
-    const Phys &ph = A.ph;
+// src_tmp = 0: read x/u/w from the current set, write the ping-pong planes;
+// src_tmp = 1: the other way round
+__global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
+                                                     int ntiles, int src_tmp) {
+  DPS_FOR_TILES(tiles, ntiles, t) {
+    const Tile tl = tiles[t];
+    const BoxDev &Bx = boxes[tl.box];
+    struct {
+        const double *xin;
+        double *xout;
+        const double *pf;
+        const int *cell_start;
+        int R;
+        int *status;
+        unsigned long long *counters;
+    } A{src_tmp ? Bx.xtmp : Bx.pf[Bx.cur], src_tmp ? Bx.pf[Bx.cur] : Bx.xtmp, Bx.pf[Bx.cur], Bx.cell_start,
+        Bx.R, Bx.status, Bx.counters};
+    const long long cap = Bx.cap;
+    const Geom g = Bx.g;
+    const Phys &ph = Bx.ph;
     const double rng_extra = ph.lubrication ? fmax(ph.h_c, 0.0) : 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.np;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
         double xi[3], ui[3], wi[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -224,16 +226,12 @@ __global__ void __launch_bounds__(128) k_dem_substep(DemArgs A) {
         if (!(d2 < 1e30)) atomicOr(A.status, ST_NAN);
         if (nlim) atomicAdd(&A.counters[CNT_LUB_LIMITED], (unsigned long long)nlim);
     }
+  }
 }
 
-void launch_dem_substep(const double *xin, double *xout, const double *pf, const int *cell_start, long long cap,
-                        long long np, int R, const Geom &g, const Phys &ph, int *status,
-                        unsigned long long *counters, cudaStream_t s) {
-    if (np <= 0) return;
-    DemArgs A{xin, xout, pf, cell_start, cap, np, R, g, ph, status, counters};
-    long long grid = (np + 127) / 128;
-    if (grid > 152 * 32) grid = 152 * 32;
-    k_dem_substep<<<(int)grid, 128, 0, s>>>(A);
+void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int src_tmp, int grid, int block,
+                        cudaStream_t s) {
+    k_dem_substep<<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp);
 }
 
 }  // namespace dps

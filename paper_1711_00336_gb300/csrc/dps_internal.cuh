@@ -142,21 +142,24 @@ struct Phys {
 };
 
 // ---- PDF storage traits ---------------------------------------------------
+// FP64 stores f_q itself; the low-precision forms store the deviation
+// f_q - w_q rho_0 (shifted populations) and do all arithmetic on deviations,
+// so that FP32 / FP16 precision applies to the small non-equilibrium parts.
 template <typename ST> struct Store;
 template <> struct Store<double> {
     static constexpr bool shifted = false;
-    __device__ static inline double load(const double *p, double) { return *p; }
-    __device__ static inline void store(double *p, double v, double) { *p = v; }
+    __device__ static inline double load(const double *p) { return *p; }
+    __device__ static inline void store(double *p, double v) { *p = v; }
 };
 template <> struct Store<float> {
     static constexpr bool shifted = true;
-    __device__ static inline float load(const float *p, float w) { return *p + w; }
-    __device__ static inline void store(float *p, float v, float w) { *p = v - w; }
+    __device__ static inline float load(const float *p) { return *p; }
+    __device__ static inline void store(float *p, float v) { *p = v; }
 };
 template <> struct Store<__half> {
     static constexpr bool shifted = true;
-    __device__ static inline float load(const __half *p, float w) { return __half2float(*p) + w; }
-    __device__ static inline void store(__half *p, float v, float w) { *p = __float2half_rn(v - w); }
+    __device__ static inline float load(const __half *p) { return __half2float(*p); }
+    __device__ static inline void store(__half *p, float v) { *p = __float2half_rn(v); }
 };
 
 }  // namespace dps

@@ -23,9 +23,9 @@ __global__ void k_pdf_rest(ST *pdf, long long N) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             if constexpr (sizeof(ST) == 8)
-                Store<ST>::store(pdf + (long long)q * N + c, WQ(q), 0.0);
-            else
-                Store<ST>::store(pdf + (long long)q * N + c, (float)WQ(q), (float)WQ(q));
+                Store<ST>::store(pdf + (long long)q * N + c, WQ(q));
+            else  // deviation from the rest state is zero
+                Store<ST>::store(pdf + (long long)q * N + c, 0.0f);
         }
     }
 }
@@ -68,7 +68,7 @@ __global__ void k_fluid_export(const ST *__restrict__ pdf, const FT *__restrict_
             float ff[Q];
             load_pdfs<ST, float, PAR>(pdf, N, c, D, ff);
 #pragma unroll
-            for (int q = 0; q < Q; ++q) f[q] = ff[q];
+            for (int q = 0; q < Q; ++q) f[q] = (double)ff[q] + WQ(q);  // undo the shift in FP64
         }
         double rho, jx, jy, jz;
         moments(f, rho, jx, jy, jz);
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_fluid_sums(const ST *__restrict
             float ff[Q];
             load_pdfs<ST, float, PAR>(pdf, N, c, D, ff);
 #pragma unroll
-            for (int q = 0; q < Q; ++q) f[q] = ff[q];
+            for (int q = 0; q < Q; ++q) f[q] = (double)ff[q] + WQ(q);  // undo the shift in FP64
         }
         double rho, j[3];
         moments(f, rho, j[0], j[1], j[2]);

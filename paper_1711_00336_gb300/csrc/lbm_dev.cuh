@@ -48,9 +48,8 @@ __device__ __forceinline__ void load_pdfs(const ST *__restrict__ pdf, long long 
                                           const NbDelta &D, CT f[Q]) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const CT w = (CT)WQ(q);
         if (PAR == 0 || q == 0) {
-            f[q] = Store<ST>::load(pdf + (long long)q * N + c, w);
+            f[q] = Store<ST>::load(pdf + (long long)q * N + c);
         } else {
             // f_q(x) was written by the upstream cell x - c_q into plane opp(q);
             // across a wall it is the own cell's bounced value in plane q.
@@ -60,9 +59,9 @@ __device__ __forceinline__ void load_pdfs(const ST *__restrict__ pdf, long long 
                 dm = (dx == INV || dy == INV || dz == INV) ? INV : dx + dy + dz;
             }
             if (dm != INV)
-                f[q] = Store<ST>::load(pdf + (long long)OPP(q) * N + c + dm, w);
+                f[q] = Store<ST>::load(pdf + (long long)OPP(q) * N + c + dm);
             else
-                f[q] = Store<ST>::load(pdf + (long long)q * N + c, w);
+                f[q] = Store<ST>::load(pdf + (long long)q * N + c);
         }
     }
 }
@@ -72,17 +71,16 @@ __device__ __forceinline__ void store_pdfs(ST *__restrict__ pdf, long long N, lo
                                            const NbDelta &D, const CT f[Q]) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const CT w = (CT)WQ(q);
         if (q == 0) {
-            Store<ST>::store(pdf + c, f[0], w);
+            Store<ST>::store(pdf + c, f[0]);
         } else if (PAR == 0) {
-            Store<ST>::store(pdf + (long long)OPP(q) * N + c, f[q], (CT)WQ(OPP(q)));
+            Store<ST>::store(pdf + (long long)OPP(q) * N + c, f[q]);
         } else {
             long long dp = nb_delta(D, q);
             if (dp != INV)
-                Store<ST>::store(pdf + (long long)q * N + c + dp, f[q], w);
+                Store<ST>::store(pdf + (long long)q * N + c + dp, f[q]);
             else  // bounce back: returns to this cell with velocity -c_q
-                Store<ST>::store(pdf + (long long)OPP(q) * N + c, f[q], (CT)WQ(OPP(q)));
+                Store<ST>::store(pdf + (long long)OPP(q) * N + c, f[q]);
         }
     }
 }

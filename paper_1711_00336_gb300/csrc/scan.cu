@@ -3,7 +3,7 @@
 // writes tile totals, the totals are scanned (recursively), a second pass
 // scans each tile and adds its offset.  Integer sums are exact, so the result
 // does not depend on the launch shape.
-#include "dps_internal.cuh"
+#include "box.cuh"
 
 namespace dps {
 
@@ -120,5 +120,89 @@ void exclusive_scan(const int *in, long long n, int *out, int *scratch, cudaStre
     exclusive_scan(sums, tiles, sums_scanned, sums_scanned + tiles + 1, s);
     k_tile_scan<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums_scanned, out, 1);
 }
+
+// ---- batched scan over the box table ----------------------------------------------
+// Scan tiles are SCAN_TILE cells of one box; Tile::first is the tile's index
+// inside its box.  Pass 1 writes each tile's count total, pass 2 scans the
+// totals of every box (one block per box), pass 3 scans inside the tiles,
+// writes cell_start (and its final entry, the particle count) and clears the
+// fill counters used by the scatter.
+__global__ void __launch_bounds__(SCAN_THREADS) k_bscan_sums(const BoxDev *__restrict__ boxes,
+                                                              const Tile *__restrict__ tiles, int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        int s = 0;
+        for (long long i = tl.begin + threadIdx.x; i < tl.end; i += SCAN_THREADS) s += B.count[i];
+        __shared__ int red[SCAN_THREADS / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int v = red[threadIdx.x];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (threadIdx.x == 0) B.scan_part[tl.first] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// one block per box: exclusive scan of its tile totals, in place
+__global__ void __launch_bounds__(SCAN_THREADS) k_bscan_parts(const BoxDev *__restrict__ boxes, int nboxes) {
+    for (int b = blockIdx.x; b < nboxes; b += gridDim.x) {
+        const BoxDev &B = boxes[b];
+        const long long nt = (B.g.ncell + SCAN_TILE - 1) / SCAN_TILE;
+        int carry = 0;
+        for (long long base = 0; base < nt; base += SCAN_THREADS) {
+            long long i = base + threadIdx.x;
+            int v = i < nt ? B.scan_part[i] : 0;
+            int total;
+            int ex = block_excl_scan(v, total);
+            if (i < nt) B.scan_part[i] = carry + ex;
+            carry += total;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_bscan_tiles(const BoxDev *__restrict__ boxes,
+                                                               const Tile *__restrict__ tiles, int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        const long long n = B.g.ncell;
+        const long long base = tl.begin + (long long)threadIdx.x * SCAN_ITEMS;
+        int v[SCAN_ITEMS];
+        int s = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            long long i = base + k;
+            v[k] = i < tl.end ? B.count[i] : 0;
+            s += v[k];
+        }
+        int total;
+        int ex = block_excl_scan(s, total);
+        int off = B.scan_part[tl.first] + ex;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            long long i = base + k;
+            if (i < tl.end) {
+                B.cell_start[i] = off;
+                B.fill[i] = 0;
+            }
+            off += v[k];
+        }
+        if (base <= n - 1 && n - 1 < base + SCAN_ITEMS && n - 1 < tl.end) B.cell_start[n] = off;
+    }
+}
+
+void launch_bscan(const BoxDev *boxes, int nboxes, const Tile *scan_tiles, int ntiles, cudaStream_t s) {
+    int grid = ntiles < 152 * 2 ? ntiles : 152 * 2;
+    k_bscan_sums<<<grid, SCAN_THREADS, 0, s>>>(boxes, scan_tiles, ntiles);
+    k_bscan_parts<<<nboxes, SCAN_THREADS, 0, s>>>(boxes, nboxes);
+    k_bscan_tiles<<<grid, SCAN_THREADS, 0, s>>>(boxes, scan_tiles, ntiles);
+}
+int scan_tile_cells() { return SCAN_TILE; }
 
 }  // namespace dps

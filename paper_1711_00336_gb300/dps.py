@@ -339,3 +339,293 @@ def op_cell_sort(n, periodic, x_dev, ids_dev, stream=None):
     if rc != DPS_OK:
         raise DPSError(rc, "dps_op_cell_sort failed")
     return cs, order[:npart]
+
+
+# ---------------------------------------------------------------------------
+# batches of boxes
+# ---------------------------------------------------------------------------
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", _ALLOC_FN),
+                ("free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+def _declare_batch(L):
+    if getattr(L, "_batch_declared", False):
+        return
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, _DP
+    ip3 = ctypes.POINTER(ctypes.c_int)
+    L.dps_batch_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(vp)]
+    L.dps_batch_destroy.argtypes = [vp]
+    L.dps_batch_add_box.argtypes = [vp, ip3, ip3, ctypes.c_double, ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int)]
+    L.dps_batch_remove_box.argtypes = [vp, ctypes.c_int]
+    L.dps_batch_add_particles.argtypes = [vp, ctypes.c_int, i64, dp, dp, dp, dp, dp]
+    L.dps_batch_set_closure.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Closure)]
+    L.dps_batch_step.argtypes = [vp, i64]
+    L.dps_batch_step_async.argtypes = [vp, i64]
+    L.dps_batch_check.argtypes = [vp]
+    L.dps_batch_read_particles.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp, i64]
+    L.dps_batch_read_fields.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, dp, i64]
+    L.dps_batch_stats.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Stats)]
+    L.dps_batch_particle_mean.argtypes = [vp, ctypes.c_int, dp]
+    L.dps_batch_num_boxes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.dps_batch_set_tuning.argtypes = [vp, ip3]
+    L.dps_batch_get_tuning.argtypes = [vp, ip3]
+    L.dps_batch_autotune.argtypes = [vp, ctypes.c_int, dp]
+    L.dps_batch_set_timing.argtypes = [vp, ctypes.c_int]
+    L.dps_batch_collect_timing.argtypes = [vp]
+    L.dps_batch_get_timing.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.dps_batch_launches_per_step.argtypes = [vp, ctypes.POINTER(i64)]
+    L.dps_box_bytes.argtypes = [ctypes.c_int, ip3, i64, ctypes.POINTER(ctypes.c_size_t)]
+    L.dps_serve_create.argtypes = [ctypes.POINTER(ServeDesc), ctypes.POINTER(vp)]
+    L.dps_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(i64)]
+    L.dps_serve_poll.argtypes = [vp, i64, ctypes.POINTER(Result)]
+    L.dps_serve_cancel.argtypes = [vp, i64]
+    L.dps_serve_wait_idle.argtypes = [vp, ctypes.c_double]
+    L.dps_serve_stats_get.argtypes = [vp, ctypes.POINTER(ServeStats)]
+    L.dps_serve_destroy.argtypes = [vp]
+    L._batch_declared = True
+
+
+def _i3(v):
+    return (ctypes.c_int * 3)(*[int(x) for x in v])
+
+
+class Batch:
+    """Many independent boxes advanced together: one launch per phase."""
+
+    def __init__(self, precision="f32", stream=None):
+        import torch
+        L = lib()
+        _declare_batch(L)
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA is not available: the dps library has no CPU path")
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        d = BatchDesc()
+        d.precision = PRECISION[precision]
+        d.stream = self.stream.cuda_stream
+        h = ctypes.c_void_p()
+        rc = L.dps_batch_create(ctypes.byref(d), ctypes.byref(h))
+        if rc != DPS_OK:
+            raise DPSError(rc, L.dps_last_error(None).decode())
+        self.h = h
+        self.boxes = {}
+
+    def _ck(self, rc):
+        if rc != DPS_OK:
+            raise DPSError(rc, "batch call failed")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dps_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_box(self, n, periodic, tau, max_particles, rho_f=1.0):
+        b = ctypes.c_int()
+        self._ck(lib().dps_batch_add_box(self.h, _i3(n), _i3(periodic), float(tau), float(rho_f),
+                                         int(max_particles), ctypes.byref(b)))
+        self.boxes[b.value] = dict(n=tuple(n), np=0)
+        return b.value
+
+    def remove_box(self, box):
+        self._ck(lib().dps_batch_remove_box(self.h, int(box)))
+        self.boxes.pop(box, None)
+
+    def add_particles(self, box, x, d, rho_p, u=None, w=None):
+        x = _vec(x, -1)
+        m = len(x)
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(d, np.float64), (m,)))
+        rho_p = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_p, np.float64), (m,)))
+        self._ck(lib().dps_batch_add_particles(self.h, int(box), m, _p(x), _p(_vec(u, m)), _p(_vec(w, m)), _p(d),
+                                               _p(rho_p)))
+        self.boxes[box]["np"] += m
+
+    def set_closure(self, box, c=None, **kw):
+        c = c if c is not None else closure(**kw)
+        self._ck(lib().dps_batch_set_closure(self.h, int(box), ctypes.byref(c)))
+
+    def step(self, n=1):
+        self._ck(lib().dps_batch_step(self.h, int(n)))
+
+    def step_async(self, n=1):
+        self._ck(lib().dps_batch_step_async(self.h, int(n)))
+
+    def check(self):
+        self._ck(lib().dps_batch_check(self.h))
+
+    def read_particles(self, box):
+        m = self.boxes[box]["np"]
+        out = {k: np.zeros((max(m, 1), 3)) for k in ("x", "u", "w", "F")}
+        self._ck(lib().dps_batch_read_particles(self.h, int(box), _p(out["x"]), _p(out["u"]), _p(out["w"]),
+                                                _p(out["F"]), max(m, 1)))
+        return {k: v[:m] for k, v in out.items()}
+
+    def read_fields(self, box, names=("ubar",)):
+        n = self.boxes[box]["n"]
+        nc = n[0] * n[1] * n[2]
+        mask, total = 0, 0
+        for nm, bit, k in FIELDS:
+            if nm in names:
+                mask |= bit
+                total += k
+        out = np.zeros(total * nc)
+        self._ck(lib().dps_batch_read_fields(self.h, int(box), mask, _p(out), out.size))
+        res, off = {}, 0
+        for nm, bit, k in FIELDS:
+            if mask & bit:
+                a = out[off:off + k * nc]
+                res[nm] = a.reshape(k, nc) if k == 3 else a.copy()
+                off += k * nc
+        return res
+
+    def particle_mean(self, box):
+        u = np.zeros(3)
+        self._ck(lib().dps_batch_particle_mean(self.h, int(box), _p(u)))
+        return u
+
+    def tuning(self):
+        c = (ctypes.c_int * 4)()
+        self._ck(lib().dps_batch_get_tuning(self.h, c))
+        return list(c)
+
+    def set_tuning(self, cfg):
+        self._ck(lib().dps_batch_set_tuning(self.h, (ctypes.c_int * 4)(*cfg)))
+
+    def autotune(self, steps=5):
+        ms = np.zeros(1)
+        self._ck(lib().dps_batch_autotune(self.h, int(steps), _p(ms)))
+        return float(ms[0])
+
+    def set_timing(self, on=True):
+        self._ck(lib().dps_batch_set_timing(self.h, int(bool(on))))
+
+    def collect_timing(self):
+        self._ck(lib().dps_batch_collect_timing(self.h))
+
+    def get_timing(self, reset=True):
+        ms = (ctypes.c_double * 9)()
+        nl = (ctypes.c_int64 * 9)()
+        self._ck(lib().dps_batch_get_timing(self.h, ctypes.byref(ms), ctypes.byref(nl), int(bool(reset))))
+        return {k: {"ms": ms[i], "launches": nl[i]} for i, k in enumerate(Domain.PHASES)}
+
+    def launches_per_step(self):
+        n = ctypes.c_int64()
+        self._ck(lib().dps_batch_launches_per_step(self.h, ctypes.byref(n)))
+        return n.value
+
+
+def box_bytes(precision, n, max_particles):
+    L = lib()
+    _declare_batch(L)
+    b = ctypes.c_size_t()
+    rc = L.dps_box_bytes(PRECISION[precision], _i3(n), int(max_particles), ctypes.byref(b))
+    if rc != DPS_OK:
+        raise DPSError(rc, "dps_box_bytes")
+    return b.value
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+class ServeDesc(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("max_boxes", ctypes.c_int),
+                ("hbm_reserve_bytes", ctypes.c_size_t), ("chunk_steps", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("periodic", ctypes.c_int * 3), ("tau", ctypes.c_double),
+                ("rho_f", ctypes.c_double), ("np", ctypes.c_int64), ("x3", _DP), ("d", _DP), ("rho_p", _DP),
+                ("closure", Closure), ("max_steps", ctypes.c_int64), ("window", ctypes.c_int64),
+                ("rel_tol", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("capped", ctypes.c_int), ("status", ctypes.c_int),
+                ("steps", ctypes.c_int64), ("up_mean", ctypes.c_double * 3), ("u_pS", ctypes.c_double * 3),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("running", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("peak_boxes", ctypes.c_int), ("cell_updates", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("wall_s", ctypes.c_double)]
+
+
+REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
+
+
+class Server:
+    """Continuous-batching server (a native worker thread owns the batch)."""
+
+    def __init__(self, precision="f32", max_boxes=64, hbm_reserve_bytes=8 << 30, chunk_steps=50, device=0):
+        L = lib()
+        _declare_batch(L)
+        d = ServeDesc()
+        d.precision = PRECISION[precision]
+        d.device = int(device)
+        d.max_boxes = int(max_boxes)
+        d.hbm_reserve_bytes = int(hbm_reserve_bytes)
+        d.chunk_steps = int(chunk_steps)
+        h = ctypes.c_void_p()
+        rc = L.dps_serve_create(ctypes.byref(d), ctypes.byref(h))
+        if rc != DPS_OK:
+            raise DPSError(rc, "dps_serve_create")
+        self.h = h
+
+    def submit(self, n, periodic, tau, x, d, rho_p, closure_obj, max_steps=20000, window=500, rel_tol=1e-3,
+               rho_f=1.0):
+        x = _vec(x, -1)
+        m = len(x)
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(d, np.float64), (m,)))
+        rho_p = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_p, np.float64), (m,)))
+        r = Request()
+        r.n[:] = [int(v) for v in n]
+        r.periodic[:] = [int(bool(v)) for v in periodic]
+        r.tau, r.rho_f, r.np = float(tau), float(rho_f), m
+        r.x3, r.d, r.rho_p = _p(x), _p(d), _p(rho_p)
+        r.closure = closure_obj
+        r.max_steps, r.window, r.rel_tol = int(max_steps), int(window), float(rel_tol)
+        i = ctypes.c_int64()
+        rc = lib().dps_serve_submit(self.h, ctypes.byref(r), ctypes.byref(i))
+        if rc != DPS_OK:
+            raise DPSError(rc, "dps_serve_submit")
+        return i.value
+
+    def poll(self, rid):
+        r = Result()
+        rc = lib().dps_serve_poll(self.h, int(rid), ctypes.byref(r))
+        if rc != DPS_OK:
+            raise DPSError(rc, "dps_serve_poll")
+        return dict(state=REQ_STATES[r.state], capped=r.capped, status=r.status, steps=r.steps,
+                    up_mean=np.array(list(r.up_mean)), u_pS=np.array(list(r.u_pS)), t_submit=r.t_submit,
+                    t_start=r.t_start, t_end=r.t_end)
+
+    def cancel(self, rid):
+        lib().dps_serve_cancel(self.h, int(rid))
+
+    def wait_idle(self, timeout=-1.0):
+        rc = lib().dps_serve_wait_idle(self.h, float(timeout))
+        if rc != DPS_OK:
+            raise DPSError(rc, "wait_idle")
+
+    def stats(self):
+        s = ServeStats()
+        lib().dps_serve_stats_get(self.h, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in ServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dps_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,191 @@
+"""Batching and serving forms: many uneven boxes advanced by one launch per
+phase must give every box exactly the result it gets alone (its kernels
+touch only its own data, in the same order), for any launch shape; the
+serving loop must reproduce a request's result whether it ran alone or among
+others, and admit / retire boxes as memory and convergence dictate."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1711_00336_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _dps():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_00336_gb300 import build, dps
+    build.build()
+    return dps
+
+
+KW = dict(e_n=0.88, mu_c=0.25, T_c=0.5, h_min=1e-5, C_am=0.5, n_int=2, n_dem=5, lub_limiter=1, lub_cap=0.25,
+          eps_min=0.05, skin=0.5, fb_mode=1)
+
+
+def _boxes():
+    """three uneven periodic boxes with different d and volume fraction"""
+    out = []
+    for L, eps, d, seed in ((14, 0.1, 0.8, 1), (19, 0.25, 1.2, 2), (11, 0.05, 1.5, 3)):
+        wl = workloads.settling_box(L=L, eps=eps, d=d, seed=seed)
+        out.append(wl)
+    return out
+
+
+def _closure(dps, wl):
+    return dps.closure(g=wl["g"], h_c=wl["d"][0], **KW)
+
+
+def _alone(dps, wl, prec, steps):
+    dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], prec, max_particles=len(wl["x"]))
+    dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+    dom.set_closure(_closure(dps, wl))
+    dom.step(steps)
+    r = dom.read_particles()
+    f = dom.read_fields(("ubar",))["ubar"]
+    dom.close()
+    return r, f
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batch_equals_each_box_alone(prec):
+    dps = _dps()
+    wls = _boxes()
+    steps = 6
+    B = dps.Batch(prec)
+    ids = []
+    for wl in wls:
+        b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
+        B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
+        B.set_closure(b, _closure(dps, wl))
+        ids.append(b)
+    B.step(steps)
+    for b, wl in zip(ids, wls):
+        r, f = _alone(dps, wl, prec, steps)
+        got = B.read_particles(b)
+        assert np.array_equal(got["x"], r["x"]) and np.array_equal(got["u"], r["u"])
+        assert np.array_equal(B.read_fields(b, ("ubar",))["ubar"], f)
+    B.close()
+
+
+def test_launch_shape_does_not_change_results():
+    dps = _dps()
+    wl = _boxes()[1]
+    res = []
+    for cfg in ([128, 1024, 128, 256], [64, 256, 64, 64], [256, 4096, 256, 512]):
+        B = dps.Batch("f32")
+        b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
+        B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
+        B.set_closure(b, _closure(dps, wl))
+        B.set_tuning(cfg)
+        B.step(4)
+        res.append(B.read_particles(b)["u"])
+        B.close()
+    assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
+
+
+def test_autotune_keeps_a_valid_shape_and_removal_leaves_others_untouched():
+    dps = _dps()
+    wls = _boxes()
+    B = dps.Batch("f32")
+    ids = []
+    for wl in wls:
+        b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
+        B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
+        B.set_closure(b, _closure(dps, wl))
+        ids.append(b)
+    ms = B.autotune(steps=2)
+    assert ms > 0
+    cfg = B.tuning()
+    assert cfg[0] % 32 == 0 and cfg[2] % 32 == 0
+    steps_done = (1 + 2) * (6 + 4)  # capture step + timed steps of each of the 10 candidates
+    B.remove_box(ids[1])
+    B.step(3)
+    r, _ = _alone(dps, wls[0], "f32", steps_done + 3)
+    assert np.array_equal(B.read_particles(ids[0])["x"], r["x"])
+    B.close()
+
+
+def test_batch_fp64_box_matches_oracle():
+    dps = _dps()
+    wl = workloads.settling_box(L=10, eps=0.15, d=1.0, seed=9)
+    B = dps.Batch("f64")
+    b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
+    B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
+    c = _closure(dps, wl)
+    B.set_closure(b, c)
+    B.step(3)
+    got = B.read_particles(b)
+    V = np.pi / 6 * wl["d"] ** 3
+    fb = -((wl["rho_p"] - 1) * V).sum() * np.asarray(wl["g"]) / (np.prod(wl["n"]) - V.sum())
+    kw = {k: v for k, v in KW.items() if k not in ("skin", "fb_mode")}
+    P = O.make_params(wl["n"], wl["periodic"], wl["tau"], g=wl["g"], f_b=fb, h_c=wl["d"][0], **kw)
+    ref = O.Domain(P, x=wl["x"], d=wl["d"], rho_p=wl["rho_p"])
+    ref.step(3)
+    r = ref.particles()
+    err = np.abs(got["u"] - r["u"]).max() / max(np.abs(r["u"]).max(), 1e-3)
+    assert err < 1e-12
+    B.close()
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+def _request(dps, L, eps, seed, d=1.0):
+    wl = workloads.settling_box(L=L, eps=eps, d=d, seed=seed)
+    c = dps.closure(g=wl["g"], h_c=d, **KW)
+    return wl, c
+
+
+def test_serving_result_is_the_same_alone_and_in_the_mix():
+    dps = _dps()
+    reqs = [_request(dps, L, e, s) for L, e, s in ((16, 0.1, 1), (12, 0.2, 2), (20, 0.05, 3))]
+    kw = dict(max_steps=600, window=200, rel_tol=1e-9)  # run to the cap: deterministic length
+    S = dps.Server("f32", max_boxes=8, hbm_reserve_bytes=1 << 30, chunk_steps=50)
+    wl, c = reqs[0]
+    rid = S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"], c, **kw)
+    S.wait_idle(600)
+    alone = S.poll(rid)
+    S.close()
+    assert alone["state"] == "done" and alone["steps"] == 600
+    S = dps.Server("f32", max_boxes=8, hbm_reserve_bytes=1 << 30, chunk_steps=50)
+    ids = []
+    for k, (wl, c) in enumerate(reqs[::-1]):  # request 0 arrives last, joins a running batch
+        ids.append(S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"], c, **kw))
+        time.sleep(0.05)
+    S.wait_idle(600)
+    mixed = S.poll(ids[-1])
+    st = S.stats()
+    S.close()
+    assert mixed["state"] == "done"
+    assert np.array_equal(mixed["up_mean"], alone["up_mean"])
+    assert np.array_equal(mixed["u_pS"], alone["u_pS"])
+    assert st["completed"] == 3 and st["cell_updates"] > 0
+
+
+def test_serving_convergence_cancel_and_admission():
+    dps = _dps()
+    S = dps.Server("f32", max_boxes=2, hbm_reserve_bytes=1 << 30, chunk_steps=50)
+    wl, c = _request(dps, 12, 0.1, 4)
+    a = S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"], c, max_steps=20000,
+                 window=500, rel_tol=1e-3)
+    b = S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"], c, max_steps=20000,
+                 window=500, rel_tol=1e-3)
+    cc = S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"], c, max_steps=20000,
+                  window=500, rel_tol=1e-3)
+    S.cancel(cc)  # third request waits for a slot and is cancelled there
+    # a box that can never fit in HBM fails at admission without allocating
+    big = S.submit((1200, 1200, 1200), (1, 1, 1), 0.65, wl["x"][:1], wl["d"][:1], wl["rho_p"][:1], c,
+                   max_steps=100, window=50, rel_tol=1e-3)
+    S.wait_idle(900)
+    ra, rb, rc, rbig = S.poll(a), S.poll(b), S.poll(cc), S.poll(big)
+    S.close()
+    assert ra["state"] == "done" and rb["state"] == "done"
+    assert ra["steps"] % 500 == 0
+    assert np.array_equal(ra["up_mean"], rb["up_mean"])
+    assert rc["state"] == "cancelled"
+    assert rbig["state"] == "failed"

