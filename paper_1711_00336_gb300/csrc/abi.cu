@@ -19,9 +19,9 @@
 namespace dps {
 // launchers (lbm.cu, coupling.cu, dem.cu, scan.cu, io.cu)
 template <typename ST, typename FT, typename CT>
-void launch_collide_stream(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+void launch_collide_stream(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 template <typename ST, typename FT, typename CT>
-void launch_moments(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+void launch_moments(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 template <typename FT, typename CT>
 void launch_fields(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename ST>
@@ -38,7 +38,6 @@ void launch_bsort_rank(const BoxDev *, const Tile *, int, int, int, cudaStream_t
 void launch_bsort_gather(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 void launch_bsort_flip(BoxDev *, int, int, cudaStream_t);
 void launch_end_step(BoxDev *, int, cudaStream_t);
-void launch_flip_parity(BoxDev *, int, cudaStream_t);
 void launch_bscan(const BoxDev *, int, const Tile *, int, cudaStream_t);
 int scan_tile_cells();
 template <typename FT>
@@ -51,7 +50,8 @@ template <typename FT>
 void launch_reaction_am(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
 void launch_reaction_drag(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
-void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
+void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
+void launch_build_nlist(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 long long scan_scratch_words(long long);
 void exclusive_scan(const int *, long long, int *, int *, cudaStream_t);
 template <typename ST>
@@ -86,7 +86,7 @@ struct BoxHost {
     std::vector<void *> allocs;
     dps_closure cl{};
     bool have_closure = false;
-    double sumV = 0, sumWb = 0, dmax = 0;
+    double sumV = 0, sumWb = 0, dmax = 0, dmin = 1e300;
     long long max_particles = 0;
     double tau = 0.65, rho_f = 1.0;
     bool prepared = false;
@@ -113,6 +113,7 @@ struct Batch {
     void *ctx = nullptr;
     std::string err;
     std::vector<BoxHost *> boxes;
+    std::vector<BoxHost *> dev_order;  // box of each device-table entry (null: removed since)
     int table_cap = 0;
     BoxDev *d_table = nullptr;
     std::vector<void *> allocs;  // batch-level buffers (table, tiles)
@@ -123,7 +124,8 @@ struct Batch {
     bool tuned = false;
     int n_int = 0, n_dem = 0;
     bool layout_dirty = true;     // table/tiles must be rebuilt and uploaded
-    cudaGraphExec_t gexec = nullptr;
+    int parity = 0;               // AA parity of every box of the batch
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // step graphs by parity
     bool use_graphs = true;
     long long launches_step = 0, launch_count = 0;
     // tracing
@@ -180,10 +182,11 @@ static void box_free(Batch *B, BoxHost *h) {
 }
 
 static void invalidate_graph(Batch *B) {
-    if (B->gexec) {
-        cudaGraphExecDestroy(B->gexec);
-        B->gexec = nullptr;
-    }
+    for (int k = 0; k < 2; ++k)
+        if (B->gexec[k]) {
+            cudaGraphExecDestroy(B->gexec[k]);
+            B->gexec[k] = nullptr;
+        }
 }
 
 // ---- phase timing -----------------------------------------------------------
@@ -216,6 +219,9 @@ static void compute_phys(BoxHost *h) {
     Phys &p = h->d.ph;
     p.tau = h->tau;
     p.omega = 1.0 / h->tau;
+    p.kf = 1.0 - 0.5 / h->tau;
+    p.omega_f = (float)p.omega;
+    p.kf_f = (float)p.kf;
     p.rho_f = h->rho_f;
     p.mu = h->rho_f * (h->tau - 0.5) / 3.0;  // Eq. visc_tau
     const double cells = (double)h->d.g.ncell;
@@ -230,11 +236,13 @@ static void compute_phys(BoxHost *h) {
         else
             p.fb[a] = c.fb[a];
     }
+    for (int a = 0; a < 3; ++a) p.fb_f[a] = (float)p.fb[a];
     if (!h->have_closure) {
         p.eps_min = 0.05;
         p.n_int = p.n_dem = 1;
         p.dt_sub = p.dt_dem = 1.0;
         h->d.R = 1;
+        p.skin = 0.0;
         p.skin_half2 = 0.25;
         return;
     }
@@ -256,27 +264,39 @@ static void compute_phys(BoxHost *h) {
     p.lubrication = c.lubrication;
     p.contact = c.contact;
     p.lub_limiter = c.lub_limiter;
+    // Verlet list: partners within (d_i+d_j)/2 + h_c + skin; linked cells of
+    // +-R cells cover that range; particles may move skin/2 between sorts
     const double cutoff = h->dmax + (c.lubrication ? std::fmax(c.h_c, 0.0) : 0.0);
-    h->d.R = (int)std::floor(cutoff + c.skin) + 1;
-    const double slack = h->d.R - cutoff;
-    p.skin_half2 = 0.25 * slack * slack;
+    p.skin = c.skin;
+    h->d.R = (int)std::floor(cutoff + c.skin + 1e-3) + 1;
+    p.skin_half2 = 0.25 * c.skin * c.skin;
 }
 
 // ---- table and tiles ------------------------------------------------------------
 // copy the device-side step state of every box into the host entries
 static int pull_state(Batch *B) {
-    if (B->boxes.empty() || !B->d_table) return DPS_OK;
+    if (B->dev_order.empty() || !B->d_table) return DPS_OK;
     CKB(B, cudaStreamSynchronize(B->stream));
-    std::vector<BoxDev> t(B->boxes.size());
+    std::vector<BoxDev> t(B->dev_order.size());
     CKB(B, cudaMemcpy(t.data(), B->d_table, sizeof(BoxDev) * t.size(), cudaMemcpyDeviceToHost));
-    for (size_t k = 0; k < B->boxes.size(); ++k) {
-        BoxDev &d = B->boxes[k]->d;
+    for (size_t k = 0; k < B->dev_order.size(); ++k) {
+        BoxHost *h = B->dev_order[k];
+        if (!h) continue;
+        BoxDev &d = h->d;
         d.parity = t[k].parity;
         d.cur = t[k].cur;
         d.have_uprev = t[k].have_uprev;
         d.have_usub = t[k].have_usub;
     }
     return DPS_OK;
+}
+
+// a box leaves the batch: its device-table entry no longer maps to it
+static void forget_box(Batch *B, BoxHost *h) {
+    for (auto &p : B->dev_order)
+        if (p == h) p = nullptr;
+    B->boxes.erase(std::remove(B->boxes.begin(), B->boxes.end(), h), B->boxes.end());
+    B->layout_dirty = true;
 }
 
 static int ensure_buf(Batch *B, Tile **p, size_t *cap, size_t need) {
@@ -340,6 +360,7 @@ static int push_layout(Batch *B) {
     B->n_cell = (int)cell.size();
     B->n_part = (int)part.size();
     B->n_scan = (int)scan.size();
+    B->dev_order = B->boxes;
     B->layout_dirty = false;
     invalidate_graph(B);
     return DPS_OK;
@@ -373,7 +394,8 @@ static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub) {
         launch_bsort_gather(T, B->d_part, B->n_part, xsel, grid_of(B->n_part), u.part_block, B->stream);
     }
     launch_bsort_flip(B->d_table, nb, mark_usub, B->stream);
-    tend(B, PH_SORT, 3 + 4 * pl + 1);
+    if (pl) launch_build_nlist(T, B->d_part, B->n_part, grid_of(B->n_part), u.part_block, B->stream);
+    tend(B, PH_SORT, 3 + 5 * pl + 1);
     tbegin(B);
     if (B->fel == 8)
         launch_eps<double>(T, B->d_cell, B->n_cell, grid_of(B->n_cell), u.cell_block, B->stream);
@@ -393,9 +415,10 @@ static void enqueue_step(Batch *B) {
     B->launch_count = 0;
     // Du_f/Dt and grad P, once per step
     tbegin(B);
-    PREC_CALL(B, (launch_moments<double, double, double>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)),
-              (launch_moments<float, float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)),
-              (launch_moments<__half, float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)));
+    const int par = B->parity;
+    PREC_CALL(B, (launch_moments<double, double, double>(T, B->d_cell, B->n_cell, par, gc, u.cell_block, s)),
+              (launch_moments<float, float, float>(T, B->d_cell, B->n_cell, par, gc, u.cell_block, s)),
+              (launch_moments<__half, float, float>(T, B->d_cell, B->n_cell, par, gc, u.cell_block, s)));
     if (f64)
         launch_fields<double, double>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
     else
@@ -426,14 +449,15 @@ static void enqueue_step(Batch *B) {
         tend(B, PH_RDRAG, 1);
         tbegin(B);
         if (pl)
-            for (int sd = 0; sd < B->n_dem; ++sd) launch_dem_substep(T, B->d_part, B->n_part, sd & 1, gp, u.part_block, s);
+            for (int sd = 0; sd < B->n_dem; ++sd)
+                launch_dem_substep(T, B->d_part, B->n_part, sd & 1, B->prec != DPS_F64, gp, u.part_block, s);
         tend(B, PH_DEM, pl * B->n_dem);
         enqueue_sort_eps(B, B->n_dem & 1, 1);
     }
     tbegin(B);
-    PREC_CALL(B, (launch_collide_stream<double, double, double>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)),
-              (launch_collide_stream<float, float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)),
-              (launch_collide_stream<__half, float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s)));
+    PREC_CALL(B, (launch_collide_stream<double, double, double>(T, B->d_cell, B->n_cell, par, gc, u.cell_block, s)),
+              (launch_collide_stream<float, float, float>(T, B->d_cell, B->n_cell, par, gc, u.cell_block, s)),
+              (launch_collide_stream<__half, float, float>(T, B->d_cell, B->n_cell, par, gc, u.cell_block, s)));
     launch_end_step(B->d_table, (int)B->boxes.size(), s);
     tend(B, PH_COLLIDE, 2);
     B->launches_step = B->launch_count;
@@ -457,7 +481,37 @@ static int check_boxes(Batch *B) {
         if (bad & ST_SKIN) m += "a particle moved more than skin/2 within one subcycle (increase skin or n_int); ";
         if (bad & ST_EPS_NEG) m += "eps_f < 0 before the floor; ";
         if (bad & ST_BAD_CELL) m += "a particle left the box through a wall; ";
+        if (bad & ST_NLIST) m += "a neighbour list overflowed; ";
         FAILB(B, DPS_ERR_UNSTABLE, "unstable: %s", m.c_str());
+    }
+    return DPS_OK;
+}
+
+// Verlet-list capacity: at most as many spheres of the smallest diameter as
+// fit (at the densest packing, 0.7405) in the list radius around a centre
+static int list_capacity(const BoxHost *h) {
+    if (h->d.np == 0 || !h->have_closure) return 1;
+    const dps_closure &c = h->cl;
+    const double rl = h->dmax + (c.lubrication ? std::fmax(c.h_c, 0.0) : 0.0) + c.skin + 1e-3;
+    const double r0 = 0.5 * h->dmin;
+    double n = 0.7405 * std::pow((rl + r0) / r0, 3.0) + 1.0;
+    n = std::fmin(n, (double)h->d.np);
+    return (int)std::fmax(1.0, std::fmin(n, 1024.0));
+}
+
+static int ensure_lists(Batch *B) {
+    for (BoxHost *h : B->boxes) {
+        const int need = list_capacity(h);
+        if (need <= h->d.maxn && h->d.nlist) continue;
+        void *p = box_alloc(B, h, (size_t)need * (size_t)h->d.cap * 4);
+        if (!p) FAILB(B, DPS_ERR_OOM, "neighbour list allocation failed");
+        if (h->d.nlist) {
+            dfree_raw(B, h->d.nlist);
+            h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void *)h->d.nlist), h->allocs.end());
+        }
+        h->d.nlist = (int *)p;
+        h->d.maxn = need;
+        B->layout_dirty = true;
     }
     return DPS_OK;
 }
@@ -474,6 +528,10 @@ static int ready(Batch *B) {
             FAILB(B, DPS_ERR_ARG, "all boxes of a batch need the same n_int and n_dem");
     bool need_prep = false;
     for (BoxHost *h : B->boxes) need_prep |= !h->prepared;
+    if (need_prep) {
+        int rc = ensure_lists(B);
+        if (rc) return rc;
+    }
     if (B->layout_dirty || need_prep) {
         int rc = pull_state(B);
         if (rc) return rc;
@@ -502,17 +560,19 @@ static int run_steps(Batch *B, long long n) {
         if (!B->use_graphs) {
             enqueue_step(B);
         } else {
-            if (!B->gexec) {
+            cudaGraphExec_t &ge = B->gexec[B->parity];
+            if (!ge) {
                 cudaGraph_t g;
                 CKB(B, cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
                 enqueue_step(B);
                 CKB(B, cudaStreamEndCapture(B->stream, &g));
-                cudaError_t e = cudaGraphInstantiate(&B->gexec, g, 0);
+                cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
                 cudaGraphDestroy(g);
                 if (e != cudaSuccess) FAILB(B, DPS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
             }
-            CKB(B, cudaGraphLaunch(B->gexec, B->stream));
+            CKB(B, cudaGraphLaunch(ge, B->stream));
         }
+        B->parity ^= 1;
         for (BoxHost *h : B->boxes) h->steps++;
     }
     cudaError_t e = cudaGetLastError();
@@ -565,7 +625,7 @@ static size_t box_bytes(int prec, long long ncell, long long cap) {
     size_t pe = prec == DPS_F64 ? 8 : (prec == DPS_F32 ? 4 : 2), fe = prec == DPS_F64 ? 8 : 4;
     size_t N = (size_t)ncell, C = (size_t)(cap > 0 ? cap : 1);
     size_t b = 19 * N * pe + 26 * N * fe;
-    b += 2 * (size_t)NPF * C * 8 + 2 * (size_t)NPI * C * 4 + 9 * C * 8;
+    b += 2 * (size_t)NPF * C * 8 + 2 * (size_t)NPI * C * 4 + 9 * C * 8 + 2 * C * 16 + C * 4 + 64 * C * 4;
     b += (3 * N + 1) * 4 + 3 * C * 4 + ((N + 8191) / 8192 + 1) * 4;
     b += 4096 + (size_t)reduce_partials_doubles() * 8;
     return b;
@@ -612,6 +672,11 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
         d.pi[s] = (int *)A((size_t)NPI * cap * 4);
     }
     d.xtmp = (double *)A(9 * cap * 8);
+    d.xf[0] = (float4 *)A(cap * 16);
+    d.xf[1] = (float4 *)A(cap * 16);
+    d.nlist_n = (int *)A(cap * 4);
+    d.nlist = nullptr;  // sized at preparation (depends on the closure)
+    d.maxn = 0;
     d.cell_start = (int *)A((N + 1) * 4);
     d.count = (int *)A(N * 4);
     d.fill = (int *)A(N * 4);
@@ -642,7 +707,9 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
         launch_fill<float>(d.eps, ncell, 1.0, s);
     for (void *p : {d.fpf, d.fam, d.acc, d.j, d.uD, d.uprev, d.gradP, d.DuDt}) cudaMemsetAsync(p, 0, 3 * N * B->fel, s);
     cudaMemsetAsync(d.rho, 0, N * B->fel, s);
+    cudaMemsetAsync(d.nlist_n, 0, cap * 4, s);
     for (int k = 0; k < 2; ++k) {
+        cudaMemsetAsync(d.xf[k], 0, cap * 16, s);
         cudaMemsetAsync(d.pf[k], 0, (size_t)NPF * cap * 8, s);
         cudaMemsetAsync(d.pi[k], 0, (size_t)NPI * cap * 4, s);
     }
@@ -675,7 +742,7 @@ static int box_add_particles(Batch *B, BoxHost *h, long long n, const double *x3
     const long long cap = h->d.cap;
     std::vector<double> st((size_t)11 * n);
     std::vector<int> ids((size_t)n);
-    double sV = 0, sW = 0, dm = h->dmax;
+    double sV = 0, sW = 0, dm = h->dmax, dn = h->dmin;
     for (long long i = 0; i < n; ++i) {
         for (int a = 0; a < 3; ++a) {
             double x = x3[3 * i + a];
@@ -699,6 +766,7 @@ static int box_add_particles(Batch *B, BoxHost *h, long long n, const double *x3
         sV += V;
         sW += (rp[i] - h->rho_f) * V;
         dm = std::fmax(dm, dd[i]);
+        dn = std::fmin(dn, dd[i]);
     }
     double *pf = h->d.pf[h->d.cur];
     const long long off = h->d.np;
@@ -714,6 +782,7 @@ static int box_add_particles(Batch *B, BoxHost *h, long long n, const double *x3
     h->sumV += sV;
     h->sumWb += sW;
     h->dmax = dm;
+    h->dmin = dn;
     h->prepared = false;
     B->layout_dirty = true;
     return DPS_OK;
@@ -752,9 +821,9 @@ static int box_read_fields(Batch *B, BoxHost *h, uint32_t mask, double *out, lon
         if (bit == DPS_FIELD_RHO || bit == DPS_FIELD_UBAR || bit == DPS_FIELD_UF || bit == DPS_FIELD_P ||
             bit == DPS_FIELD_FEXT) {
             int what = bit == DPS_FIELD_RHO ? 0 : bit == DPS_FIELD_UBAR ? 1 : bit == DPS_FIELD_UF ? 2 : bit == DPS_FIELD_P ? 3 : 4;
-            PREC_CALL(B, (launch_fluid_export<double, double>(d.pdf, d.eps, d.fpf, d.g, fb, d.parity, what, buf, B->stream)),
-                      (launch_fluid_export<float, float>(d.pdf, d.eps, d.fpf, d.g, fb, d.parity, what, buf, B->stream)),
-                      (launch_fluid_export<__half, float>(d.pdf, d.eps, d.fpf, d.g, fb, d.parity, what, buf, B->stream)));
+            PREC_CALL(B, (launch_fluid_export<double, double>(d.pdf, d.eps, d.fpf, d.g, fb, B->parity, what, buf, B->stream)),
+                      (launch_fluid_export<float, float>(d.pdf, d.eps, d.fpf, d.g, fb, B->parity, what, buf, B->stream)),
+                      (launch_fluid_export<__half, float>(d.pdf, d.eps, d.fpf, d.g, fb, B->parity, what, buf, B->stream)));
         } else {
             const void *src = bit == DPS_FIELD_EPS ? d.eps : bit == DPS_FIELD_FPF ? d.fpf : bit == DPS_FIELD_GRADP ? d.gradP : d.DuDt;
             if (B->fel == 8)
@@ -823,9 +892,9 @@ static int box_stats(Batch *B, BoxHost *h, dps_stats *s) {
     compute_phys(h);
     const BoxDev &d = h->d;
     double fl[12], pt[6];
-    PREC_CALL(B, (launch_fluid_sums<double, double>(d.pdf, d.eps, d.fpf, d.g, d.ph.fb, d.parity, h->d_red, h->d_redout, B->stream)),
-              (launch_fluid_sums<float, float>(d.pdf, d.eps, d.fpf, d.g, d.ph.fb, d.parity, h->d_red, h->d_redout, B->stream)),
-              (launch_fluid_sums<__half, float>(d.pdf, d.eps, d.fpf, d.g, d.ph.fb, d.parity, h->d_red, h->d_redout, B->stream)));
+    PREC_CALL(B, (launch_fluid_sums<double, double>(d.pdf, d.eps, d.fpf, d.g, d.ph.fb, B->parity, h->d_red, h->d_redout, B->stream)),
+              (launch_fluid_sums<float, float>(d.pdf, d.eps, d.fpf, d.g, d.ph.fb, B->parity, h->d_red, h->d_redout, B->stream)),
+              (launch_fluid_sums<__half, float>(d.pdf, d.eps, d.fpf, d.g, d.ph.fb, B->parity, h->d_red, h->d_redout, B->stream)));
     CKB(B, cudaMemcpyAsync(fl, h->d_redout, sizeof(fl), cudaMemcpyDeviceToHost, B->stream));
     CKB(B, cudaStreamSynchronize(B->stream));
     launch_particle_sums(d.pf[d.cur], d.pf[d.cur], d.cap, d.np, h->d_red, h->d_redout, B->stream);
@@ -995,10 +1064,11 @@ int dps_collide_stream(dps_handle h, int64_t n) {
     if (rc) return rc;
     if ((rc = push_layout(B))) return rc;
     for (int64_t s = 0; s < n; ++s) {
-        PREC_CALL(B, (launch_collide_stream<double, double, double>(B->d_table, B->d_cell, B->n_cell, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
-                  (launch_collide_stream<float, float, float>(B->d_table, B->d_cell, B->n_cell, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
-                  (launch_collide_stream<__half, float, float>(B->d_table, B->d_cell, B->n_cell, grid_of(B->n_cell), B->tune.cell_block, B->stream)));
-        launch_flip_parity(B->d_table, (int)B->boxes.size(), B->stream);
+        const int par = B->parity;
+        PREC_CALL(B, (launch_collide_stream<double, double, double>(B->d_table, B->d_cell, B->n_cell, par, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
+                  (launch_collide_stream<float, float, float>(B->d_table, B->d_cell, B->n_cell, par, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
+                  (launch_collide_stream<__half, float, float>(B->d_table, B->d_cell, B->n_cell, par, grid_of(B->n_cell), B->tune.cell_block, B->stream)));
+        B->parity ^= 1;
     }
     return check_boxes(B);
 }
@@ -1054,9 +1124,9 @@ int dps_read_pdfs(dps_handle h, double *out, int64_t cap) {
     if (cap < (long long)Q * N) FAILB(B, DPS_ERR_ARG, "output capacity too small");
     double *buf = nullptr;
     CKB(B, cudaMallocAsync((void **)&buf, 8 * Q * N, B->stream));
-    PREC_CALL(B, launch_pdf_export<double>(d.pdf, d.g, d.parity, buf, B->stream),
-              launch_pdf_export<float>(d.pdf, d.g, d.parity, buf, B->stream),
-              launch_pdf_export<__half>(d.pdf, d.g, d.parity, buf, B->stream));
+    PREC_CALL(B, launch_pdf_export<double>(d.pdf, d.g, B->parity, buf, B->stream),
+              launch_pdf_export<float>(d.pdf, d.g, B->parity, buf, B->stream),
+              launch_pdf_export<__half>(d.pdf, d.g, B->parity, buf, B->stream));
     CKB(B, cudaMemcpyAsync(out, buf, 8 * Q * N, cudaMemcpyDeviceToHost, B->stream));
     CKB(B, cudaFreeAsync(buf, B->stream));
     CKB(B, cudaStreamSynchronize(B->stream));
@@ -1078,8 +1148,9 @@ int dps_write_pdfs(dps_handle h, const double *in, int64_t count) {
               launch_pdf_import<__half>(d.pdf, N, buf, B->stream));
     CKB(B, cudaFreeAsync(buf, B->stream));
     CKB(B, cudaStreamSynchronize(B->stream));
-    d.parity = 0;
-    return push_layout(B);
+    B->parity = 0;  // imported in the canonical layout
+    invalidate_graph(B);
+    return DPS_OK;
 }
 
 int dps_read_particles(dps_handle h, double *x3, double *u3, double *w3, double *F3, int64_t cap) {
@@ -1149,7 +1220,7 @@ static long long b_launches_per_step(Batch *B) {
     const int pl = np > 0;
     const int n_int = B->boxes.empty() ? 1 : B->boxes[0]->cl.n_int;
     const int n_dem = B->boxes.empty() ? 1 : B->boxes[0]->cl.n_dem;
-    return 2 + 2 + (long long)n_int * (2 * pl + 2 + pl * n_dem + 3 + 4 * pl + 1 + 1);
+    return 2 + 2 + (long long)n_int * (2 * pl + 2 + pl * n_dem + 3 + 5 * pl + 1 + 1);
 }
 
 int dps_set_timing(dps_handle h, int enable) { return h ? b_set_timing(&h->B, enable) : DPS_ERR_ARG; }
@@ -1226,8 +1297,7 @@ int dps_batch_remove_box(dps_batch b, int id) {
     BOX_OR_FAIL(b, id, h);
     int rc = pull_state(&b->B);
     if (rc) return rc;
-    auto &v = b->B.boxes;
-    v.erase(std::remove(v.begin(), v.end(), h), v.end());
+    forget_box(&b->B, h);
     b->ids.erase(std::remove_if(b->ids.begin(), b->ids.end(), [&](const std::pair<int, BoxHost *> &p) { return p.first == id; }),
                  b->ids.end());
     box_free(&b->B, h);

@@ -13,8 +13,8 @@ struct BoxDev {
     Geom g;
     Phys ph;
     int R;             // neighbour search radius (cells)
-    // step state, advanced on the device so that one captured graph serves
-    // every step: AA parity, current particle set, history flags
+    // step state advanced on the device (current particle set, history
+    // flags); the AA parity is common to the batch and passed per launch
     int parity, cur, have_uprev, have_usub;
     long long np, cap;
     // fluid
@@ -24,6 +24,11 @@ struct BoxDev {
     double *pf[2];
     int *pi[2];
     double *xtmp;
+    float4 *xf[2];     // float (x, y, z, d) of the current set / of the ping-pong planes
+    int *nlist;        // Verlet list, k-major: nlist[k*cap + i]
+    int *nlist_n;      // list length per particle
+    int maxn;          // list capacity per particle
+    int pad2_;
     // linked cells
     int *cell_start, *count, *fill, *key, *tmp, *perm;
     int *scan_part;    // per scan tile partial sums of this box

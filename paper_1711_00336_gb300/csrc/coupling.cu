@@ -180,6 +180,7 @@ __global__ void k_bsort_gather(const BoxDev *__restrict__ boxes, const Tile *__r
             dsti[IID * cap + k] = srci[IID * cap + i];
             dsti[ICELL * cap + k] = B.key[i];
             dsti[IKEY * cap + k] = B.key[i];
+            B.xf[0][k] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)srcf[PD * cap + i]);
         }
     }
 }
@@ -194,19 +195,10 @@ __global__ void k_bsort_flip(BoxDev *boxes, int nboxes, int mark_usub) {
     }
 }
 
-// fluid-only collide-stream step: only the AA parity flips
-__global__ void k_flip_parity(BoxDev *boxes, int nboxes) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nboxes) boxes[b].parity ^= 1;
-}
-
-// end of an LBM step: the AA parity flips, the previous-step velocity exists
+// end of an LBM step: the previous-step fluid velocity now exists
 __global__ void k_end_step(BoxDev *boxes, int nboxes) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nboxes) {
-        boxes[b].parity ^= 1;
-        boxes[b].have_uprev = 1;
-    }
+    if (b < nboxes) boxes[b].have_uprev = 1;
 }
 
 // ---- 27-cell gather helpers ---------------------------------------------------
@@ -544,7 +536,6 @@ void launch_bsort_flip(BoxDev *b, int nb, int mark_usub, cudaStream_t s) {
     k_bsort_flip<<<(nb + 127) / 128, 128, 0, s>>>(b, nb, mark_usub);
 }
 void launch_end_step(BoxDev *b, int nb, cudaStream_t s) { k_end_step<<<(nb + 127) / 128, 128, 0, s>>>(b, nb); }
-void launch_flip_parity(BoxDev *b, int nb, cudaStream_t s) { k_flip_parity<<<(nb + 127) / 128, 128, 0, s>>>(b, nb); }
 
 template <typename FT>
 void launch_eps(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {

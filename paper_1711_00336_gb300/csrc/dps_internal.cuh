@@ -52,6 +52,7 @@ enum : int {
     ST_EPS_NEG = 4,    // eps_f below zero before the floor
     ST_BAD_CELL = 8,   // particle outside the box on a wall axis
     ST_TIMEOUT = 16,
+    ST_NLIST = 32,     // a neighbour list overflowed its capacity
 };
 
 // counters (unsigned long long) in device memory
@@ -130,13 +131,15 @@ __host__ __device__ inline int containing_cell(double x, int L) {
 
 // closure constants, derived once on the host
 struct Phys {
-    double tau, omega, rho_f, mu;
+    double tau, omega, kf, rho_f, mu;   // kf = 1 - 1/(2 tau) (Eq. Forcing)
+    float omega_f, kf_f, fb_f[3];       // the same in FP32 for the low-precision forms
     double g[3], fb[3];
     double e_n, mu_c, T_c, h_c, h_min, C_am;
     double lub_cap;
     double eps_min;
     double dt_sub, dt_dem;
-    double skin_half2;   // (usable skin / 2)^2
+    double skin;         // Verlet skin (dx)
+    double skin_half2;   // (skin / 2)^2: largest displacement between two sorts
     int n_int, n_dem;
     int drag, pressure, added_mass, lubrication, contact, lub_limiter;
 };

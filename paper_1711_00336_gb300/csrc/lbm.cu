@@ -89,26 +89,26 @@ __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const 
     store_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
 }
 
-// K1: every cell tile of every box; the AA parity is the box's own
-template <typename ST, typename FT, typename CT>
-__global__ void __launch_bounds__(256) k_collide_stream(const BoxDev *__restrict__ boxes,
-                                                        const Tile *__restrict__ tiles, int ntiles) {
+template <typename CT> __device__ __forceinline__ CT pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+// K1: every cell tile of every box, AA parity PAR (common to the batch)
+template <typename ST, typename FT, typename CT, int PAR>
+__global__ void __launch_bounds__(128, sizeof(CT) == 8 ? 2 : 4) k_collide_stream(const BoxDev *__restrict__ boxes,
+                                                           const Tile *__restrict__ tiles, int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &B = boxes[tl.box];
         const Geom g = B.g;
         ST *pdf = (ST *)B.pdf;
         const FT *eps = (const FT *)B.eps, *fpf = (const FT *)B.fpf;
-        const CT fbx = (CT)B.ph.fb[0], fby = (CT)B.ph.fb[1], fbz = (CT)B.ph.fb[2];
-        const CT omega = (CT)B.ph.omega, kf = (CT)(1.0 - 0.5 / B.ph.tau);
+        const CT fbx = pick<CT>(B.ph.fb[0], B.ph.fb_f[0]), fby = pick<CT>(B.ph.fb[1], B.ph.fb_f[1]),
+                 fbz = pick<CT>(B.ph.fb[2], B.ph.fb_f[2]);
+        const CT omega = pick<CT>(B.ph.omega, B.ph.omega_f), kf = pick<CT>(B.ph.kf, B.ph.kf_f);
         int *st = B.status;
-        if (B.parity == 0) {
-            for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
-                collide_stream_cell<ST, FT, CT, 0>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, st);
-        } else {
-            for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
-                collide_stream_cell<ST, FT, CT, 1>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, st);
-        }
+        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
+            collide_stream_cell<ST, FT, CT, PAR>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, st);
     }
 }
 
@@ -139,9 +139,9 @@ __device__ __forceinline__ void moments_cell(const ST *__restrict__ pdf, const F
     uD[2 * N + c] = (FT)((jz + CT(0.5) * Fz) * s);
 }
 
-template <typename ST, typename FT, typename CT>
-__global__ void __launch_bounds__(256) k_moments(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
-                                                 int ntiles) {
+template <typename ST, typename FT, typename CT, int PAR>
+__global__ void __launch_bounds__(128, sizeof(CT) == 8 ? 2 : 4) k_moments(const BoxDev *__restrict__ boxes,
+                                                    const Tile *__restrict__ tiles, int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &B = boxes[tl.box];
@@ -149,14 +149,10 @@ __global__ void __launch_bounds__(256) k_moments(const BoxDev *__restrict__ boxe
         const ST *pdf = (const ST *)B.pdf;
         const FT *eps = (const FT *)B.eps, *fpf = (const FT *)B.fpf;
         FT *rho = (FT *)B.rho, *j = (FT *)B.j, *uD = (FT *)B.uD;
-        const CT fbx = (CT)B.ph.fb[0], fby = (CT)B.ph.fb[1], fbz = (CT)B.ph.fb[2];
-        if (B.parity == 0) {
-            for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
-                moments_cell<ST, FT, CT, 0>(pdf, eps, fpf, g, c, fbx, fby, fbz, rho, j, uD);
-        } else {
-            for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
-                moments_cell<ST, FT, CT, 1>(pdf, eps, fpf, g, c, fbx, fby, fbz, rho, j, uD);
-        }
+        const CT fbx = pick<CT>(B.ph.fb[0], B.ph.fb_f[0]), fby = pick<CT>(B.ph.fb[1], B.ph.fb_f[1]),
+                 fbz = pick<CT>(B.ph.fb[2], B.ph.fb_f[2]);
+        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
+            moments_cell<ST, FT, CT, PAR>(pdf, eps, fpf, g, c, fbx, fby, fbz, rho, j, uD);
     }
 }
 
@@ -267,13 +263,23 @@ static int grid_for(long long n, int block) {
 }
 
 template <typename ST, typename FT, typename CT>
-void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, int grid, int block, cudaStream_t s) {
-    k_collide_stream<ST, FT, CT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, int parity, int grid, int block,
+                           cudaStream_t s) {
+    if (block > 128) block = 128;  // register budget of __launch_bounds__(128, 4)
+    if (parity)
+        k_collide_stream<ST, FT, CT, 1><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+    else
+        k_collide_stream<ST, FT, CT, 0><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
 }
 
 template <typename ST, typename FT, typename CT>
-void launch_moments(const BoxDev *boxes, const Tile *tiles, int ntiles, int grid, int block, cudaStream_t s) {
-    k_moments<ST, FT, CT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+void launch_moments(const BoxDev *boxes, const Tile *tiles, int ntiles, int parity, int grid, int block,
+                    cudaStream_t s) {
+    if (block > 128) block = 128;
+    if (parity)
+        k_moments<ST, FT, CT, 1><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+    else
+        k_moments<ST, FT, CT, 0><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
 }
 
 template <typename FT, typename CT>
@@ -298,8 +304,8 @@ void launch_pdf_import(void *pdf, long long N, const double *in, cudaStream_t s)
 
 // explicit instantiations for the three precision forms
 #define DPS_LBM_INST(ST, FT, CT)                                                                             \
-    template void launch_collide_stream<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t); \
-    template void launch_moments<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+    template void launch_collide_stream<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t); \
+    template void launch_moments<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 DPS_LBM_INST(double, double, double)
 DPS_LBM_INST(float, float, float)
 DPS_LBM_INST(__half, float, float)

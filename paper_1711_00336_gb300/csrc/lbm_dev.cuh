@@ -8,36 +8,37 @@ namespace dps {
 
 // linear-index deltas to the -1/+1 neighbour along each axis; INV marks a
 // neighbour beyond a wall.
-constexpr long long INV = (1LL << 62);
+// (ncell < 2^30, so no real delta can equal INV)
+constexpr int INV = (1 << 30);
 
 struct NbDelta {
-    long long d[3][3];  // [axis][offset+1]
+    int d[3][3];  // [axis][offset+1]
 };
 
 __device__ __forceinline__ void cell_coords(const Geom &g, long long c, int &ix, int &iy, int &iz) {
-    long long nxy = (long long)g.n[0] * g.n[1];
-    iz = (int)(c / nxy);
-    long long r = c - (long long)iz * nxy;
-    iy = (int)(r / g.n[0]);
-    ix = (int)(r - (long long)iy * g.n[0]);
+    const unsigned cc = (unsigned)c, nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
+    const unsigned z = cc / nxy, r = cc - z * nxy, y = r / nx;
+    iz = (int)z;
+    iy = (int)y;
+    ix = (int)(r - y * nx);
 }
 
 __device__ __forceinline__ NbDelta neighbour_deltas(const Geom &g, int ix, int iy, int iz) {
     NbDelta D;
     const int ii[3] = {ix, iy, iz};
-    long long stride[3] = {1, g.n[0], (long long)g.n[0] * g.n[1]};
+    const int stride[3] = {1, g.n[0], g.n[0] * g.n[1]};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        int L = g.n[a];
+        const int L = g.n[a];
         D.d[a][1] = 0;
-        D.d[a][0] = ii[a] > 0 ? -stride[a] : (g.per[a] ? (long long)(L - 1) * stride[a] : INV);
-        D.d[a][2] = ii[a] < L - 1 ? stride[a] : (g.per[a] ? -(long long)(L - 1) * stride[a] : INV);
+        D.d[a][0] = ii[a] > 0 ? -stride[a] : (g.per[a] ? (L - 1) * stride[a] : INV);
+        D.d[a][2] = ii[a] < L - 1 ? stride[a] : (g.per[a] ? -(L - 1) * stride[a] : INV);
     }
     return D;
 }
 
-__device__ __forceinline__ long long nb_delta(const NbDelta &D, int q) {
-    long long dx = D.d[0][CX(q) + 1], dy = D.d[1][CY(q) + 1], dz = D.d[2][CZ(q) + 1];
+__device__ __forceinline__ int nb_delta(const NbDelta &D, int q) {
+    const int dx = D.d[0][CX(q) + 1], dy = D.d[1][CY(q) + 1], dz = D.d[2][CZ(q) + 1];
     if (dx == INV || dy == INV || dz == INV) return INV;
     return dx + dy + dz;
 }
@@ -53,9 +54,9 @@ __device__ __forceinline__ void load_pdfs(const ST *__restrict__ pdf, long long 
         } else {
             // f_q(x) was written by the upstream cell x - c_q into plane opp(q);
             // across a wall it is the own cell's bounced value in plane q.
-            long long dm;
+            int dm;
             {
-                long long dx = D.d[0][-CX(q) + 1], dy = D.d[1][-CY(q) + 1], dz = D.d[2][-CZ(q) + 1];
+                const int dx = D.d[0][-CX(q) + 1], dy = D.d[1][-CY(q) + 1], dz = D.d[2][-CZ(q) + 1];
                 dm = (dx == INV || dy == INV || dz == INV) ? INV : dx + dy + dz;
             }
             if (dm != INV)
@@ -76,7 +77,7 @@ __device__ __forceinline__ void store_pdfs(ST *__restrict__ pdf, long long N, lo
         } else if (PAR == 0) {
             Store<ST>::store(pdf + (long long)OPP(q) * N + c, f[q]);
         } else {
-            long long dp = nb_delta(D, q);
+            const int dp = nb_delta(D, q);
             if (dp != INV)
                 Store<ST>::store(pdf + (long long)q * N + c + dp, f[q]);
             else  // bounce back: returns to this cell with velocity -c_q

@@ -161,9 +161,9 @@ def test_serving_result_is_the_same_alone_and_in_the_mix():
     mixed = S.poll(ids[-1])
     st = S.stats()
     S.close()
-    assert mixed["state"] == "done"
-    assert np.array_equal(mixed["up_mean"], alone["up_mean"])
-    assert np.array_equal(mixed["u_pS"], alone["u_pS"])
+    assert mixed["state"] == "done", mixed
+    assert np.array_equal(mixed["up_mean"], alone["up_mean"]), (mixed, alone)
+    assert np.array_equal(mixed["u_pS"], alone["u_pS"]), (mixed, alone)
     assert st["completed"] == 3 and st["cell_updates"] > 0
 
 
