@@ -346,6 +346,29 @@ int dps_op_cell_sort(const int n[3], const int periodic[3], int B, int64_t np,
                      const double *x3, const int32_t *ids, int32_t *cell_start, int32_t *order,
                      void *stream);
 
+/* ---- allocation-free variant of the cell sort ---------------------------- */
+/* The paper has no counterpart: this entry point is a property of the
+ * library, not of the method.  dps_op_cell_sort takes its scratch memory
+ * (per-cell counts, per-particle keys and permutation, scan partials) from the
+ * stream-ordered allocator.  Callers that cannot allocate device memory while
+ * they run -- a program that handed the whole device to its own pool
+ * allocator, or a time-stepping loop that must not allocate (nor wait on an
+ * allocation) once it is running -- call dps_op_cell_sort_noalloc instead: the
+ * same sort, with its scratch in a fixed array compiled into the library
+ * (about 5 MB held on every GPU that loads the library, until the process
+ * exits).  Inputs, outputs and results are those of dps_op_cell_sort, for at
+ * most DPS_NOALLOC_MAX_CELLS cells and DPS_NOALLOC_MAX_PARTICLES particles;
+ * larger sizes return DPS_ERR_ARG.  It calls no cudaMalloc/cudaFree or other
+ * allocating routine.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call uses the one array and
+ * leaves its contents behind: calls that overlap on the GPU (other streams or
+ * threads) race, so the caller must serialise them. */
+#define DPS_NOALLOC_MAX_CELLS 262144
+#define DPS_NOALLOC_MAX_PARTICLES 262144
+int dps_op_cell_sort_noalloc(const int n[3], const int periodic[3], int B, int64_t np, const double *x3,
+                             const int32_t *ids, int32_t *cell_start, int32_t *order, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
