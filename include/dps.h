@@ -18,6 +18,7 @@
  *     host buffer it passes; each transfer is a copy (host pointers are read or
  *     written before the call returns);
  *   - calls on one handle are not thread-safe; distinct handles are independent;
+ *   - a box holds at most 2^27 lattice cells;
  *   - the "op" entry points at the end work on caller-owned DEVICE buffers and
  *     are stream-ordered on the stream they are given.
  */
@@ -257,9 +258,10 @@ int dps_batch_stats(dps_batch b, int box, dps_stats *s);
 /* mean particle velocity of a box (FP64, fixed summation order) */
 int dps_batch_particle_mean(dps_batch b, int box, double u[3]);
 int dps_batch_num_boxes(dps_batch b, int *n);
-/* launch shape: cfg = {cell threads/block, cells/tile, particle threads/block, particles/tile} */
-int dps_batch_set_tuning(dps_batch b, const int cfg[4]);
-int dps_batch_get_tuning(dps_batch b, int cfg[4]);
+/* launch shape: cfg = {cell threads/block, cells/tile, particle threads/block,
+ * particles/tile, collide-stream register-budget variant (0, 1 or 2)} */
+int dps_batch_set_tuning(dps_batch b, const int cfg[5]);
+int dps_batch_get_tuning(dps_batch b, int cfg[5]);
 /* autotuner: time every candidate launch shape for `steps` steps on the
  * current boxes (their state advances) and keep the fastest; ms[0] receives
  * the best time per step */

@@ -19,7 +19,7 @@
 namespace dps {
 // launchers (lbm.cu, coupling.cu, dem.cu, scan.cu, io.cu)
 template <typename ST, typename FT, typename CT>
-void launch_collide_stream(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
+void launch_collide_stream(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
 template <typename ST, typename FT, typename CT>
 void launch_moments(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 template <typename FT, typename CT>
@@ -101,6 +101,7 @@ enum { PH_MOM = 0, PH_FAM, PH_RAM, PH_FDRAG, PH_RDRAG, PH_DEM, PH_SORT, PH_EPS, 
 struct Tuning {
     int cell_block = 128, cell_tile = 1024;   // threads per block, cells per tile
     int part_block = 128, part_tile = 256;    // threads per block, particles per tile
+    int k1v = 0;                              // collide-stream register-budget variant
 };
 
 struct Batch {
@@ -264,6 +265,12 @@ static void compute_phys(BoxHost *h) {
     p.lubrication = c.lubrication;
     p.contact = c.contact;
     p.lub_limiter = c.lub_limiter;
+    {
+        const double le = std::log(c.e_n);
+        p.kfac = (PI_H * PI_H + le * le) / (c.T_c * c.T_c);  // k_n / m_ij
+        p.xfac = -2.0 * le / c.T_c;                          // xi_n / m_ij
+        p.capfac = c.lub_cap / p.dt_dem;                     // lubrication cap / m_ij
+    }
     // Verlet list: partners within (d_i+d_j)/2 + h_c + skin; linked cells of
     // +-R cells cover that range; particles may move skin/2 between sorts
     const double cutoff = h->dmax + (c.lubrication ? std::fmax(c.h_c, 0.0) : 0.0);
@@ -455,9 +462,9 @@ static void enqueue_step(Batch *B) {
         enqueue_sort_eps(B, B->n_dem & 1, 1);
     }
     tbegin(B);
-    PREC_CALL(B, (launch_collide_stream<double, double, double>(T, B->d_cell, B->n_cell, par, gc, u.cell_block, s)),
-              (launch_collide_stream<float, float, float>(T, B->d_cell, B->n_cell, par, gc, u.cell_block, s)),
-              (launch_collide_stream<__half, float, float>(T, B->d_cell, B->n_cell, par, gc, u.cell_block, s)));
+    PREC_CALL(B, (launch_collide_stream<double, double, double>(T, B->d_cell, B->n_cell, par, u.k1v, gc, u.cell_block, s)),
+              (launch_collide_stream<float, float, float>(T, B->d_cell, B->n_cell, par, u.k1v, gc, u.cell_block, s)),
+              (launch_collide_stream<__half, float, float>(T, B->d_cell, B->n_cell, par, u.k1v, gc, u.cell_block, s)));
     launch_end_step(B->d_table, (int)B->boxes.size(), s);
     tend(B, PH_COLLIDE, 2);
     B->launches_step = B->launch_count;
@@ -625,7 +632,7 @@ static size_t box_bytes(int prec, long long ncell, long long cap) {
     size_t pe = prec == DPS_F64 ? 8 : (prec == DPS_F32 ? 4 : 2), fe = prec == DPS_F64 ? 8 : 4;
     size_t N = (size_t)ncell, C = (size_t)(cap > 0 ? cap : 1);
     size_t b = 19 * N * pe + 26 * N * fe;
-    b += 2 * (size_t)NPF * C * 8 + 2 * (size_t)NPI * C * 4 + 9 * C * 8 + 2 * C * 16 + C * 4 + 64 * C * 4;
+    b += 2 * (size_t)NPF * C * 8 + 2 * (size_t)NPI * C * 4 + 9 * C * 8 + 6 * C * 16 + C * 4 + 64 * C * 4 + 15 * C * 4;
     b += (3 * N + 1) * 4 + 3 * C * 4 + ((N + 8191) / 8192 + 1) * 4;
     b += 4096 + (size_t)reduce_partials_doubles() * 8;
     return b;
@@ -638,7 +645,7 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
     for (int a = 0; a < 3; ++a)
         if (n[a] < 1) FAILB(B, DPS_ERR_ARG, "lattice size must be >= 1 per axis");
     long long ncell = (long long)n[0] * n[1] * n[2];
-    if (ncell >= (1LL << 31) - 1) FAILB(B, DPS_ERR_ARG, "lattice too large for 32-bit cell indices");
+    if (ncell > (1LL << 27)) FAILB(B, DPS_ERR_ARG, "lattice too large: at most 2^27 cells per box");
     if (!(tau > 0.5) || !(rho_f > 0.0) || max_particles < 0 || max_particles >= (1LL << 31))
         FAILB(B, DPS_ERR_ARG, "invalid box (tau > 0.5, rho_f > 0, particle capacity)");
     BoxHost *h = new BoxHost();
@@ -672,9 +679,15 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
         d.pi[s] = (int *)A((size_t)NPI * cap * 4);
     }
     d.xtmp = (double *)A(9 * cap * 8);
-    d.xf[0] = (float4 *)A(cap * 16);
-    d.xf[1] = (float4 *)A(cap * 16);
+    for (int k = 0; k < 2; ++k) {
+        d.xf[k] = (float4 *)A(cap * 16);
+        d.vf[k] = (float4 *)A(cap * 16);
+        d.of[k] = (float4 *)A(cap * 16);
+    }
     d.nlist_n = (int *)A(cap * 4);
+    d.lowp = B->prec != DPS_F64;
+    d.pwf = d.lowp ? (float *)A(9 * cap * 4) : nullptr;
+    d.f32p = d.lowp ? (float *)A(6 * cap * 4) : nullptr;
     d.nlist = nullptr;  // sized at preparation (depends on the closure)
     d.maxn = 0;
     d.cell_start = (int *)A((N + 1) * 4);
@@ -710,6 +723,8 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
     cudaMemsetAsync(d.nlist_n, 0, cap * 4, s);
     for (int k = 0; k < 2; ++k) {
         cudaMemsetAsync(d.xf[k], 0, cap * 16, s);
+        cudaMemsetAsync(d.vf[k], 0, cap * 16, s);
+        cudaMemsetAsync(d.of[k], 0, cap * 16, s);
         cudaMemsetAsync(d.pf[k], 0, (size_t)NPF * cap * 8, s);
         cudaMemsetAsync(d.pi[k], 0, (size_t)NPI * cap * 4, s);
     }
@@ -1065,9 +1080,10 @@ int dps_collide_stream(dps_handle h, int64_t n) {
     if ((rc = push_layout(B))) return rc;
     for (int64_t s = 0; s < n; ++s) {
         const int par = B->parity;
-        PREC_CALL(B, (launch_collide_stream<double, double, double>(B->d_table, B->d_cell, B->n_cell, par, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
-                  (launch_collide_stream<float, float, float>(B->d_table, B->d_cell, B->n_cell, par, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
-                  (launch_collide_stream<__half, float, float>(B->d_table, B->d_cell, B->n_cell, par, grid_of(B->n_cell), B->tune.cell_block, B->stream)));
+        const int v = B->tune.k1v;
+        PREC_CALL(B, (launch_collide_stream<double, double, double>(B->d_table, B->d_cell, B->n_cell, par, v, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
+                  (launch_collide_stream<float, float, float>(B->d_table, B->d_cell, B->n_cell, par, v, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
+                  (launch_collide_stream<__half, float, float>(B->d_table, B->d_cell, B->n_cell, par, v, grid_of(B->n_cell), B->tune.cell_block, B->stream)));
         B->parity ^= 1;
     }
     return check_boxes(B);
@@ -1372,24 +1388,26 @@ int dps_batch_num_boxes(dps_batch b, int *n) {
     *n = (int)b->B.boxes.size();
     return DPS_OK;
 }
-int dps_batch_set_tuning(dps_batch b, const int cfg[4]) {
+int dps_batch_set_tuning(dps_batch b, const int cfg[5]) {
     if (!b || !cfg) return DPS_ERR_ARG;
     for (int k = 0; k < 4; ++k)
         if (cfg[k] < 32 || cfg[k] > (1 << 20)) FAILB(&b->B, DPS_ERR_ARG, "invalid launch shape");
     if (cfg[0] > 256 || cfg[2] > 256 || (cfg[0] & 31) || (cfg[2] & 31))
         FAILB(&b->B, DPS_ERR_ARG, "threads per block must be a multiple of 32, at most 256");
+    if (cfg[4] < 0 || cfg[4] > 2) FAILB(&b->B, DPS_ERR_ARG, "collide-stream variant must be 0, 1 or 2");
     int rc = pull_state(&b->B);
     if (rc) return rc;
-    b->B.tune = Tuning{cfg[0], cfg[1], cfg[2], cfg[3]};
+    b->B.tune = Tuning{cfg[0], cfg[1], cfg[2], cfg[3], cfg[4]};
     b->B.layout_dirty = true;
     return DPS_OK;
 }
-int dps_batch_get_tuning(dps_batch b, int cfg[4]) {
+int dps_batch_get_tuning(dps_batch b, int cfg[5]) {
     if (!b || !cfg) return DPS_ERR_ARG;
     cfg[0] = b->B.tune.cell_block;
     cfg[1] = b->B.tune.cell_tile;
     cfg[2] = b->B.tune.part_block;
     cfg[3] = b->B.tune.part_tile;
+    cfg[4] = b->B.tune.k1v;
     return DPS_OK;
 }
 
@@ -1429,6 +1447,15 @@ static int autotune(Batch *B, int steps, double *best_ms) {
         if ((rc = time_cfg(t, &ms))) break;
         if (ms < bms) { bms = ms; best = t; }
     }
+    if (!rc && B->prec != DPS_F64)
+        for (int v = 0; v < 3; ++v) {
+            if (v == best.k1v) continue;
+            Tuning t = best;
+            t.k1v = v;
+            double ms;
+            if ((rc = time_cfg(t, &ms))) break;
+            if (ms < bms) { bms = ms; best = t; }
+        }
     if (!rc)
         for (auto &c : part_c) {
             Tuning t = best;

@@ -25,10 +25,14 @@ struct BoxDev {
     int *pi[2];
     double *xtmp;
     float4 *xf[2];     // float (x, y, z, d) of the current set / of the ping-pong planes
+    float4 *vf[2];     // float (u, m) likewise
+    float4 *of[2];     // float (omega, 0) likewise
     int *nlist;        // Verlet list, k-major: nlist[k*cap + i]
     int *nlist_n;      // list length per particle
     int maxn;          // list capacity per particle
-    int pad2_;
+    int lowp;          // 1: low-precision form (FP32 coupling arithmetic)
+    float *pwf;        // FP32 kernel weights [9][cap] (low-precision forms)
+    float *f32p;       // FP32 copies of F_am (3 planes) and F_d (3 planes) [6][cap]
     // linked cells
     int *cell_start, *count, *fill, *key, *tmp, *perm;
     int *scan_part;    // per scan tile partial sums of this box

@@ -51,6 +51,40 @@ __device__ __forceinline__ void axis_weights(double x, int L, int periodic, doub
     }
 }
 
+// FP32 variant for the low-precision forms: the distances to the cell
+// centres are taken in FP64 (positions are FP64), the kernel in FP32
+__device__ __forceinline__ float roma_phi_f(float r) {
+    r = fabsf(r);
+    if (r < 0.5f) return (1.0f + sqrtf(1.0f - 3.0f * r * r)) * (1.0f / 3.0f);
+    if (r < 1.5f) {
+        const float s = 1.0f - r;
+        return (5.0f - 3.0f * r - sqrtf(1.0f - 3.0f * s * s)) * (1.0f / 6.0f);
+    }
+    return 0.0f;
+}
+__device__ __forceinline__ void axis_weights_f(double x, int L, int periodic, float w[3]) {
+    int i = containing_cell(x, L);
+    float sum = 0.0f;
+#pragma unroll
+    for (int o = -1; o <= 1; ++o) {
+        int c = i + o;
+        bool ok = periodic || (c >= 0 && c < L);
+        w[o + 1] = ok ? roma_phi_f((float)((c + 0.5) - x)) : 0.0f;
+        sum += w[o + 1];
+    }
+    if (!periodic) {
+        if (sum > 0.0f) {
+            const float inv = 1.0f / sum;
+            w[0] *= inv;
+            w[1] *= inv;
+            w[2] *= inv;
+        } else {
+            w[0] = w[2] = 0.0f;
+            w[1] = 1.0f;
+        }
+    }
+}
+
 __device__ __forceinline__ long long particle_cell(const Geom &g, double x, double y, double z, int *st) {
     int ix = containing_cell(x, g.n[0]), iy = containing_cell(y, g.n[1]), iz = containing_cell(z, g.n[2]);
     if (st && ((!g.per[0] && (x < 0.0 || x >= g.n[0])) || (!g.per[1] && (y < 0.0 || y >= g.n[1])) ||
@@ -171,16 +205,28 @@ __global__ void k_bsort_gather(const BoxDev *__restrict__ boxes, const Tile *__r
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 dstf[(PXS0 + a) * cap + k] = x[a];
-                double w[3];
-                axis_weights(x[a], g.n[a], g.per[a], w);
-                dstf[(PW0 + 3 * a + 0) * cap + k] = w[0];
-                dstf[(PW0 + 3 * a + 1) * cap + k] = w[1];
-                dstf[(PW0 + 3 * a + 2) * cap + k] = w[2];
+                if (B.lowp) {
+                    float w[3];
+                    axis_weights_f(x[a], g.n[a], g.per[a], w);
+                    B.pwf[(3 * a + 0) * cap + k] = w[0];
+                    B.pwf[(3 * a + 1) * cap + k] = w[1];
+                    B.pwf[(3 * a + 2) * cap + k] = w[2];
+                } else {
+                    double w[3];
+                    axis_weights(x[a], g.n[a], g.per[a], w);
+                    dstf[(PW0 + 3 * a + 0) * cap + k] = w[0];
+                    dstf[(PW0 + 3 * a + 1) * cap + k] = w[1];
+                    dstf[(PW0 + 3 * a + 2) * cap + k] = w[2];
+                }
             }
             dsti[IID * cap + k] = srci[IID * cap + i];
             dsti[ICELL * cap + k] = B.key[i];
             dsti[IKEY * cap + k] = B.key[i];
-            B.xf[0][k] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)srcf[PD * cap + i]);
+            const double dd = srcf[PD * cap + i];
+            const double m = srcf[PRHO * cap + i] * PI_D / 6.0 * dd * dd * dd;
+            B.xf[0][k] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)dd);
+            B.vf[0][k] = make_float4((float)xuw[3 * cap + i], (float)xuw[4 * cap + i], (float)xuw[5 * cap + i], (float)m);
+            B.of[0][k] = make_float4((float)xuw[6 * cap + i], (float)xuw[7 * cap + i], (float)xuw[8 * cap + i], 0.f);
         }
     }
 }
@@ -207,11 +253,11 @@ struct CellNb {
 };
 
 __device__ __forceinline__ void cell_coords_c(const Geom &g, long long c, int &ix, int &iy, int &iz) {
-    long long nxy = (long long)g.n[0] * g.n[1];
-    iz = (int)(c / nxy);
-    long long r = c - (long long)iz * nxy;
-    iy = (int)(r / g.n[0]);
-    ix = (int)(r - (long long)iy * g.n[0]);
+    const unsigned cc = (unsigned)c, nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
+    const unsigned z = cc / nxy, r = cc - z * nxy, y = r / nx;
+    iz = (int)z;
+    iy = (int)y;
+    ix = (int)(r - y * nx);
 }
 
 __device__ __forceinline__ int wrap_axis(int i, int L, int per) {
@@ -224,9 +270,9 @@ __device__ __forceinline__ int wrap_axis(int i, int L, int per) {
 // of the 27 cells c+o, o in {-1,0,1}^3, with weight W_p(c) =
 // w_x[1-o_x] w_y[1-o_y] w_z[1-o_z].  Visit order: o_z, o_y, o_x ascending,
 // then the sorted order inside a cell.
-template <typename Fn>
+template <typename WT, typename Fn>
 __device__ __forceinline__ void gather27(const Geom &g, long long c, const int *__restrict__ cell_start,
-                                         const double *__restrict__ pf, long long cap, Fn &&fn) {
+                                         const WT *__restrict__ w, long long cap, Fn &&fn) {
     int ix, iy, iz;
     cell_coords_c(g, c, ix, iy, iz);
 #pragma unroll 1
@@ -237,24 +283,31 @@ __device__ __forceinline__ void gather27(const Geom &g, long long c, const int *
         for (int oy = -1; oy <= 1; ++oy) {
             int y = wrap_axis(iy + oy, g.n[1], g.per[1]);
             if (y < 0) continue;
+            const WT *wz = w + (6 + 1 - oz) * cap, *wy = w + (3 + 1 - oy) * cap;
 #pragma unroll 1
             for (int ox = -1; ox <= 1; ++ox) {
                 int x = wrap_axis(ix + ox, g.n[0], g.per[0]);
                 if (x < 0) continue;
-                long long n = cell_index(g, x, y, z);
-                int s = cell_start[n], e = cell_start[n + 1];
-                for (int p = s; p < e; ++p) {
-                    double W = pf[(PW0 + 0 + 1 - ox) * cap + p] * pf[(PW0 + 3 + 1 - oy) * cap + p] *
-                               pf[(PW0 + 6 + 1 - oz) * cap + p];
-                    fn(p, W);
-                }
+                const long long n = cell_index(g, x, y, z);
+                const int s = cell_start[n], e = cell_start[n + 1];
+                const WT *wx = w + (1 - ox) * cap;
+                for (int p = s; p < e; ++p) fn(p, wx[p] * wy[p] * wz[p]);
             }
         }
     }
 }
 
+// the kernel weights of a box in the compute type FT of its form
+template <typename FT> __device__ __forceinline__ const FT *weights_of(const BoxDev &B, const double *pf);
+template <> __device__ __forceinline__ const double *weights_of<double>(const BoxDev &B, const double *pf) {
+    return pf + PW0 * B.cap;
+}
+template <> __device__ __forceinline__ const float *weights_of<float>(const BoxDev &B, const double *) { return B.pwf; }
+
 // ---- S2: eps_f ------------------------------------------------------------------
-// also clears the sort counts for the next sort (every cell visited once)
+// FT is the compute type of the form: FP64 for the plain method, FP32 (with
+// FP32 kernel weights) for the low-precision forms.  Also clears the sort
+// counts for the next sort (every cell is visited once).
 template <typename FT>
 __global__ void k_eps_gather(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
@@ -263,22 +316,24 @@ __global__ void k_eps_gather(const BoxDev *__restrict__ boxes, const Tile *__res
         const Geom g = B.g;
         const double *pf = B.pf[B.cur];
         const long long cap = B.cap;
+        const FT *w = weights_of<FT>(B, pf);
+        const float4 *xf = B.xf[0];
         FT *eps = (FT *)B.eps;
-        const double eps_min = B.ph.eps_min;
+        const FT eps_min = (FT)B.ph.eps_min;
         unsigned nclamp = 0;
         for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
-            double ep = 0.0;
-            gather27(g, c, B.cell_start, pf, cap, [&](int p, double W) {
-                double d = pf[PD * cap + p];
-                ep += W * (PI_D / 6.0 * d * d * d);
+            FT ep = 0;
+            gather27(g, c, B.cell_start, w, cap, [&](int p, FT W) {
+                const FT d = sizeof(FT) == 8 ? (FT)pf[PD * cap + p] : (FT)xf[p].w;
+                ep += W * (FT(PI_D / 6.0) * d * d * d);
             });
-            double e = 1.0 - ep;
+            FT e = FT(1) - ep;
             if (e < eps_min) {
-                if (e < 0.0) atomicOr(B.status, ST_EPS_NEG);
+                if (e < FT(0)) atomicOr(B.status, ST_EPS_NEG);
                 ++nclamp;
                 e = eps_min;
             }
-            eps[c] = (FT)e;
+            eps[c] = e;
             B.count[c] = 0;
         }
         if (nclamp) atomicAdd(&B.counters[CNT_EPS_CLAMP], (unsigned long long)nclamp);
@@ -286,66 +341,80 @@ __global__ void k_eps_gather(const BoxDev *__restrict__ boxes, const Tile *__res
 }
 
 // ---- S4: particle forces --------------------------------------------------------
-// interpolation (Eq. interpolation) of ncomp planes of a field at particle p
-template <typename FT, int NC>
-__device__ __forceinline__ void interp(const Geom &g, const double *__restrict__ pf, long long cap, long long p,
-                                       const FT *__restrict__ field, double out[NC]) {
-    const long long N = g.ncell;
-    double wx[3], wy[3], wz[3];
+// the 27-cell support of particle p: weights and the base cell of the sort
+template <typename FT>
+struct Support {
+    FT wx[3], wy[3], wz[3];
+    int b[3];
+};
+
+template <typename FT>
+__device__ __forceinline__ Support<FT> support_of(const BoxDev &B, const double *pf, long long p) {
+    const long long cap = B.cap;
+    const FT *w = weights_of<FT>(B, pf);
+    Support<FT> S;
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
-        wx[o] = pf[(PW0 + o) * cap + p];
-        wy[o] = pf[(PW0 + 3 + o) * cap + p];
-        wz[o] = pf[(PW0 + 6 + o) * cap + p];
+        S.wx[o] = w[o * cap + p];
+        S.wy[o] = w[(3 + o) * cap + p];
+        S.wz[o] = w[(6 + o) * cap + p];
     }
-    int bx = containing_cell(pf[PXS0 * cap + p], g.n[0]);
-    int by = containing_cell(pf[(PXS0 + 1) * cap + p], g.n[1]);
-    int bz = containing_cell(pf[(PXS0 + 2) * cap + p], g.n[2]);
 #pragma unroll
-    for (int k = 0; k < NC; ++k) out[k] = 0.0;
+    for (int a = 0; a < 3; ++a) S.b[a] = containing_cell(pf[(PXS0 + a) * cap + p], B.g.n[a]);
+    return S;
+}
+
+// visit the in-domain cells of the support (Eq. interpolation), fn(cell, W)
+template <typename FT, typename Fn>
+__device__ __forceinline__ void for_support(const Geom &g, const Support<FT> &S, Fn &&fn) {
 #pragma unroll 1
     for (int oz = 0; oz < 3; ++oz) {
-        int z = wrap_axis(bz + oz - 1, g.n[2], g.per[2]);
+        const int z = wrap_axis(S.b[2] + oz - 1, g.n[2], g.per[2]);
         if (z < 0) continue;
         for (int oy = 0; oy < 3; ++oy) {
-            int y = wrap_axis(by + oy - 1, g.n[1], g.per[1]);
+            const int y = wrap_axis(S.b[1] + oy - 1, g.n[1], g.per[1]);
             if (y < 0) continue;
             for (int ox = 0; ox < 3; ++ox) {
-                int x = wrap_axis(bx + ox - 1, g.n[0], g.per[0]);
+                const int x = wrap_axis(S.b[0] + ox - 1, g.n[0], g.per[0]);
                 if (x < 0) continue;
-                long long c = cell_index(g, x, y, z);
-                double W = wx[ox] * wy[oy] * wz[oz];
-#pragma unroll
-                for (int k = 0; k < NC; ++k) out[k] += W * (double)field[k * N + c];
+                fn(cell_index(g, x, y, z), S.wx[ox] * S.wy[oy] * S.wz[oz]);
             }
         }
     }
 }
 
 // K5a: added mass, F_am = C_am rho_f V (Du_f/Dt|p - du_p/dt) (Table 1);
-// du_p/dt is the change of u_p over the previous subcycle.
+// du_p/dt is the change of u_p over the previous subcycle (taken in FP64).
 template <typename FT>
 __global__ void k_force_am(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &B = boxes[tl.box];
         const Geom g = B.g;
+        const long long N = g.ncell;
         const Phys &ph = B.ph;
         double *pf = B.pf[B.cur];
         const long long cap = B.cap;
         const FT *DuDt = (const FT *)B.DuDt;
         const int have_usub = B.have_usub;
         for (long long p = tl.begin + threadIdx.x; p < tl.end; p += blockDim.x) {
-            double Du[3];
-            interp<FT, 3>(g, pf, cap, p, DuDt, Du);
-            double d = pf[PD * cap + p];
-            double V = PI_D / 6.0 * d * d * d;
+            const Support<FT> S = support_of<FT>(B, pf, p);
+            FT Du[3] = {0, 0, 0};
+            for_support(g, S, [&](long long c, FT W) {
+                Du[0] += W * DuDt[c];
+                Du[1] += W * DuDt[N + c];
+                Du[2] += W * DuDt[2 * N + c];
+            });
+            const double d = pf[PD * cap + p];
+            const FT cV = (FT)(ph.C_am * ph.rho_f * PI_D / 6.0 * d * d * d);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                double u = pf[(PU + a) * cap + p];
-                double dudt = have_usub ? (u - pf[(PUS0 + a) * cap + p]) / ph.dt_sub : 0.0;
+                const double u = pf[(PU + a) * cap + p];
+                const double dudt = have_usub ? (u - pf[(PUS0 + a) * cap + p]) / ph.dt_sub : 0.0;
                 pf[(PUS0 + a) * cap + p] = u;
-                pf[(PFA0 + a) * cap + p] = ph.added_mass ? ph.C_am * ph.rho_f * V * (Du[a] - dudt) : 0.0;
+                const FT Fa = ph.added_mass ? cV * (Du[a] - (FT)dudt) : FT(0);
+                pf[(PFA0 + a) * cap + p] = (double)Fa;
+                if (sizeof(FT) == 4) B.f32p[a * cap + p] = (float)Fa;
             }
         }
     }
@@ -359,6 +428,15 @@ __device__ __forceinline__ double drag_cd(double Re, double e) {
     double A = 5.81 * e / e13 + 0.48 * cbrt(e) / (e13 * e1);
     double e3 = e * e * e;
     double B = e3 * Re * (0.95 + 0.61 * e3 / (e1 * e1));
+    return e1 * (cd0 / e13 + A + B);
+}
+__device__ __forceinline__ float drag_cd(float Re, float e) {
+    float e1 = 1.0f - e;
+    float e13 = e1 * e1 * e1;
+    float cd0 = 1.0f + 0.15f * powf(Re, 0.687f);
+    float A = 5.81f * e / e13 + 0.48f * cbrtf(e) / (e13 * e1);
+    float e3 = e * e * e;
+    float B = e3 * Re * (0.95f + 0.61f * e3 / (e1 * e1));
     return e1 * (cd0 / e13 + A + B);
 }
 
@@ -376,67 +454,58 @@ __global__ void k_force_drag(const BoxDev *__restrict__ boxes, const Tile *__res
         double *pf = Bx.pf[Bx.cur];
         const FT *rho = (const FT *)Bx.rho, *j = (const FT *)Bx.j, *eps = (const FT *)Bx.eps;
         const FT *fam = (const FT *)Bx.fam, *gradP = (const FT *)Bx.gradP;
+        const FT fb[3] = {(FT)ph.fb[0], (FT)ph.fb[1], (FT)ph.fb[2]};
         for (long long p = tl.begin + threadIdx.x; p < tl.end; p += blockDim.x) {
-            double wx[3], wy[3], wz[3];
+            const Support<FT> S = support_of<FT>(Bx, pf, p);
+            FT uf[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, ef = 0;
+            for_support(g, S, [&](long long c, FT W) {
+                const FT e = eps[c];
+                const FT s = FT(1) / (rho[c] * e);
 #pragma unroll
-            for (int o = 0; o < 3; ++o) {
-                wx[o] = pf[(PW0 + o) * cap + p];
-                wy[o] = pf[(PW0 + 3 + o) * cap + p];
-                wz[o] = pf[(PW0 + 6 + o) * cap + p];
-            }
-            int bx = containing_cell(pf[PXS0 * cap + p], g.n[0]);
-            int by = containing_cell(pf[(PXS0 + 1) * cap + p], g.n[1]);
-            int bz = containing_cell(pf[(PXS0 + 2) * cap + p], g.n[2]);
-            double uf[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, ef = 0.0;
-#pragma unroll 1
-            for (int oz = 0; oz < 3; ++oz) {
-                int z = wrap_axis(bz + oz - 1, g.n[2], g.per[2]);
-                if (z < 0) continue;
-                for (int oy = 0; oy < 3; ++oy) {
-                    int y = wrap_axis(by + oy - 1, g.n[1], g.per[1]);
-                    if (y < 0) continue;
-                    for (int ox = 0; ox < 3; ++ox) {
-                        int x = wrap_axis(bx + ox - 1, g.n[0], g.per[0]);
-                        if (x < 0) continue;
-                        long long c = cell_index(g, x, y, z);
-                        double W = wx[ox] * wy[oy] * wz[oz];
-                        double e = (double)eps[c], r = (double)rho[c];
-                        double s = 1.0 / (r * e);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            double F = e * ph.fb[a] + (double)fam[a * N + c];
-                            uf[a] += W * ((double)j[a * N + c] + 0.5 * F) * s;
-                            gp[a] += W * (double)gradP[a * N + c];
-                        }
-                        ef += W * e;
-                    }
+                for (int a = 0; a < 3; ++a) {
+                    const FT F = e * fb[a] + fam[a * N + c];
+                    uf[a] += W * (j[a * N + c] + FT(0.5) * F) * s;
+                    gp[a] += W * gradP[a * N + c];
                 }
-            }
-            double d = pf[PD * cap + p], rp = pf[PRHO * cap + p];
-            double V = PI_D / 6.0 * d * d * d;
-            double ep = 1.0 - ef;
-            double du[3], dun = 0.0;
+                ef += W * e;
+            });
+            const double d = pf[PD * cap + p], rp = pf[PRHO * cap + p];
+            const double V = PI_D / 6.0 * d * d * d;
+            const FT ep = FT(1) - ef;
+            FT du[3], dun = 0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                du[a] = uf[a] - pf[(PU + a) * cap + p];
+                du[a] = uf[a] - (FT)pf[(PU + a) * cap + p];
                 dun += du[a] * du[a];
             }
             dun = sqrt(dun);
-            double Re = ef * ph.rho_f * d * dun / ph.mu;
-            double coef = ph.drag ? 3.0 * PI_D * d * ph.mu * (1.0 - ep) * drag_cd(Re, ep) : 0.0;
+            const FT mu = (FT)ph.mu, dd = (FT)d;
+            const FT Re = ef * (FT)ph.rho_f * dd * dun / mu;
+            const FT coef = ph.drag ? FT(3.0 * PI_D) * dd * mu * (FT(1) - ep) * drag_cd(Re, ep) : FT(0);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                double Fd = coef * du[a];
-                double Fpr = ph.pressure ? -V * gp[a] : 0.0;
-                double Fg = (rp - ph.rho_f) * V * ph.g[a];  // gravity + buoyancy
-                pf[(PFD0 + a) * cap + p] = Fd;
-                pf[(PFH0 + a) * cap + p] = Fd + Fpr + pf[(PFA0 + a) * cap + p] + Fg;
+                const FT Fd = coef * du[a];
+                const FT Fpr = ph.pressure ? -(FT)V * gp[a] : FT(0);
+                const double Fg = (rp - ph.rho_f) * V * ph.g[a];  // gravity + buoyancy
+                pf[(PFD0 + a) * cap + p] = (double)Fd;
+                if (sizeof(FT) == 4) Bx.f32p[(3 + a) * cap + p] = (float)Fd;
+                pf[(PFH0 + a) * cap + p] = (double)Fd + (double)Fpr + pf[(PFA0 + a) * cap + p] + Fg;
             }
         }
     }
 }
 
 // ---- S5: reaction force density (Eq. forces_pf) -----------------------------------
+// particle force planes in the compute type: FP64 planes of the particle SoA,
+// or their FP32 copies in the low-precision forms
+template <typename FT> __device__ __forceinline__ const FT *force_planes(const BoxDev &B, const double *pf, int which);
+template <> __device__ __forceinline__ const double *force_planes<double>(const BoxDev &B, const double *pf, int which) {
+    return pf + (which ? PFD0 : PFA0) * B.cap;
+}
+template <> __device__ __forceinline__ const float *force_planes<float>(const BoxDev &B, const double *, int which) {
+    return B.f32p + (which ? 3 : 0) * B.cap;
+}
+
 // K6a: f_pf,am(c) = -sum_p W F_am
 template <typename FT>
 __global__ void k_reaction_am(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
@@ -446,17 +515,18 @@ __global__ void k_reaction_am(const BoxDev *__restrict__ boxes, const Tile *__re
         const Geom g = B.g;
         const long long N = g.ncell, cap = B.cap;
         const double *pf = B.pf[B.cur];
+        const FT *w = weights_of<FT>(B, pf), *Fa = force_planes<FT>(B, pf, 0);
         FT *fam = (FT *)B.fam;
         for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
-            double s[3] = {0, 0, 0};
-            gather27(g, c, B.cell_start, pf, cap, [&](int p, double W) {
-                s[0] += W * pf[PFA0 * cap + p];
-                s[1] += W * pf[(PFA0 + 1) * cap + p];
-                s[2] += W * pf[(PFA0 + 2) * cap + p];
+            FT s[3] = {0, 0, 0};
+            gather27(g, c, B.cell_start, w, cap, [&](int p, FT W) {
+                s[0] += W * Fa[p];
+                s[1] += W * Fa[cap + p];
+                s[2] += W * Fa[2 * cap + p];
             });
-            fam[c] = (FT)(-s[0]);
-            fam[N + c] = (FT)(-s[1]);
-            fam[2 * N + c] = (FT)(-s[2]);
+            fam[c] = -s[0];
+            fam[N + c] = -s[1];
+            fam[2 * N + c] = -s[2];
         }
     }
 }
@@ -472,24 +542,25 @@ __global__ void k_reaction_drag(const BoxDev *__restrict__ boxes, const Tile *__
         const Geom g = B.g;
         const long long N = g.ncell, cap = B.cap;
         const double *pf = B.pf[B.cur];
+        const FT *w = weights_of<FT>(B, pf), *Fd = force_planes<FT>(B, pf, 1);
         const FT *fam = (const FT *)B.fam;
         FT *acc = (FT *)B.acc, *fpf = (FT *)B.fpf;
-        const double inv_nint = B.ph.dt_sub;
+        const FT inv_nint = (FT)B.ph.dt_sub;
         for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
-            double s[3] = {0, 0, 0};
-            gather27(g, c, B.cell_start, pf, cap, [&](int p, double W) {
-                s[0] += W * pf[PFD0 * cap + p];
-                s[1] += W * pf[(PFD0 + 1) * cap + p];
-                s[2] += W * pf[(PFD0 + 2) * cap + p];
+            FT s[3] = {0, 0, 0};
+            gather27(g, c, B.cell_start, w, cap, [&](int p, FT W) {
+                s[0] += W * Fd[p];
+                s[1] += W * Fd[cap + p];
+                s[2] += W * Fd[2 * cap + p];
             });
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                double k = (double)fam[a * N + c] - s[a];
-                double v = first ? k : (double)acc[a * N + c] + k;
+                const FT k = fam[a * N + c] - s[a];
+                const FT v = first ? k : acc[a * N + c] + k;
                 if (last)
-                    fpf[a * N + c] = (FT)(v * inv_nint);
+                    fpf[a * N + c] = v * inv_nint;
                 else
-                    acc[a * N + c] = (FT)v;
+                    acc[a * N + c] = v;
             }
         }
     }

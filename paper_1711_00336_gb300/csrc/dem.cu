@@ -52,10 +52,10 @@ __device__ __forceinline__ void partner(const Phys &ph, const T n[3], T dist, T 
                                         double Tq[3], unsigned &nlim) {
     const T delta = sumr - dist;
     if (ph.contact && delta > T(0)) {
-        const T le = (T)log(ph.e_n);
-        const T pi2 = (T)(PI_D * PI_D);
-        const T k_n = m_ij * (pi2 + le * le) / (T)(ph.T_c * ph.T_c);
-        const T xi = T(-2) * le * sqrt(m_ij * k_n) / sqrt(pi2 + le * le);
+        // k_n and xi_n of Eqs. damping_to_stiffness / collision_time, solved
+        // for the given e_n and T_c: both proportional to m_ij
+        const T k_n = m_ij * (T)ph.kfac;
+        const T xi = m_ij * (T)ph.xfac;
         T ws[3], wx[3], ur[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) ws[a] = T(0.5) * di * wi[a] + wjh[a];
@@ -73,9 +73,9 @@ __device__ __forceinline__ void partner(const Phys &ph, const T n[3], T dist, T 
         const T ut_abs = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
         T Ft[3] = {0, 0, 0};
         if (ut_abs > T(0)) {
-            const T mag = fmin((T)ph.mu_c * Fn_abs, xi * ut_abs);
+            const T mag = fmin((T)ph.mu_c * Fn_abs, xi * ut_abs) / ut_abs;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) Ft[a] = -mag * ut[a] / ut_abs;
+            for (int a = 0; a < 3; ++a) Ft[a] = -mag * ut[a];
         }
         T nF[3];
         cross3(n, Ft, nF);
@@ -88,16 +88,16 @@ __device__ __forceinline__ void partner(const Phys &ph, const T n[3], T dist, T 
     const T h = dist - sumr;
     if (ph.lubrication && h < (T)ph.h_c) {
         const T hh = fmax(h, (T)ph.h_min);
-        const T L = log(dmean / (T(2) * hh));
+        const T r = dmean / hh;          // <d>/h
+        const T L = log(T(0.5) * r);     // ln(<d>/(2h))
         const T mu = (T)ph.mu;
-        T a_sq = T(1.5 * PI_D) * mu * dmean * (dmean / (T(4) * hh) + T(18.0 / 40.0) * L + T(9.0 / 84.0) * (hh / dmean) * L);
-        const T a_sh0 = T(0.5 * PI_D) * mu * dmean * L * (dmean + hh) * (dmean + hh) / T(4);
-        const T s = T(2) / (hh + dmean);
-        T a_sh = a_sh0 * s * s;
+        T a_sq = T(1.5 * PI_D) * mu * dmean * (T(0.25) * r + T(18.0 / 40.0) * L + T(9.0 / 84.0) * L / r);
+        // a_sh (2/(h+<d>))^2 = (pi/2) mu <d> ln(<d>/(2h))
+        T a_sh = T(0.5 * PI_D) * mu * dmean * L;
         a_sq = fmax(a_sq, T(0));
         a_sh = fmax(a_sh, T(0));
         if (ph.lub_limiter) {
-            const T cap = (T)ph.lub_cap * m_ij / (T)ph.dt_dem;
+            const T cap = m_ij * (T)ph.capfac;
             if (a_sq > cap) { a_sq = cap; ++nlim; }
             if (a_sh > cap) { a_sh = cap; ++nlim; }
         }
@@ -197,13 +197,14 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
         const BoxDev &Bx = boxes[tl.box];
         const double *xin = src_tmp ? Bx.xtmp : Bx.pf[Bx.cur];
         double *xout = src_tmp ? Bx.pf[Bx.cur] : Bx.xtmp;
-        const float4 *fin = Bx.xf[src_tmp];
-        float4 *fout = Bx.xf[1 - src_tmp];
+        const float4 *fin = Bx.xf[src_tmp], *vin = Bx.vf[src_tmp], *oin = Bx.of[src_tmp];
+        float4 *fout = Bx.xf[1 - src_tmp], *vout = Bx.vf[1 - src_tmp], *oout = Bx.of[1 - src_tmp];
         const double *pf = Bx.pf[Bx.cur];
         const long long cap = Bx.cap;
         const Geom g = Bx.g;
         const Phys &ph = Bx.ph;
         const double rng_extra = ph.lubrication ? fmax(ph.h_c, 0.0) : 0.0;
+        const float rng_extra_f = (float)rng_extra;
         const float Lf[3] = {(float)g.n[0], (float)g.n[1], (float)g.n[2]};
         for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
             double xi[3], ui[3], wi[3];
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                 ui[a] = xin[(3 + a) * cap + i];
                 wi[a] = xin[(6 + a) * cap + i];
             }
-            const float4 pi = fin[i];
+            const float4 pi = fin[i], vi = vin[i], oi = oin[i];
             const double di = pf[PD * cap + i];
             const double mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
             double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
@@ -225,44 +226,48 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                 const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
                 const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
                 const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
-                const float fr = 0.5f * (pi.w + pj.w) + (float)rng_extra + SCREEN_MARGIN;
-                if (!(fx * fx + fy * fy + fz * fz < fr * fr)) continue;
-                // exact separation in FP64
+                const float sumr_f = 0.5f * (pi.w + pj.w);
+                const float fr = sumr_f + rng_extra_f + SCREEN_MARGIN;
+                const float d2f = fx * fx + fy * fy + fz * fz;
+                if (!(d2f < fr * fr)) continue;
+                if (MIXED) {
+                    // away from contact: the whole pair in FP32 from the float copies
+                    const float distf = sqrtf(d2f);
+                    if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
+                        if (!(distf < sumr_f + rng_extra_f)) continue;
+                        const float4 vj = vin[j], oj = oin[j];
+                        const float inv = 1.0f / distf;
+                        const float n[3] = {fx * inv, fy * inv, fz * inv};
+                        const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
+                        const float uj[3] = {vj.x, vj.y, vj.z};
+                        const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
+                        const float m_ij = vi.w * vj.w / (vi.w + vj.w);
+                        const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
+                        partner<float>(ph, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, F, T, nlim);
+                        continue;
+                    }
+                }
+                // exact separation and forces in FP64
                 double dx[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) dx[a] = min_image(xin[a * cap + j] - xi[a], g.n[a], g.per[a]);
                 const double dist2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
                 const double dj = pf[PD * cap + j];
                 const double sumr = 0.5 * (di + dj);
-                const double range = sumr + rng_extra;
                 const double dist = sqrt(dist2);
-                if (!(dist < range) || dist == 0.0) continue;
+                if (!(dist < sumr + rng_extra) || dist == 0.0) continue;
                 const double mj = pf[PRHO * cap + j] * PI_D / 6.0 * dj * dj * dj;
                 const double m_ij = mi * mj / (mi + mj);
                 const double dmean = 2.0 * di * dj / (di + dj);
-                if (!MIXED || dist - sumr < H_NEAR) {
-                    const double n[3] = {dx[0] / dist, dx[1] / dist, dx[2] / dist};
-                    double uj[3], wjh[3];
+                const double inv = 1.0 / dist;
+                const double n[3] = {dx[0] * inv, dx[1] * inv, dx[2] * inv};
+                double uj[3], wjh[3];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        uj[a] = xin[(3 + a) * cap + j];
-                        wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
-                    }
-                    partner<double>(ph, n, dist, sumr, ui, wi, di, uj, wjh, m_ij, dmean, F, T, nlim);
-                } else {
-                    const float inv = 1.0f / (float)dist;
-                    const float n[3] = {(float)dx[0] * inv, (float)dx[1] * inv, (float)dx[2] * inv};
-                    float uif[3], wif[3], uj[3], wjh[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        uif[a] = (float)ui[a];
-                        wif[a] = (float)wi[a];
-                        uj[a] = (float)xin[(3 + a) * cap + j];
-                        wjh[a] = 0.5f * (float)dj * (float)xin[(6 + a) * cap + j];
-                    }
-                    partner<float>(ph, n, (float)dist, (float)sumr, uif, wif, (float)di, uj, wjh, (float)m_ij,
-                                   (float)dmean, F, T, nlim);
+                for (int a = 0; a < 3; ++a) {
+                    uj[a] = xin[(3 + a) * cap + j];
+                    wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
                 }
+                partner<double>(ph, n, dist, sumr, ui, wi, di, uj, wjh, m_ij, dmean, F, T, nlim);
             }
             // walls: the faces of every non-periodic axis (m_ij = m_i, <d> = 2 d_i)
             const double zero[3] = {0, 0, 0};
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
             }
             // Eq. particle_motion, semi-implicit Euler with I = m d^2 / 10
             const double I = mi * di * di / 10.0;
-            double d2 = 0.0, xn3[3];
+            double d2 = 0.0, xn3[3], un3[3], wn3[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const double Ft = pf[(PFH0 + a) * cap + i] + F[a];
@@ -296,6 +301,8 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                     if (xn >= L) xn -= L;
                 }
                 xn3[a] = xn;
+                un3[a] = un;
+                wn3[a] = wn;
                 xout[a * cap + i] = xn;
                 xout[(3 + a) * cap + i] = un;
                 xout[(6 + a) * cap + i] = wn;
@@ -303,6 +310,8 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                 d2 += dd * dd;
             }
             fout[i] = make_float4((float)xn3[0], (float)xn3[1], (float)xn3[2], pi.w);
+            vout[i] = make_float4((float)un3[0], (float)un3[1], (float)un3[2], vi.w);
+            oout[i] = make_float4((float)wn3[0], (float)wn3[1], (float)wn3[2], 0.f);
             if (d2 > ph.skin_half2) atomicOr(Bx.status, ST_SKIN);
             if (!(d2 < 1e30)) atomicOr(Bx.status, ST_NAN);
             if (nlim) atomicAdd(&Bx.counters[CNT_LUB_LIMITED], (unsigned long long)nlim);

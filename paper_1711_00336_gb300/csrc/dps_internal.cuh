@@ -139,6 +139,8 @@ struct Phys {
     double eps_min;
     double dt_sub, dt_dem;
     double skin;         // Verlet skin (dx)
+    double kfac, xfac;   // k_n = m_ij kfac, xi_n = m_ij xfac (Eqs. damping_to_stiffness, collision_time)
+    double capfac;       // lubrication cap = m_ij capfac
     double skin_half2;   // (skin / 2)^2: largest displacement between two sorts
     int n_int, n_dem;
     int drag, pressure, added_mass, lubrication, contact, lub_limiter;

@@ -67,15 +67,21 @@ __device__ __forceinline__ void collide(CT f[Q], CT eps, CT Fx, CT Fy, CT Fz, CT
     rho_out = rho;
 }
 
-// K1 body for one cell
+// K1 body for one cell: load the 19 populations (AA parity PAR), relax them
+// (Eq. LBM_Equation, same algebra as collide()) and store each opposite pair
+// as soon as it is computed, which keeps few values live.
 template <typename ST, typename FT, typename CT, int PAR>
 __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const FT *__restrict__ eps,
                                                     const FT *__restrict__ fpf, const Geom &g, long long c, CT fbx,
                                                     CT fby, CT fbz, CT omega, CT kf, int *status) {
+    constexpr bool DEV = Store<ST>::shifted;
     const long long N = g.ncell;
-    int ix, iy, iz;
-    cell_coords(g, c, ix, iy, iz);
-    NbDelta D = neighbour_deltas(g, ix, iy, iz);
+    NbDelta D;
+    if (PAR) {
+        int ix, iy, iz;
+        cell_coords(g, c, ix, iy, iz);
+        D = neighbour_deltas(g, ix, iy, iz);
+    }
     CT f[Q];
     load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
     const CT e = (CT)eps[c];
@@ -83,10 +89,45 @@ __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const 
     const CT Fx = (CT)fpf[c] + e * fbx;
     const CT Fy = (CT)fpf[N + c] + e * fby;
     const CT Fz = (CT)fpf[2 * N + c] + e * fbz;
-    CT rho;
-    collide<CT, Store<ST>::shifted>(f, e, Fx, Fy, Fz, omega, kf, rho);
+    CT s = f[0], jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+        s += f[k] + f[k + 9];
+        const CT d = f[k] - f[k + 9];
+        if (CX(k) != 0) jx += CX(k) * d;
+        if (CY(k) != 0) jy += CY(k) * d;
+        if (CZ(k) != 0) jz += CZ(k) * d;
+    }
+    const CT rho = DEV ? CT(1) + s : s;
     if (!(rho > CT(0)) || !(rho < CT(1e30))) atomicOr(status, ST_NAN);
-    store_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
+    const CT ir = CT(1) / rho;
+    const CT ux = (jx + CT(0.5) * Fx) * ir;  // Eq. MacVel
+    const CT uy = (jy + CT(0.5) * Fy) * ir;
+    const CT uz = (jz + CT(0.5) * Fz) * ir;
+    const CT ie = CT(1) / e;
+    const CT uu = ux * ux + uy * uy + uz * uz;
+    const CT uF = ux * Fx + uy * Fy + uz * Fz;
+    const CT om1 = CT(1) - omega;
+    const CT b2 = CT(-1.5) * uu * ie;
+    const CT e0 = DEV ? omega * (s + rho * b2) : omega * rho * (CT(1) + b2);
+    const CT f0 = CT(-3) * kf * uF * ie;
+    const CT k1 = omega * rho * CT(4.5) * ie, k2 = CT(9) * kf * ie;
+    const CT k3 = CT(3) * omega * rho, k4 = CT(3) * kf;
+    {
+        const CT v = om1 * f[0] + (CT)WQ(0) * (e0 + f0);
+        Store<ST>::store(pdf + (unsigned)c, v);
+    }
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+        const CT w = (CT)WQ(k);
+        CT cu = 0, cF = 0;
+        if (CX(k) != 0) { cu += CX(k) * ux; cF += CX(k) * Fx; }
+        if (CY(k) != 0) { cu += CY(k) * uy; cF += CY(k) * Fy; }
+        if (CZ(k) != 0) { cu += CZ(k) * uz; cF += CZ(k) * Fz; }
+        const CT E = w * (e0 + f0 + cu * (k1 * cu + k2 * cF));
+        const CT O = w * (k3 * cu + k4 * cF);
+        store_pair<ST, CT, PAR>(pdf, N, c, D, k, om1 * f[k] + (E + O), om1 * f[k + 9] + (E - O));
+    }
 }
 
 template <typename CT> __device__ __forceinline__ CT pick(double d, float f);
@@ -94,8 +135,8 @@ template <> __device__ __forceinline__ double pick<double>(double d, float) { re
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 // K1: every cell tile of every box, AA parity PAR (common to the batch)
-template <typename ST, typename FT, typename CT, int PAR>
-__global__ void __launch_bounds__(128, sizeof(CT) == 8 ? 2 : 4) k_collide_stream(const BoxDev *__restrict__ boxes,
+template <typename ST, typename FT, typename CT, int PAR, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__restrict__ boxes,
                                                            const Tile *__restrict__ tiles, int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
@@ -262,14 +303,29 @@ static int grid_for(long long n, int block) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// variant: register budget of K1 (blocks of 128 threads per SM the compiler
+// must fit); chosen by the batch autotuner
 template <typename ST, typename FT, typename CT>
-void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, int parity, int grid, int block,
-                           cudaStream_t s) {
-    if (block > 128) block = 128;  // register budget of __launch_bounds__(128, 4)
-    if (parity)
-        k_collide_stream<ST, FT, CT, 1><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, int parity, int variant, int grid,
+                           int block, cudaStream_t s) {
+    block = 128;
+    if (sizeof(CT) == 8) variant = 0;  // FP64: one register-heavy variant
+#define DPS_K1(MB)                                                                             \
+    do {                                                                                       \
+        if (parity)                                                                            \
+            k_collide_stream<ST, FT, CT, 1, MB><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
+        else                                                                                   \
+            k_collide_stream<ST, FT, CT, 0, MB><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
+    } while (0)
+    if (sizeof(CT) == 8)
+        DPS_K1(2);
+    else if (variant == 1)
+        DPS_K1(3);
+    else if (variant == 2)
+        DPS_K1(5);
     else
-        k_collide_stream<ST, FT, CT, 0><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+        DPS_K1(4);
+#undef DPS_K1
 }
 
 template <typename ST, typename FT, typename CT>
@@ -304,7 +360,7 @@ void launch_pdf_import(void *pdf, long long N, const double *in, cudaStream_t s)
 
 // explicit instantiations for the three precision forms
 #define DPS_LBM_INST(ST, FT, CT)                                                                             \
-    template void launch_collide_stream<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t); \
+    template void launch_collide_stream<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t); \
     template void launch_moments<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 DPS_LBM_INST(double, double, double)
 DPS_LBM_INST(float, float, float)

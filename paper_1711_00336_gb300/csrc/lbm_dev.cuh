@@ -8,7 +8,7 @@ namespace dps {
 
 // linear-index deltas to the -1/+1 neighbour along each axis; INV marks a
 // neighbour beyond a wall.
-// (ncell < 2^30, so no real delta can equal INV)
+// (ncell <= 2^27: 19 planes of offsets fit in 32 bits and no real delta equals INV)
 constexpr int INV = (1 << 30);
 
 struct NbDelta {
@@ -50,7 +50,7 @@ __device__ __forceinline__ void load_pdfs(const ST *__restrict__ pdf, long long 
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (PAR == 0 || q == 0) {
-            f[q] = Store<ST>::load(pdf + (long long)q * N + c);
+            f[q] = Store<ST>::load(pdf + (unsigned)(q * (unsigned)N + (unsigned)c));
         } else {
             // f_q(x) was written by the upstream cell x - c_q into plane opp(q);
             // across a wall it is the own cell's bounced value in plane q.
@@ -60,9 +60,9 @@ __device__ __forceinline__ void load_pdfs(const ST *__restrict__ pdf, long long 
                 dm = (dx == INV || dy == INV || dz == INV) ? INV : dx + dy + dz;
             }
             if (dm != INV)
-                f[q] = Store<ST>::load(pdf + (long long)OPP(q) * N + c + dm);
+                f[q] = Store<ST>::load(pdf + (unsigned)(OPP(q) * (unsigned)N + (unsigned)c + (unsigned)dm));
             else
-                f[q] = Store<ST>::load(pdf + (long long)q * N + c);
+                f[q] = Store<ST>::load(pdf + (unsigned)(q * (unsigned)N + (unsigned)c));
         }
     }
 }
@@ -75,14 +75,31 @@ __device__ __forceinline__ void store_pdfs(ST *__restrict__ pdf, long long N, lo
         if (q == 0) {
             Store<ST>::store(pdf + c, f[0]);
         } else if (PAR == 0) {
-            Store<ST>::store(pdf + (long long)OPP(q) * N + c, f[q]);
+            Store<ST>::store(pdf + (unsigned)(OPP(q) * (unsigned)N + (unsigned)c), f[q]);
         } else {
             const int dp = nb_delta(D, q);
             if (dp != INV)
-                Store<ST>::store(pdf + (long long)q * N + c + dp, f[q]);
+                Store<ST>::store(pdf + (unsigned)(q * (unsigned)N + (unsigned)c + (unsigned)dp), f[q]);
             else  // bounce back: returns to this cell with velocity -c_q
-                Store<ST>::store(pdf + (long long)OPP(q) * N + c, f[q]);
+                Store<ST>::store(pdf + (unsigned)(OPP(q) * (unsigned)N + (unsigned)c), f[q]);
         }
+    }
+}
+
+// store the post-collision pair (k, k+9) under the AA parity
+template <typename ST, typename CT, int PAR>
+__device__ __forceinline__ void store_pair(ST *__restrict__ pdf, long long N, long long c, const NbDelta &D, int k,
+                                           CT vk, CT vo) {
+    const int o = k + 9;
+    if (PAR == 0) {
+        Store<ST>::store(pdf + (unsigned)(o * (unsigned)N + (unsigned)c), vk);
+        Store<ST>::store(pdf + (unsigned)(k * (unsigned)N + (unsigned)c), vo);
+    } else {
+        const int dk = nb_delta(D, k), d_o = nb_delta(D, o);
+        if (dk != INV) Store<ST>::store(pdf + (unsigned)(k * (unsigned)N + (unsigned)c + (unsigned)dk), vk);
+        else Store<ST>::store(pdf + (unsigned)(o * (unsigned)N + (unsigned)c), vk);
+        if (d_o != INV) Store<ST>::store(pdf + (unsigned)(o * (unsigned)N + (unsigned)c + (unsigned)d_o), vo);
+        else Store<ST>::store(pdf + (unsigned)(k * (unsigned)N + (unsigned)c), vo);
     }
 }
 

@@ -53,6 +53,7 @@ struct dps_server_s {
     std::map<int64_t, Req *> all;
     std::vector<Req *> running;
     bool stop = false;
+    int admitting = 0;  // requests taken from the queue, not yet in `running`
     int64_t next_id = 1;
     clk::time_point t0;
     dps_serve_stats st{};
@@ -103,6 +104,7 @@ struct dps_server_s {
             }
             queue.pop_front();
             st.queued--;
+            admitting++;
             lk.unlock();
             int box = -1;
             int rc = dps_batch_add_box(batch, q->r.n, q->r.periodic, q->r.tau, q->r.rho_f, q->r.np, &box);
@@ -111,6 +113,7 @@ struct dps_server_s {
                                              q->rho.data());
             if (rc == DPS_OK) rc = dps_batch_set_closure(batch, box, &q->r.closure);
             lk.lock();
+            admitting--;
             if (rc != DPS_OK) {
                 if (box >= 0) {
                     lk.unlock();
@@ -294,7 +297,7 @@ int dps_serve_cancel(dps_server s, int64_t id) {
 int dps_serve_wait_idle(dps_server s, double timeout_s) {
     if (!s) return DPS_ERR_ARG;
     std::unique_lock<std::mutex> lk(s->mu);
-    auto idle = [&] { return s->queue.empty() && s->running.empty(); };
+    auto idle = [&] { return s->queue.empty() && s->running.empty() && s->admitting == 0; };
     if (timeout_s < 0) {
         s->cv.wait(lk, idle);
         return DPS_OK;

@@ -489,12 +489,14 @@ class Batch:
         return u
 
     def tuning(self):
-        c = (ctypes.c_int * 4)()
+        """[cell threads/block, cells/tile, particle threads/block, particles/tile, collide variant]"""
+        c = (ctypes.c_int * 5)()
         self._ck(lib().dps_batch_get_tuning(self.h, c))
         return list(c)
 
     def set_tuning(self, cfg):
-        self._ck(lib().dps_batch_set_tuning(self.h, (ctypes.c_int * 4)(*cfg)))
+        cfg = list(cfg) + [0] * (5 - len(cfg))
+        self._ck(lib().dps_batch_set_tuning(self.h, (ctypes.c_int * 5)(*cfg)))
 
     def autotune(self, steps=5):
         ms = np.zeros(1)
