@@ -214,7 +214,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--forms", default="f32,f16s", help="extra precision forms to time (comma list, '' for none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--suite", default="", help="precision,accuracy,batch,serve: measure the forms instead")
     args = ap.parse_args()
+    if args.suite:
+        run_suite(args)
+        return
     wl = workloads.wall_suspension()
     ncell = int(np.prod(wl["n"]))
     if args.impl == "reference":
@@ -304,6 +308,204 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+
+
+# ---------------------------------------------------------------------------
+# suite: the precision, batching and serving forms (python bench.py --suite)
+# ---------------------------------------------------------------------------
+def _settling_closure(dps, wl, d):
+    return dps.closure(g=wl["g"], h_c=d, e_n=0.88, mu_c=0.25, T_c=0.5, h_min=1e-5, C_am=0.5, n_int=2, n_dem=10,
+                       lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5, fb_mode=1)
+
+
+def suite_precision(dps, steps=5, warmup=2, L=256, d=1.5, eps_list=(0.05, 0.2, 0.4)):
+    """Triply periodic settling at L^3 in the three precision forms: device
+    time per step (CUDA events), MLUPS and particle-steps/s."""
+    import torch
+    out = []
+    for eps in eps_list:
+        wl = workloads.settling_box(L=L, eps=eps, d=d, seed=int(eps * 100))
+        for prec in ("f64", "f32", "f16s"):
+            dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], prec, max_particles=len(wl["x"]))
+            dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+            dom.set_closure(_settling_closure(dps, wl, d))
+            dom.step(warmup)
+            dom.set_timing(True)
+            dom.step(1)
+            dom.get_timing(reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(dom.stream)
+            for _ in range(steps):
+                dom.step_async(1)
+                dom.collect_timing()
+            e1.record(dom.stream)
+            dom.check()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            ph = dom.get_timing(reset=True)
+            st = dom.stats()
+            n = int(np.prod(wl["n"]))
+            out.append({"workload": wl["name"], "precision": prec, "particles": len(wl["x"]), "ms_per_step": ms,
+                        "MLUPS": n / (ms * 1e-3) / 1e6, "particle_steps_per_s": len(wl["x"]) / (ms * 1e-3),
+                        "phases_ms": {k: v["ms"] / steps for k, v in ph.items()}, "u_pS_z": float(st["u_pS"][2]),
+                        "eps_clamps": int(st["n_eps_clamp"]), "status": int(st["status"])})
+            dom.close()
+            print(json.dumps({"suite": "precision", **out[-1]}), flush=True)
+    return out
+
+
+def suite_accuracy(dps, steps=2000, L=64, d=1.5, eps_list=(0.05, 0.2, 0.4)):
+    """Low-precision forms against the FP64 path (itself pinned to the CPU
+    oracle) at 64^3: velocity-field relative L2 error and <u_pS> error."""
+    out = []
+    for eps in eps_list:
+        wl = workloads.settling_box(L=L, eps=eps, d=d, seed=int(eps * 100) + 1)
+        res = {}
+        for prec in ("f64", "f32", "f16s"):
+            dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], prec, max_particles=len(wl["x"]))
+            dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+            dom.set_closure(_settling_closure(dps, wl, d))
+            dom.step(steps)
+            f = dom.read_fields(("u_f",))["u_f"]
+            res[prec] = (f, float(dom.stats()["u_pS"][2]))
+            dom.close()
+        ref_f, ref_u = res["f64"]
+        for prec in ("f32", "f16s"):
+            f, u = res[prec]
+            line = {"suite": "accuracy", "workload": wl["name"], "steps": steps, "precision": prec,
+                    "u_f_rel_l2": float(np.linalg.norm(f - ref_f) / np.linalg.norm(ref_f)),
+                    "u_pS_z": u, "u_pS_z_f64": ref_u, "u_pS_rel_err": abs(u - ref_u) / abs(ref_u)}
+            out.append(line)
+            print(json.dumps(line), flush=True)
+    return out
+
+
+def _batch_boxes(seed=7, count=64):
+    rng = np.random.default_rng(seed)
+    boxes = []
+    for k in range(count):
+        L = int(round(np.exp(rng.uniform(np.log(24), np.log(96)))))
+        eps = rng.uniform(0.01, 0.45)
+        d = rng.uniform(0.8, 1.5)
+        boxes.append(workloads.settling_box(L=L, eps=eps, d=d, seed=seed * 1000 + k))
+    return boxes
+
+
+def suite_batch(dps, steps=20, count=64):
+    """64 uneven periodic boxes: FP32 batch (one launch per phase, autotuned)
+    against the plain FP64 method stepping every box as its own domain."""
+    import torch
+    boxes = _batch_boxes(count=count)
+    cells = sum(int(np.prod(b["n"])) for b in boxes)
+    parts = sum(len(b["x"]) for b in boxes)
+    B = dps.Batch("f32")
+    ids = []
+    for wl in boxes:
+        b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
+        B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
+        B.set_closure(b, _settling_closure(dps, wl, wl["d"][0]))
+        ids.append(b)
+    tune_ms = B.autotune(steps=3)
+    B.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.step(steps)
+    torch.cuda.synchronize()
+    ms_b = (time.perf_counter() - t0) / steps * 1e3
+    ub = [B.particle_mean(b)[2] for b in ids]
+    cfg = B.tuning()
+    B.close()
+    # plain FP64 method, box after box (same steps)
+    ms_p = 0.0
+    up = []
+    for wl in boxes:
+        dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
+        dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+        dom.set_closure(_settling_closure(dps, wl, wl["d"][0]))
+        dom.step(4 * 12 + 2)  # same history as the batch: 12 tuning candidates x (1 + 3) steps, then 2
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dom.step(steps)
+        torch.cuda.synchronize()
+        ms_p += (time.perf_counter() - t0) / steps * 1e3
+        up.append(dom.read_particles()["u"][:, 2].mean())
+        dom.close()
+    err = [abs(a - b) / max(abs(b), 1e-12) for a, b in zip(ub, up)]
+    line = {"suite": "batch", "boxes": count, "cells": cells, "particles": parts, "steps": steps,
+            "f32_batch_ms_per_step": ms_b, "f32_batch_MLUPS": cells / (ms_b * 1e-3) / 1e6,
+            "f64_plain_ms_per_step": ms_p, "f64_plain_MLUPS": cells / (ms_p * 1e-3) / 1e6,
+            "speedup": ms_p / ms_b, "tuning": cfg, "autotune_best_ms": tune_ms,
+            "mean_up_rel_err_vs_f64_median": float(np.median(err)), "max": float(np.max(err))}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def suite_serve(dps, n_req=24, rate=20.0, cap=2000, seed=11):
+    """Poisson-arriving settling requests (edge log-uniform 32..160, eps
+    U(0.01, 0.45), d = 1, FP32) on the continuous-batching server; every 20th
+    request is rerun alone with the plain FP64 method."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n_req):
+        L = int(round(np.exp(rng.uniform(np.log(32), np.log(160)))))
+        eps = rng.uniform(0.01, 0.45)
+        reqs.append(workloads.settling_box(L=L, eps=eps, d=1.0, seed=seed * 1000 + k))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    S = dps.Server("f32", max_boxes=64, hbm_reserve_bytes=16 << 30, chunk_steps=50)
+    t0 = time.perf_counter()
+    ids = []
+    for wl, ta in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        ids.append(S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"],
+                            _settling_closure(dps, wl, 1.0), max_steps=cap, window=500, rel_tol=1e-3))
+    S.wait_idle(3600)
+    res = [S.poll(i) for i in ids]
+    st = S.stats()
+    S.close()
+    lat = [r["t_end"] - r["t_submit"] for r in res]
+    errs = []
+    for k in range(0, n_req, 20):
+        wl = reqs[k]
+        dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
+        dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+        dom.set_closure(_settling_closure(dps, wl, 1.0))
+        steps = res[k]["steps"]
+        w, acc = 500, np.zeros(3)
+        dom.step(steps - w)
+        for _ in range(w // 50):
+            dom.step(50)
+            acc += dom.read_particles()["u"].mean(0)
+        dom.close()
+        um = acc / (w // 50)
+        errs.append(abs(res[k]["up_mean"][2] - um[2]) / abs(um[2]))
+    line = {"suite": "serve", "requests": n_req, "rate_per_s": rate, "cap_steps": cap,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "aggregate_MLUPS": st["cell_updates"] / st["busy_s"] / 1e6 if st["busy_s"] > 0 else None,
+            "completed": st["completed"], "failed": st["failed"], "peak_boxes": st["peak_boxes"],
+            "capped": int(sum(r["capped"] for r in res)),
+            "f64_rerun_up_rel_err": [float(e) for e in errs]}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_suite(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1711_00336_gb300 import build, dps
+    build.build()
+    which = args.suite.split(",")
+    if "precision" in which:
+        suite_precision(dps)
+    if "accuracy" in which:
+        suite_accuracy(dps)
+    if "batch" in which:
+        suite_batch(dps)
+    if "serve" in which:
+        suite_serve(dps)
 
 
 if __name__ == "__main__":
