@@ -241,6 +241,8 @@ typedef struct {
 } dps_batch_desc;
 
 int dps_batch_create(const dps_batch_desc *desc, dps_batch *out);
+/* message of the last failing call on b */
+const char *dps_batch_last_error(dps_batch b);
 int dps_batch_destroy(dps_batch b);
 /* add a box (fluid at rest, no particles); *box receives its id */
 int dps_batch_add_box(dps_batch b, const int n[3], const int periodic[3], double tau, double rho_f,

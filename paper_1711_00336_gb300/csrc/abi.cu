@@ -40,6 +40,7 @@ void launch_bsort_flip(BoxDev *, int, int, cudaStream_t);
 void launch_end_step(BoxDev *, int, cudaStream_t);
 void launch_bscan(const BoxDev *, int, const Tile *, int, cudaStream_t);
 int scan_tile_cells();
+void brick_tiles(int, const int *, std::vector<Tile> &);
 template <typename FT>
 void launch_eps(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
@@ -118,9 +119,9 @@ struct Batch {
     int table_cap = 0;
     BoxDev *d_table = nullptr;
     std::vector<void *> allocs;  // batch-level buffers (table, tiles)
-    Tile *d_cell = nullptr, *d_part = nullptr, *d_scan = nullptr;
-    int n_cell = 0, n_part = 0, n_scan = 0;
-    size_t cap_cell = 0, cap_part = 0, cap_scan = 0;
+    Tile *d_cell = nullptr, *d_part = nullptr, *d_scan = nullptr, *d_brick = nullptr;
+    int n_cell = 0, n_part = 0, n_scan = 0, n_brick = 0;
+    size_t cap_cell = 0, cap_part = 0, cap_scan = 0, cap_brick = 0;
     Tuning tune;
     bool tuned = false;
     int n_int = 0, n_dem = 0;
@@ -338,7 +339,7 @@ static int push_layout(Batch *B) {
         B->table_cap = cap;
     }
     std::vector<BoxDev> tab(nb);
-    std::vector<Tile> cell, part, scan;
+    std::vector<Tile> cell, part, scan, brick;
     const long long ST = scan_tile_cells();
     for (int k = 0; k < nb; ++k) {
         BoxHost *h = B->boxes[k];
@@ -351,11 +352,13 @@ static int push_layout(Batch *B) {
             part.push_back(Tile{k, 0, p, std::min(np, p + B->tune.part_tile)});
         int idx = 0;
         for (long long c = 0; c < N; c += ST) scan.push_back(Tile{k, idx++, c, std::min(N, c + ST)});
+        brick_tiles(k, h->d.g.n, brick);
     }
     int rc;
     if ((rc = ensure_buf(B, &B->d_cell, &B->cap_cell, cell.size()))) return rc;
     if ((rc = ensure_buf(B, &B->d_part, &B->cap_part, part.size()))) return rc;
     if ((rc = ensure_buf(B, &B->d_scan, &B->cap_scan, scan.size()))) return rc;
+    if ((rc = ensure_buf(B, &B->d_brick, &B->cap_brick, brick.size()))) return rc;
     if (nb) CKB(B, cudaMemcpyAsync(B->d_table, tab.data(), sizeof(BoxDev) * nb, cudaMemcpyHostToDevice, B->stream));
     if (!cell.empty())
         CKB(B, cudaMemcpyAsync(B->d_cell, cell.data(), sizeof(Tile) * cell.size(), cudaMemcpyHostToDevice, B->stream));
@@ -363,10 +366,13 @@ static int push_layout(Batch *B) {
         CKB(B, cudaMemcpyAsync(B->d_part, part.data(), sizeof(Tile) * part.size(), cudaMemcpyHostToDevice, B->stream));
     if (!scan.empty())
         CKB(B, cudaMemcpyAsync(B->d_scan, scan.data(), sizeof(Tile) * scan.size(), cudaMemcpyHostToDevice, B->stream));
+    if (!brick.empty())
+        CKB(B, cudaMemcpyAsync(B->d_brick, brick.data(), sizeof(Tile) * brick.size(), cudaMemcpyHostToDevice, B->stream));
     CKB(B, cudaStreamSynchronize(B->stream));
     B->n_cell = (int)cell.size();
     B->n_part = (int)part.size();
     B->n_scan = (int)scan.size();
+    B->n_brick = (int)brick.size();
     B->dev_order = B->boxes;
     B->layout_dirty = false;
     invalidate_graph(B);
@@ -405,16 +411,16 @@ static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub) {
     tend(B, PH_SORT, 3 + 5 * pl + 1);
     tbegin(B);
     if (B->fel == 8)
-        launch_eps<double>(T, B->d_cell, B->n_cell, grid_of(B->n_cell), u.cell_block, B->stream);
+        launch_eps<double>(T, B->d_brick, B->n_brick, grid_of(B->n_brick), 256, B->stream);
     else
-        launch_eps<float>(T, B->d_cell, B->n_cell, grid_of(B->n_cell), u.cell_block, B->stream);
+        launch_eps<float>(T, B->d_brick, B->n_brick, grid_of(B->n_brick), 256, B->stream);
     tend(B, PH_EPS, 1);
 }
 
 static void enqueue_step(Batch *B) {
     const BoxDev *T = B->d_table;
     const Tuning &u = B->tune;
-    const int gc = grid_of(B->n_cell), gp = grid_of(B->n_part);
+    const int gc = grid_of(B->n_cell), gp = grid_of(B->n_part), gb = grid_of(B->n_brick);
     const int pl = B->n_part > 0;
     const bool f64 = B->fel == 8;
     cudaStream_t s = B->stream;
@@ -439,8 +445,8 @@ static void enqueue_step(Batch *B) {
         }
         tend(B, PH_FAM, pl);
         tbegin(B);
-        if (f64) launch_reaction_am<double>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
-        else launch_reaction_am<float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
+        if (f64) launch_reaction_am<double>(T, B->d_brick, B->n_brick, gb, 256, s);
+        else launch_reaction_am<float>(T, B->d_brick, B->n_brick, gb, 256, s);
         tend(B, PH_RAM, 1);
         tbegin(B);
         if (pl) {
@@ -450,9 +456,9 @@ static void enqueue_step(Batch *B) {
         tend(B, PH_FDRAG, pl);
         tbegin(B);
         if (f64)
-            launch_reaction_drag<double>(T, B->d_cell, B->n_cell, k == 0, k == B->n_int - 1, gc, u.cell_block, s);
+            launch_reaction_drag<double>(T, B->d_brick, B->n_brick, k == 0, k == B->n_int - 1, gb, 256, s);
         else
-            launch_reaction_drag<float>(T, B->d_cell, B->n_cell, k == 0, k == B->n_int - 1, gc, u.cell_block, s);
+            launch_reaction_drag<float>(T, B->d_brick, B->n_brick, k == 0, k == B->n_int - 1, gb, 256, s);
         tend(B, PH_RDRAG, 1);
         tbegin(B);
         if (pl)
@@ -1284,6 +1290,8 @@ int dps_batch_create(const dps_batch_desc *desc, dps_batch *out) {
     *out = b;
     return DPS_OK;
 }
+
+const char *dps_batch_last_error(dps_batch b) { return b ? b->B.err.c_str() : g_create_err.c_str(); }
 
 int dps_batch_destroy(dps_batch b) {
     if (!b) return DPS_ERR_ARG;

@@ -9,6 +9,8 @@
 //     each lattice cell: no atomics, a fixed summation order.
 //  S4 particle forces (Table 1): added mass; pressure gradient, drag, gravity.
 //  S5 reaction force density (Eq. forces_pf) as the same 27-cell gather.
+#include <vector>
+
 #include "box.cuh"
 
 namespace dps {
@@ -304,16 +306,98 @@ template <> __device__ __forceinline__ const double *weights_of<double>(const Bo
 }
 template <> __device__ __forceinline__ const float *weights_of<float>(const BoxDev &B, const double *) { return B.pwf; }
 
+// ---- brick-tiled gathers ---------------------------------------------------------
+// A brick is a block of up to 8x8x8 cells of one box (Tile::begin and
+// Tile::end pack its origin and extent, 21 bits per axis).  The block first
+// stages the particle ranges of the brick's cells and their one-cell halo in
+// shared memory (one cell_start pair per halo cell instead of 27 per cell),
+// then every thread gathers over the 27 neighbours of its cells in a fixed
+// order: o_z, o_y, o_x ascending, then the sorted order inside a cell.
+constexpr int BRICK = 8;
+constexpr int HALO = BRICK + 2;
+constexpr int HALO3 = HALO * HALO * HALO;
+
+__host__ __device__ inline long long brick_pack(int x, int y, int z) {
+    return (long long)x | ((long long)y << 21) | ((long long)z << 42);
+}
+__device__ __forceinline__ void brick_unpack(long long v, int &x, int &y, int &z) {
+    x = (int)(v & 0x1FFFFF);
+    y = (int)((v >> 21) & 0x1FFFFF);
+    z = (int)((v >> 42) & 0x1FFFFF);
+}
+
+struct BrickRanges {
+    int s[HALO3], e[HALO3];
+};
+
+// stage the particle ranges of the halo cells of brick (ox,oy,oz)+[0,ex)x[0,ey)x[0,ez)
+__device__ __forceinline__ void stage_ranges(const BoxDev &B, int ox, int oy, int oz, BrickRanges &R) {
+    const Geom &g = B.g;
+    for (int h = threadIdx.x; h < HALO3; h += blockDim.x) {
+        const int hx = h % HALO, hy = (h / HALO) % HALO, hz = h / (HALO * HALO);
+        const int x = wrap_axis(ox + hx - 1, g.n[0], g.per[0]);
+        const int y = wrap_axis(oy + hy - 1, g.n[1], g.per[1]);
+        const int z = wrap_axis(oz + hz - 1, g.n[2], g.per[2]);
+        if (x < 0 || y < 0 || z < 0) {
+            R.s[h] = R.e[h] = 0;
+        } else {
+            const long long n = cell_index(g, x, y, z);
+            R.s[h] = B.cell_start[n];
+            R.e[h] = B.cell_start[n + 1];
+        }
+    }
+}
+
+// gather over the 27 halo neighbours of brick cell (lx,ly,lz) with weights w
+template <typename WT, typename Fn>
+__device__ __forceinline__ void gather27_staged(const BrickRanges &R, int lx, int ly, int lz, const WT *__restrict__ w,
+                                                long long cap, Fn &&fn) {
+#pragma unroll 1
+    for (int oz = -1; oz <= 1; ++oz) {
+        const WT *wz = w + (6 + 1 - oz) * cap;
+#pragma unroll 1
+        for (int oy = -1; oy <= 1; ++oy) {
+            const WT *wy = w + (3 + 1 - oy) * cap;
+            const int hrow = (lz + 1 + oz) * HALO * HALO + (ly + 1 + oy) * HALO + (lx + 1);
+#pragma unroll
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int h = hrow + ox;
+                const int s = R.s[h], e = R.e[h];
+                const WT *wx = w + (1 - ox) * cap;
+                for (int p = s; p < e; ++p) fn(p, wx[p] * wy[p] * wz[p]);
+            }
+        }
+    }
+}
+
+// iterate the cells of the current brick tile: fn(cell index, lx, ly, lz)
+template <typename Fn>
+__device__ __forceinline__ void for_brick_cells(const Geom &g, int ox, int oy, int oz, int ex, int ey, int ez, Fn &&fn) {
+    const int nb = ex * ey * ez;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        const int lx = k % ex, ly = (k / ex) % ey, lz = k / (ex * ey);
+        fn(cell_index(g, ox + lx, oy + ly, oz + lz), lx, ly, lz);
+    }
+}
+
 // ---- S2: eps_f ------------------------------------------------------------------
 // FT is the compute type of the form: FP64 for the plain method, FP32 (with
 // FP32 kernel weights) for the low-precision forms.  Also clears the sort
 // counts for the next sort (every cell is visited once).
 template <typename FT>
-__global__ void k_eps_gather(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
+__global__ void __launch_bounds__(256) k_eps_gather(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
+                                                    int ntiles) {
+    __shared__ BrickRanges R;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &B = boxes[tl.box];
         const Geom g = B.g;
+        int ox, oy, oz, ex, ey, ez;
+        brick_unpack(tl.begin, ox, oy, oz);
+        brick_unpack(tl.end, ex, ey, ez);
+        __syncthreads();  // the previous brick is done with R
+        stage_ranges(B, ox, oy, oz, R);
+        __syncthreads();
         const double *pf = B.pf[B.cur];
         const long long cap = B.cap;
         const FT *w = weights_of<FT>(B, pf);
@@ -321,9 +405,9 @@ __global__ void k_eps_gather(const BoxDev *__restrict__ boxes, const Tile *__res
         FT *eps = (FT *)B.eps;
         const FT eps_min = (FT)B.ph.eps_min;
         unsigned nclamp = 0;
-        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
+        for_brick_cells(g, ox, oy, oz, ex, ey, ez, [&](long long c, int lx, int ly, int lz) {
             FT ep = 0;
-            gather27(g, c, B.cell_start, w, cap, [&](int p, FT W) {
+            gather27_staged(R, lx, ly, lz, w, cap, [&](int p, FT W) {
                 const FT d = sizeof(FT) == 8 ? (FT)pf[PD * cap + p] : (FT)xf[p].w;
                 ep += W * (FT(PI_D / 6.0) * d * d * d);
             });
@@ -335,7 +419,7 @@ __global__ void k_eps_gather(const BoxDev *__restrict__ boxes, const Tile *__res
             }
             eps[c] = e;
             B.count[c] = 0;
-        }
+        });
         if (nclamp) atomicAdd(&B.counters[CNT_EPS_CLAMP], (unsigned long long)nclamp);
     }
 }
@@ -508,47 +592,62 @@ template <> __device__ __forceinline__ const float *force_planes<float>(const Bo
 
 // K6a: f_pf,am(c) = -sum_p W F_am
 template <typename FT>
-__global__ void k_reaction_am(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
+__global__ void __launch_bounds__(256) k_reaction_am(const BoxDev *__restrict__ boxes,
+                                                     const Tile *__restrict__ tiles, int ntiles) {
+    __shared__ BrickRanges R;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &B = boxes[tl.box];
         const Geom g = B.g;
+        int ox, oy, oz, ex, ey, ez;
+        brick_unpack(tl.begin, ox, oy, oz);
+        brick_unpack(tl.end, ex, ey, ez);
+        __syncthreads();
+        stage_ranges(B, ox, oy, oz, R);
+        __syncthreads();
         const long long N = g.ncell, cap = B.cap;
         const double *pf = B.pf[B.cur];
         const FT *w = weights_of<FT>(B, pf), *Fa = force_planes<FT>(B, pf, 0);
         FT *fam = (FT *)B.fam;
-        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
-            FT s[3] = {0, 0, 0};
-            gather27(g, c, B.cell_start, w, cap, [&](int p, FT W) {
-                s[0] += W * Fa[p];
-                s[1] += W * Fa[cap + p];
-                s[2] += W * Fa[2 * cap + p];
+        for_brick_cells(g, ox, oy, oz, ex, ey, ez, [&](long long c, int lx, int ly, int lz) {
+            FT s0 = 0, s1 = 0, s2 = 0;
+            gather27_staged(R, lx, ly, lz, w, cap, [&](int p, FT W) {
+                s0 += W * Fa[p];
+                s1 += W * Fa[cap + p];
+                s2 += W * Fa[2 * cap + p];
             });
-            fam[c] = -s[0];
-            fam[N + c] = -s[1];
-            fam[2 * N + c] = -s[2];
-        }
+            fam[c] = -s0;
+            fam[N + c] = -s1;
+            fam[2 * N + c] = -s2;
+        });
     }
 }
 
 // K6b: acc = (first ? 0 : acc) + f_pf,am - sum_p W F_d; after the last subcycle
 // the applied f_pf is the subcycle average.
 template <typename FT>
-__global__ void k_reaction_drag(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles,
-                                int first, int last) {
+__global__ void __launch_bounds__(256) k_reaction_drag(const BoxDev *__restrict__ boxes,
+                                                       const Tile *__restrict__ tiles, int ntiles, int first, int last) {
+    __shared__ BrickRanges R;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &B = boxes[tl.box];
         const Geom g = B.g;
+        int ox, oy, oz, ex, ey, ez;
+        brick_unpack(tl.begin, ox, oy, oz);
+        brick_unpack(tl.end, ex, ey, ez);
+        __syncthreads();
+        stage_ranges(B, ox, oy, oz, R);
+        __syncthreads();
         const long long N = g.ncell, cap = B.cap;
         const double *pf = B.pf[B.cur];
         const FT *w = weights_of<FT>(B, pf), *Fd = force_planes<FT>(B, pf, 1);
         const FT *fam = (const FT *)B.fam;
         FT *acc = (FT *)B.acc, *fpf = (FT *)B.fpf;
         const FT inv_nint = (FT)B.ph.dt_sub;
-        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
+        for_brick_cells(g, ox, oy, oz, ex, ey, ez, [&](long long c, int lx, int ly, int lz) {
             FT s[3] = {0, 0, 0};
-            gather27(g, c, B.cell_start, w, cap, [&](int p, FT W) {
+            gather27_staged(R, lx, ly, lz, w, cap, [&](int p, FT W) {
                 s[0] += W * Fd[p];
                 s[1] += W * Fd[cap + p];
                 s[2] += W * Fd[2 * cap + p];
@@ -562,11 +661,23 @@ __global__ void k_reaction_drag(const BoxDev *__restrict__ boxes, const Tile *__
                 else
                     acc[a * N + c] = v;
             }
-        }
+        });
     }
 }
 
 // ---- host launchers ------------------------------------------------------------------
+// brick tiles of one box (appended to `out`)
+void brick_tiles(int box, const int n[3], std::vector<Tile> &out) {
+    for (int z = 0; z < n[2]; z += BRICK)
+        for (int y = 0; y < n[1]; y += BRICK)
+            for (int x = 0; x < n[0]; x += BRICK) {
+                const int ex = n[0] - x < BRICK ? n[0] - x : BRICK;
+                const int ey = n[1] - y < BRICK ? n[1] - y : BRICK;
+                const int ez = n[2] - z < BRICK ? n[2] - z : BRICK;
+                out.push_back(Tile{box, 0, brick_pack(x, y, z), brick_pack(ex, ey, ez)});
+            }
+}
+
 static int grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     if (g > 152LL * 16) g = 152LL * 16;
@@ -610,7 +721,7 @@ void launch_end_step(BoxDev *b, int nb, cudaStream_t s) { k_end_step<<<(nb + 127
 
 template <typename FT>
 void launch_eps(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
-    k_eps_gather<FT><<<grid, block, 0, s>>>(b, t, nt);
+    k_eps_gather<FT><<<grid, 256, 0, s>>>(b, t, nt);
 }
 template <typename FT>
 void launch_force_am(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
@@ -622,12 +733,12 @@ void launch_force_drag(const BoxDev *b, const Tile *t, int nt, int grid, int blo
 }
 template <typename FT>
 void launch_reaction_am(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
-    k_reaction_am<FT><<<grid, block, 0, s>>>(b, t, nt);
+    k_reaction_am<FT><<<grid, 256, 0, s>>>(b, t, nt);
 }
 template <typename FT>
 void launch_reaction_drag(const BoxDev *b, const Tile *t, int nt, int first, int last, int grid, int block,
                           cudaStream_t s) {
-    k_reaction_drag<FT><<<grid, block, 0, s>>>(b, t, nt, first, last);
+    k_reaction_drag<FT><<<grid, 256, 0, s>>>(b, t, nt, first, last);
 }
 
 #define DPS_CPL_INST(FT)                                                                                  \

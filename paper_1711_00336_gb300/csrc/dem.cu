@@ -43,19 +43,42 @@ __device__ __forceinline__ void cross3(const T a[3], const T b[3], T o[3]) {
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// force and torque on i from one partner (sphere or wall), Sec. 3.1.1 / 3.1.3,
-// in arithmetic T; the torque is (d_i/2) n x F_t (r x F at the contact point
-// r = d_i/2 n).  Results accumulate into FP64.
+// closure constants of the pair forces in arithmetic T, converted once per
+// tile (no FP64 conversions inside the FP32 pair loop)
 template <typename T>
-__device__ __forceinline__ void partner(const Phys &ph, const T n[3], T dist, T sumr, const T ui[3], const T wi[3],
-                                        T di, const T uj[3], const T wjh[3], T m_ij, T dmean, double F[3],
-                                        double Tq[3], unsigned &nlim) {
+struct PairPar {
+    T kfac, xfac, mu_c, h_c, h_min, mu, capfac;
+    int contact, lubrication, lub_limiter;
+};
+template <typename T>
+__device__ __forceinline__ PairPar<T> pair_par(const Phys &ph) {
+    PairPar<T> q;
+    q.kfac = (T)ph.kfac;
+    q.xfac = (T)ph.xfac;
+    q.mu_c = (T)ph.mu_c;
+    q.h_c = (T)ph.h_c;
+    q.h_min = (T)ph.h_min;
+    q.mu = (T)ph.mu;
+    q.capfac = (T)ph.capfac;
+    q.contact = ph.contact;
+    q.lubrication = ph.lubrication;
+    q.lub_limiter = ph.lub_limiter;
+    return q;
+}
+
+// force and torque on i from one partner (sphere or wall), Sec. 3.1.1 / 3.1.3,
+// in arithmetic T, accumulated in T; the torque is (d_i/2) n x F_t (r x F at
+// the contact point r = d_i/2 n).
+template <typename T>
+__device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T dist, T sumr, const T ui[3],
+                                        const T wi[3], T di, const T uj[3], const T wjh[3], T m_ij, T dmean, T F[3],
+                                        T Tq[3], unsigned &nlim) {
     const T delta = sumr - dist;
     if (ph.contact && delta > T(0)) {
         // k_n and xi_n of Eqs. damping_to_stiffness / collision_time, solved
         // for the given e_n and T_c: both proportional to m_ij
-        const T k_n = m_ij * (T)ph.kfac;
-        const T xi = m_ij * (T)ph.xfac;
+        const T k_n = m_ij * ph.kfac;
+        const T xi = m_ij * ph.xfac;
         T ws[3], wx[3], ur[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) ws[a] = T(0.5) * di * wi[a] + wjh[a];
@@ -73,7 +96,7 @@ __device__ __forceinline__ void partner(const Phys &ph, const T n[3], T dist, T 
         const T ut_abs = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
         T Ft[3] = {0, 0, 0};
         if (ut_abs > T(0)) {
-            const T mag = fmin((T)ph.mu_c * Fn_abs, xi * ut_abs) / ut_abs;
+            const T mag = fmin(ph.mu_c * Fn_abs, xi * ut_abs) / ut_abs;
 #pragma unroll
             for (int a = 0; a < 3; ++a) Ft[a] = -mag * ut[a];
         }
@@ -81,23 +104,22 @@ __device__ __forceinline__ void partner(const Phys &ph, const T n[3], T dist, T 
         cross3(n, Ft, nF);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            F[a] += (double)(Fn[a] + Ft[a]);
-            Tq[a] += (double)(T(0.5) * di * nF[a]);
+            F[a] += Fn[a] + Ft[a];
+            Tq[a] += T(0.5) * di * nF[a];
         }
     }
     const T h = dist - sumr;
-    if (ph.lubrication && h < (T)ph.h_c) {
-        const T hh = fmax(h, (T)ph.h_min);
+    if (ph.lubrication && h < ph.h_c) {
+        const T hh = fmax(h, ph.h_min);
         const T r = dmean / hh;          // <d>/h
         const T L = log(T(0.5) * r);     // ln(<d>/(2h))
-        const T mu = (T)ph.mu;
-        T a_sq = T(1.5 * PI_D) * mu * dmean * (T(0.25) * r + T(18.0 / 40.0) * L + T(9.0 / 84.0) * L / r);
+        T a_sq = T(1.5 * PI_D) * ph.mu * dmean * (T(0.25) * r + T(18.0 / 40.0) * L + T(9.0 / 84.0) * L / r);
         // a_sh (2/(h+<d>))^2 = (pi/2) mu <d> ln(<d>/(2h))
-        T a_sh = T(0.5 * PI_D) * mu * dmean * L;
+        T a_sh = T(0.5 * PI_D) * ph.mu * dmean * L;
         a_sq = fmax(a_sq, T(0));
         a_sh = fmax(a_sh, T(0));
         if (ph.lub_limiter) {
-            const T cap = m_ij * (T)ph.capfac;
+            const T cap = m_ij * ph.capfac;
             if (a_sq > cap) { a_sq = cap; ++nlim; }
             if (a_sh > cap) { a_sh = cap; ++nlim; }
         }
@@ -106,7 +128,7 @@ __device__ __forceinline__ void partner(const Phys &ph, const T n[3], T dist, T 
         for (int a = 0; a < 3; ++a) upr[a] = ui[a] - uj[a];
         const T upn = upr[0] * n[0] + upr[1] * n[1] + upr[2] * n[2];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) F[a] += (double)(-a_sq * upn * n[a] - a_sh * (upr[a] - upn * n[a]));
+        for (int a = 0; a < 3; ++a) F[a] += -a_sq * upn * n[a] - a_sh * (upr[a] - upn * n[a]);
     }
 }
 
@@ -206,6 +228,8 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
         const double rng_extra = ph.lubrication ? fmax(ph.h_c, 0.0) : 0.0;
         const float rng_extra_f = (float)rng_extra;
         const float Lf[3] = {(float)g.n[0], (float)g.n[1], (float)g.n[2]};
+        const PairPar<double> pd = pair_par<double>(ph);
+        const PairPar<float> pfl = pair_par<float>(ph);
         for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
             double xi[3], ui[3], wi[3];
 #pragma unroll
@@ -218,6 +242,7 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
             const double di = pf[PD * cap + i];
             const double mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
             double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+            float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};  // FP32 pairs of the mixed forms
             unsigned nlim = 0;
             const int nn = Bx.nlist_n[i];
             for (int k = 0; k < nn; ++k) {
@@ -243,7 +268,7 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                         const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
                         const float m_ij = vi.w * vj.w / (vi.w + vj.w);
                         const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
-                        partner<float>(ph, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, F, T, nlim);
+                        partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf, nlim);
                         continue;
                     }
                 }
@@ -267,7 +292,12 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                     uj[a] = xin[(3 + a) * cap + j];
                     wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
                 }
-                partner<double>(ph, n, dist, sumr, ui, wi, di, uj, wjh, m_ij, dmean, F, T, nlim);
+                partner<double>(pd, n, dist, sumr, ui, wi, di, uj, wjh, m_ij, dmean, F, T, nlim);
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                F[a] += (double)Ff[a];
+                T[a] += (double)Tf[a];
             }
             // walls: the faces of every non-periodic axis (m_ij = m_i, <d> = 2 d_i)
             const double zero[3] = {0, 0, 0};
@@ -281,7 +311,7 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                     if (!(dist < range)) continue;
                     double n[3] = {0, 0, 0};
                     n[a] = side == 0 ? -1.0 : 1.0;
-                    partner<double>(ph, n, dist, 0.5 * di, ui, wi, di, zero, zero, mi, 2.0 * di, F, T, nlim);
+                    partner<double>(pd, n, dist, 0.5 * di, ui, wi, di, zero, zero, mi, 2.0 * di, F, T, nlim);
                 }
             }
             // Eq. particle_motion, semi-implicit Euler with I = m d^2 / 10

@@ -355,6 +355,8 @@ def _declare_batch(L):
     vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, _DP
     ip3 = ctypes.POINTER(ctypes.c_int)
     L.dps_batch_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(vp)]
+    L.dps_batch_last_error.argtypes = [vp]
+    L.dps_batch_last_error.restype = ctypes.c_char_p
     L.dps_batch_destroy.argtypes = [vp]
     L.dps_batch_add_box.argtypes = [vp, ip3, ip3, ctypes.c_double, ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int)]
     L.dps_batch_remove_box.argtypes = [vp, ctypes.c_int]
@@ -412,7 +414,7 @@ class Batch:
 
     def _ck(self, rc):
         if rc != DPS_OK:
-            raise DPSError(rc, "batch call failed")
+            raise DPSError(rc, lib().dps_batch_last_error(self.h).decode())
 
     def close(self):
         if getattr(self, "h", None):
