@@ -55,6 +55,9 @@ class Params(ctypes.Structure):
         ("lub_cap", ctypes.c_double),
         ("eps_min", ctypes.c_double),
         ("pair_search", ctypes.c_int),
+        ("lift", ctypes.c_int),
+        ("eilers", ctypes.c_int),
+        ("smagorinsky", ctypes.c_int),
     ]
 
 
@@ -88,6 +91,11 @@ def lib():
         L.orc_reynolds.restype = ctypes.c_double
         L.orc_reynolds.argtypes = [ctypes.c_double] * 5
         L.orc_rz_kappa.restype = ctypes.c_double
+        L.orc_eilers_factor.restype = ctypes.c_double
+        L.orc_eilers_factor.argtypes = [ctypes.c_double]
+        L.orc_tau_turb.restype = ctypes.c_double
+        L.orc_tau_turb.argtypes = [ctypes.c_double] * 3
+        L.orc_tau_e.restype = ctypes.c_double
         L.orc_rz_kappa.argtypes = [ctypes.c_double]
         L.orc_fluid_fraction.restype = ctypes.c_long
         L.orc_step.restype = ctypes.c_int
@@ -107,7 +115,7 @@ def ptr(a):
 def make_params(n, periodic, tau, g=(0.0, 0.0, 0.0), f_b=(0.0, 0.0, 0.0), rho_f=1.0,
                 e_n=0.9, mu_c=0.25, T_c=1.0, h_c=1.0, h_min=1e-5, C_am=0.5, n_int=1,
                 n_dem=1, drag=1, pressure=1, added_mass=1, lubrication=1, contact=1,
-                lub_limiter=1, lub_cap=0.25, eps_min=0.05, pair_search=1):
+                lub_limiter=1, lub_cap=0.25, eps_min=0.05, pair_search=1, lift=0, eilers=0, smagorinsky=0):
     P = Params()
     P.n[:] = [int(v) for v in n]
     P.periodic[:] = [int(bool(v)) for v in periodic]
@@ -119,6 +127,7 @@ def make_params(n, periodic, tau, g=(0.0, 0.0, 0.0), f_b=(0.0, 0.0, 0.0), rho_f=
     P.drag, P.pressure, P.added_mass = drag, pressure, added_mass
     P.lubrication, P.contact = lubrication, contact
     P.lub_limiter, P.lub_cap, P.eps_min, P.pair_search = lub_limiter, lub_cap, eps_min, pair_search
+    P.lift, P.eilers, P.smagorinsky = lift, eilers, smagorinsky
     return P
 
 
@@ -217,6 +226,35 @@ def lattice_gradient(P, phi_field):
     out = np.zeros(3 * ncell(P))
     lib().orc_lattice_gradient(ctypes.byref(P), ptr(phi_field), ptr(out))
     return out.reshape(3, -1)
+
+
+def lattice_curl(P, psi):
+    psi = np.ascontiguousarray(psi, np.float64).ravel()
+    out = np.zeros(3 * ncell(P))
+    lib().orc_lattice_curl(ctypes.byref(P), ptr(psi), ptr(out))
+    return out.reshape(3, -1)
+
+
+def eilers_factor(eps_p):
+    return lib().orc_eilers_factor(float(eps_p))
+
+
+def tau_turb(tau_star, Qbar, rho):
+    return lib().orc_tau_turb(float(tau_star), float(Qbar), float(rho))
+
+
+def tau_e(P, f, rho, u, eps):
+    f = np.ascontiguousarray(f, np.float64)
+    u = np.ascontiguousarray(u, np.float64)
+    return lib().orc_tau_e(ctypes.byref(P), ptr(f), ctypes.c_double(rho), ptr(u), ctypes.c_double(eps))
+
+
+def lift(d, mu, rho_f, du, w):
+    du = np.ascontiguousarray(du, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    out = np.zeros(3)
+    lib().orc_lift(ctypes.c_double(d), ctypes.c_double(mu), ctypes.c_double(rho_f), ptr(du), ptr(w), ptr(out))
+    return out
 
 
 def cd(Re, eps_p):

@@ -51,6 +51,7 @@ void orc_lattice(int c[19][3], double w[19], int opp[19]) {
     }
 }
 
+static void cross(const double a[3], const double b[3], double out[3]);
 static long ncell_of(const orc_params *P) { return (long)P->n[0] * P->n[1] * P->n[2]; }
 static long cidx(const orc_params *P, int ix, int iy, int iz) {
     return ix + (long)P->n[0] * (iy + (long)P->n[1] * iz);
@@ -247,10 +248,12 @@ void orc_collide_stream(const orc_params *P, const double *f, const double *eps,
                     F[a] = fext[a * nc + c];
                     u[a] = j[a] / rho + F[a] / (2.0 * rho);
                 }
+                /* Eq. tau_e: constant tau, or the Eilers / Smagorinsky value */
+                double tau = (P->eilers || P->smagorinsky) ? orc_tau_e(P, fl, rho, u, eps[c]) : P->tau;
                 orc_equilibrium(rho, u, eps[c], feq);
-                orc_forcing(P->tau, u, eps[c], F, Fq);
+                orc_forcing(tau, u, eps[c], F, Fq);
                 for (int q = 0; q < NQ; ++q) {
-                    double post = fl[q] + (feq[q] - fl[q]) / P->tau + Fq[q];
+                    double post = fl[q] + (feq[q] - fl[q]) / tau + Fq[q];
                     int tx = nb_index(ix + CQ[q][0], P->n[0], P->periodic[0]);
                     int ty = nb_index(iy + CQ[q][1], P->n[1], P->periodic[1]);
                     int tz = nb_index(iz + CQ[q][2], P->n[2], P->periodic[2]);
@@ -288,6 +291,94 @@ void orc_lattice_gradient(const orc_params *P, const double *phi, double *grad) 
                 }
                 for (int a = 0; a < 3; ++a) grad[a * nc + c] = g[a] / CS2;
             }
+}
+
+/* Sec. 3.2.3: curl psi ~ c_s^-2 sum_q w_q c_q x psi(x + c_q), same neighbour
+ * rule as the gradient */
+void orc_lattice_curl(const orc_params *P, const double *psi, double *curl) {
+    long nc = ncell_of(P);
+    for (int iz = 0; iz < P->n[2]; ++iz)
+        for (int iy = 0; iy < P->n[1]; ++iy)
+            for (int ix = 0; ix < P->n[0]; ++ix) {
+                long c = cidx(P, ix, iy, iz);
+                double r[3] = {0, 0, 0};
+                for (int q = 0; q < NQ; ++q) {
+                    int tx = clamp_index(ix + CQ[q][0], P->n[0], P->periodic[0]);
+                    int ty = clamp_index(iy + CQ[q][1], P->n[1], P->periodic[1]);
+                    int tz = clamp_index(iz + CQ[q][2], P->n[2], P->periodic[2]);
+                    long n = cidx(P, tx, ty, tz);
+                    double v[3] = {psi[n], psi[nc + n], psi[2 * nc + n]};
+                    double cq[3] = {CQ[q][0], CQ[q][1], CQ[q][2]};
+                    r[0] += wq(q) * (cq[1] * v[2] - cq[2] * v[1]);
+                    r[1] += wq(q) * (cq[2] * v[0] - cq[0] * v[2]);
+                    r[2] += wq(q) * (cq[0] * v[1] - cq[1] * v[0]);
+                }
+                for (int a = 0; a < 3; ++a) curl[a * nc + c] = r[a] / CS2;
+            }
+}
+
+/* ---------------------------------------------------------------------------
+ * Eq. visc_eilers: mu_* / mu_0 = (1 + 0.5 [mu] eps_p / (1 - eps_p/eps_cp))^2,
+ * [mu] = 2.5, eps_cp = 0.64.  reading: the printed "(1 - eps_p)/eps_cp" is
+ * taken as Eilers' (1 - eps_p/eps_cp) (the printed form contradicts the
+ * Einstein limit 1 + 2.5 eps_p); eps_p/eps_cp is capped at 0.9 where the
+ * closure diverges.
+ * ------------------------------------------------------------------------- */
+double orc_eilers_factor(double eps_p) {
+    const double intrinsic = 2.5, eps_cp = 0.64;
+    double ratio = eps_p / eps_cp;
+    if (ratio > 0.9) ratio = 0.9;
+    if (ratio < 0.0) ratio = 0.0;
+    double a = 1.0 + 0.5 * intrinsic * (ratio * eps_cp) / (1.0 - ratio);
+    return a * a;
+}
+
+/* Eq. tau_t (Smagorinsky, C_S = 0.1, dx_LES = dx = 1).
+ * reading: Qbar is the one Eq. visc_turb defines, sqrt(2 sum Q_ab Q_ab).
+ * Eq. visc_turb with tau_e = tau_* + tau_t gives the quadratic
+ * tau_t (tau_* + tau_t) = C_S^2 Qbar / (2 rho c_s^4); its positive root is the
+ * printed Eq. tau_t once the printed 2 sqrt(2) factor is taken with the
+ * momentum-flux norm sqrt(sum Q_ab Q_ab) of the cited LES scheme, i.e. with
+ * Qbar / sqrt(2). */
+double orc_tau_turb(double tau_star, double Qbar, double rho) {
+    const double Cs = 0.1;
+    double arg = tau_star * tau_star + 2.0 * Cs * Cs / (rho * CS2 * CS2) * Qbar;
+    return 0.5 * (sqrt(arg) - tau_star);
+}
+
+/* Eqs. visc_tau_*, visc_turb, tau_e for one cell: tau_* from mu_* (Eilers,
+ * with eps_p = 1 - eps_f of the cell) and tau_t from the non-equilibrium
+ * momentum flux Q_ab = sum_q c_a c_b (f_q - f_q^eq) */
+double orc_tau_e(const orc_params *P, const double f[19], double rho, const double u[3], double eps) {
+    double nu0 = (P->tau - 0.5) * CS2;
+    double tau_star = P->tau;
+    if (P->eilers) tau_star = 0.5 + nu0 * orc_eilers_factor(1.0 - eps) / CS2;
+    if (!P->smagorinsky) return tau_star;
+    double feq[NQ];
+    orc_equilibrium(rho, u, eps, feq);
+    double Q2 = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double Qab = 0.0;
+            for (int q = 0; q < NQ; ++q) Qab += CQ[q][a] * CQ[q][b] * (f[q] - feq[q]);
+            Q2 += Qab * Qab;
+        }
+    double Qbar = sqrt(2.0 * Q2);
+    return tau_star + orc_tau_turb(tau_star, Qbar, rho);
+}
+
+/* Table 1: F_l = 1.61 d^2 sqrt(mu rho_f / |w|) ((u_f - u_p) x w), w = curl u_f
+ * at the particle; zero where the vorticity vanishes */
+void orc_lift(double d, double mu, double rho_f, const double du[3], const double w[3], double F[3]) {
+    double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (!(wn > 0.0)) {
+        F[0] = F[1] = F[2] = 0.0;
+        return;
+    }
+    double k = 1.61 * d * d * sqrt(mu * rho_f / wn);
+    double c[3];
+    cross(du, w, c);
+    for (int a = 0; a < 3; ++a) F[a] = k * c[a];
 }
 
 /* ---------------------------------------------------------------------------
@@ -636,11 +727,12 @@ int orc_step(const orc_params *P, orc_state *S, long nsteps) {
     double *fpf_k = (double *)malloc(sizeof(double) * 3 * nc);
     double *fpf_sum = (double *)malloc(sizeof(double) * 3 * nc);
     double *uf = (double *)malloc(sizeof(double) * 3 * nc);
+    double *curl = (double *)malloc(sizeof(double) * 3 * nc);
     double *fnew = (double *)malloc(sizeof(double) * NQ * nc);
     double *F_am = (double *)malloc(sizeof(double) * 3 * (np > 0 ? np : 1));
     double *F_d = (double *)malloc(sizeof(double) * 3 * (np > 0 ? np : 1));
     if (!rho || !j || !P_tot || !gradP || !uD || !DuDt || !grad || !F || !fpf_k || !fpf_sum ||
-        !uf || !fnew || !F_am || !F_d)
+        !uf || !curl || !fnew || !F_am || !F_d)
         return -1;
 
     for (long s = 0; s < nsteps; ++s) {
@@ -675,8 +767,17 @@ int orc_step(const orc_params *P, orc_state *S, long nsteps) {
              * its own particle reactions; the LBM step uses their average. */
             for (long k = 0; k < 3 * nc; ++k) fpf_k[k] = 0.0;
 
+            /* Algorithm 1: u_f and its curl at the subcycle start (f_ext =
+             * eps_f f_b), for the lift force */
+            if (P->lift) {
+                for (int a = 0; a < 3; ++a)
+                    for (long c = 0; c < nc; ++c) F[a * nc + c] = S->eps_f[c] * P->f_b[a];
+                fluid_velocity(nc, rho, j, S->eps_f, F, uf);
+                orc_lattice_curl(P, uf, curl);
+            }
             /* added mass: F_am = C_am rho_f V (Du_f/Dt|p - du_p/dt).
-             * reading: du_p/dt is the change of u_p over the last subcycle. */
+             * reading: du_p/dt is the change of u_p over the last subcycle.
+             * The lift force (Table 1) is distributed together with it. */
             for (long i = 0; i < np; ++i) {
                 double V = PI / 6.0 * S->d[i] * S->d[i] * S->d[i];
                 double Dup[3], dudt[3];
@@ -685,6 +786,14 @@ int orc_step(const orc_params *P, orc_state *S, long nsteps) {
                     dudt[a] = S->have_u_sub ? (S->u[3 * i + a] - S->u_sub[3 * i + a]) / dt_sub : 0.0;
                     S->u_sub[3 * i + a] = S->u[3 * i + a];
                     F_am[3 * i + a] = P->added_mass ? P->C_am * P->rho_f * V * (Dup[a] - dudt[a]) : 0.0;
+                }
+                if (P->lift) {
+                    double ufp[3], wp[3], du[3], Fl[3];
+                    orc_interpolate(P, uf, 3, &S->x[3 * i], ufp);
+                    orc_interpolate(P, curl, 3, &S->x[3 * i], wp);
+                    for (int a = 0; a < 3; ++a) du[a] = ufp[a] - S->u[3 * i + a];
+                    orc_lift(S->d[i], mu, P->rho_f, du, wp, Fl);
+                    for (int a = 0; a < 3; ++a) F_am[3 * i + a] += Fl[a];
                 }
             }
             S->have_u_sub = 1;
@@ -747,7 +856,7 @@ int orc_step(const orc_params *P, orc_state *S, long nsteps) {
         S->step++;
     }
     free(rho); free(j); free(P_tot); free(gradP); free(uD); free(DuDt); free(grad);
-    free(F); free(fpf_k); free(fpf_sum); free(uf); free(fnew); free(F_am); free(F_d);
+    free(F); free(fpf_k); free(fpf_sum); free(uf); free(curl); free(fnew); free(F_am); free(F_d);
     return 0;
 }
 

@@ -47,6 +47,9 @@ typedef struct {
     double lub_cap;
     double eps_min;      /* floor of eps_f */
     int pair_search;     /* 0: brute force O(N^2), 1: linked cells */
+    int lift;            /* Table 1 shear lift (Saffman) with the lattice curl */
+    int eilers;          /* Eq. visc_eilers: modified viscosity mu_* from eps_p */
+    int smagorinsky;     /* Eqs. visc_turb, tau_t: Smagorinsky LES relaxation time */
 } orc_params;
 
 typedef struct {
@@ -102,6 +105,18 @@ void orc_collide_stream(const orc_params *P, const double *f, const double *eps,
                         const double *fext, double *fnew);
 /* Sec. 3.2.3: lattice gradient of a scalar field */
 void orc_lattice_gradient(const orc_params *P, const double *phi, double *grad);
+
+/* Sec. 3.2.3: lattice curl of a vector field (3 planes) */
+void orc_lattice_curl(const orc_params *P, const double *psi, double *curl);
+/* Eq. visc_eilers (reading: (1 - eps_p/eps_cp) in the denominator) */
+double orc_eilers_factor(double eps_p);
+/* Eq. tau_t: Smagorinsky relaxation time from Qbar, tau_* and rho */
+double orc_tau_turb(double tau_star, double Qbar, double rho);
+/* per-cell relaxation time tau_e = tau_* + tau_t (Eq. tau_e) for the
+ * pre-collision populations f of one cell */
+double orc_tau_e(const orc_params *P, const double f[19], double rho, const double u[3], double eps);
+/* Table 1: shear lift force on a particle */
+void orc_lift(double d, double mu, double rho_f, const double du[3], const double w[3], double F[3]);
 
 /* Table 1: drag coefficient and Reynolds number */
 double orc_cd(double Re, double eps_p);
