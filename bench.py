@@ -315,9 +315,31 @@ def main():
 # ---------------------------------------------------------------------------
 # suite: the precision, batching and serving forms (python bench.py --suite)
 # ---------------------------------------------------------------------------
-def _settling_closure(dps, wl, d):
-    return dps.closure(g=wl["g"], h_c=d, e_n=0.88, mu_c=0.25, T_c=0.5, h_min=1e-5, C_am=0.5, n_int=2, n_dem=10,
-                       lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5, fb_mode=1)
+def _subcycles(wl):
+    """Interaction subcycles for a settling box.  The fluid-particle force is
+    frozen over a subcycle, so the drag relaxes u_p explicitly: the rate
+    beta/m of the Table 1 drag (low Re, taken at a local solid fraction of
+    1.3 <eps_p>, at most 0.6) times dt/n_int stays below 0.8.  Dense boxes of
+    small spheres need more subcycles, as the paper notes for large solid
+    volume fractions (Sec. 4)."""
+    d, L = float(wl["d"][0]), np.asarray(wl["n"], float)
+    V = math.pi / 6 * d ** 3
+    eps = min(0.6, 1.3 * len(wl["x"]) * V / L.prod())
+    e1 = 1.0 - eps
+    A = 5.81 * eps / e1 ** 3 + 0.48 * eps ** (1 / 3) / e1 ** 4
+    cd = e1 * (1.0 / e1 ** 3 + A)
+    mu = (wl["tau"] - 0.5) / 3.0
+    rate = 3 * math.pi * d * mu * e1 * cd / (float(wl["rho_p"][0]) * V)
+    return max(2, math.ceil(rate / 0.8))
+
+
+def _settling_closure(dps, wl, d, n_int=None):
+    """Sec. 4 settling closure; n_int from _subcycles unless given, and
+    n_int n_DEM >= 20 DEM substeps per step (10 per collision time T_c = dt/2)."""
+    n_int = n_int or _subcycles(wl)
+    return dps.closure(g=wl["g"], h_c=d, e_n=0.88, mu_c=0.25, T_c=0.5, h_min=1e-5, C_am=0.5, n_int=n_int,
+                       n_dem=max(1, math.ceil(20 / n_int)), lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5,
+                       fb_mode=1)
 
 
 def suite_precision(dps, steps=5, warmup=2, L=256, d=1.5, eps_list=(0.05, 0.2, 0.4)):
@@ -330,7 +352,8 @@ def suite_precision(dps, steps=5, warmup=2, L=256, d=1.5, eps_list=(0.05, 0.2, 0
         for prec in ("f64", "f32", "f16s"):
             dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], prec, max_particles=len(wl["x"]))
             dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
-            dom.set_closure(_settling_closure(dps, wl, d))
+            cl = _settling_closure(dps, wl, d)
+            dom.set_closure(cl)
             dom.step(warmup)
             dom.set_timing(True)
             dom.step(1)
@@ -347,7 +370,8 @@ def suite_precision(dps, steps=5, warmup=2, L=256, d=1.5, eps_list=(0.05, 0.2, 0
             ph = dom.get_timing(reset=True)
             st = dom.stats()
             n = int(np.prod(wl["n"]))
-            out.append({"workload": wl["name"], "precision": prec, "particles": len(wl["x"]), "ms_per_step": ms,
+            out.append({"workload": wl["name"], "precision": prec, "particles": len(wl["x"]),
+                        "n_int": cl.n_int, "n_dem": cl.n_dem, "ms_per_step": ms,
                         "MLUPS": n / (ms * 1e-3) / 1e6, "particle_steps_per_s": len(wl["x"]) / (ms * 1e-3),
                         "phases_ms": {k: v["ms"] / steps for k, v in ph.items()}, "u_pS_z": float(st["u_pS"][2]),
                         "eps_clamps": int(st["n_eps_clamp"]), "status": int(st["status"])})
@@ -400,12 +424,13 @@ def suite_batch(dps, steps=20, count=64):
     boxes = _batch_boxes(count=count)
     cells = sum(int(np.prod(b["n"])) for b in boxes)
     parts = sum(len(b["x"]) for b in boxes)
+    n_int = max(_subcycles(wl) for wl in boxes)  # one subcycle count per batch
     B = dps.Batch("f32")
     ids = []
     for wl in boxes:
         b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
         B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
-        B.set_closure(b, _settling_closure(dps, wl, wl["d"][0]))
+        B.set_closure(b, _settling_closure(dps, wl, wl["d"][0], n_int))
         ids.append(b)
     tune_ms = B.autotune(steps=3)
     B.step(2)
@@ -423,7 +448,7 @@ def suite_batch(dps, steps=20, count=64):
     for wl in boxes:
         dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
         dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
-        dom.set_closure(_settling_closure(dps, wl, wl["d"][0]))
+        dom.set_closure(_settling_closure(dps, wl, wl["d"][0], n_int))
         dom.step(4 * 12 + 2)  # same history as the batch: 12 tuning candidates x (1 + 3) steps, then 2
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -453,6 +478,7 @@ def suite_serve(dps, n_req=24, rate=20.0, cap=2000, seed=11):
         eps = rng.uniform(0.01, 0.45)
         reqs.append(workloads.settling_box(L=L, eps=eps, d=1.0, seed=seed * 1000 + k))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    n_int = max(_subcycles(wl) for wl in reqs)  # one subcycle count: the requests share batches
     S = dps.Server("f32", max_boxes=64, hbm_reserve_bytes=16 << 30, chunk_steps=50)
     t0 = time.perf_counter()
     ids = []
@@ -461,7 +487,7 @@ def suite_serve(dps, n_req=24, rate=20.0, cap=2000, seed=11):
         if ta > now:
             time.sleep(ta - now)
         ids.append(S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"],
-                            _settling_closure(dps, wl, 1.0), max_steps=cap, window=500, rel_tol=1e-3))
+                            _settling_closure(dps, wl, 1.0, n_int), max_steps=cap, window=500, rel_tol=1e-3))
     S.wait_idle(3600)
     res = [S.poll(i) for i in ids]
     st = S.stats()
@@ -472,7 +498,7 @@ def suite_serve(dps, n_req=24, rate=20.0, cap=2000, seed=11):
         wl = reqs[k]
         dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
         dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
-        dom.set_closure(_settling_closure(dps, wl, 1.0))
+        dom.set_closure(_settling_closure(dps, wl, 1.0, n_int))
         steps = res[k]["steps"]
         w, acc = 500, np.zeros(3)
         dom.step(steps - w)

@@ -106,6 +106,14 @@ typedef struct {
     double eps_min;           /* floor of eps_f, in (0, 1) */
     double skin;              /* neighbour-list skin in dx (>= 0): particles may move skin/2
                                  within one subcycle before DPS_ERR_UNSTABLE is raised */
+    int lift;                 /* Table 1 shear lift 1.61 d^2 sqrt(mu rho_f/|w|) (u_f - u_p) x w, with
+                                 w the lattice curl (Sec. 3.2.3) of u_f at the subcycle start; it is
+                                 applied and distributed together with the added-mass force */
+    int eilers;               /* Eq. visc_eilers: tau_* of each cell from the Eilers viscosity of its
+                                 eps_p = 1 - eps_f (eps_p/eps_cp capped at 0.9); the particle closures
+                                 keep the base viscosity of tau */
+    int smagorinsky;          /* Eqs. visc_turb, tau_t, tau_e: Smagorinsky LES (C_S = 0.1) added to
+                                 tau_* per cell from the non-equilibrium momentum flux */
 } dps_closure;
 
 /* Global sums (FP64, deterministic order). */

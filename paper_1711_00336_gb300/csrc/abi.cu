@@ -19,11 +19,13 @@
 namespace dps {
 // launchers (lbm.cu, coupling.cu, dem.cu, scan.cu, io.cu)
 template <typename ST, typename FT, typename CT>
-void launch_collide_stream(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
+void launch_collide_stream(const BoxDev *, const Tile *, int, int, int, bool, int, int, cudaStream_t);
 template <typename ST, typename FT, typename CT>
 void launch_moments(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 template <typename FT, typename CT>
 void launch_fields(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+template <typename FT, typename CT>
+void launch_curl(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename ST>
 void launch_pdf_export(const void *, const Geom &, int, double *, cudaStream_t);
 template <typename ST>
@@ -125,6 +127,9 @@ struct Batch {
     Tuning tune;
     bool tuned = false;
     int n_int = 0, n_dem = 0;
+    bool any_lift = false;        // some box applies the lift force (curl launch per subcycle)
+    int n_cell_plain = 0;         // cell tiles of boxes with a constant tau (listed first);
+                                  // the rest relax with a per-cell tau_e (K1 variant)
     bool layout_dirty = true;     // table/tiles must be rebuilt and uploaded
     int parity = 0;               // AA parity of every box of the batch
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // step graphs by parity
@@ -239,6 +244,9 @@ static void compute_phys(BoxHost *h) {
             p.fb[a] = c.fb[a];
     }
     for (int a = 0; a < 3; ++a) p.fb_f[a] = (float)p.fb[a];
+    p.lift = h->have_closure ? c.lift : 0;
+    p.eilers = h->have_closure ? c.eilers : 0;
+    p.smag = h->have_closure ? c.smagorinsky : 0;
     if (!h->have_closure) {
         p.eps_min = 0.05;
         p.n_int = p.n_dem = 1;
@@ -341,19 +349,25 @@ static int push_layout(Batch *B) {
     std::vector<BoxDev> tab(nb);
     std::vector<Tile> cell, part, scan, brick;
     const long long ST = scan_tile_cells();
+    std::vector<Tile> cellv;  // cell tiles of the boxes with a per-cell tau_e
+    B->any_lift = false;
     for (int k = 0; k < nb; ++k) {
         BoxHost *h = B->boxes[k];
         compute_phys(h);
+        B->any_lift |= h->d.ph.lift && h->d.np > 0;
+        std::vector<Tile> &ct = (h->d.ph.eilers || h->d.ph.smag) ? cellv : cell;
         tab[k] = h->d;
         const long long N = h->d.g.ncell, np = h->d.np;
         for (long long c = 0; c < N; c += B->tune.cell_tile)
-            cell.push_back(Tile{k, 0, c, std::min(N, c + B->tune.cell_tile)});
+            ct.push_back(Tile{k, 0, c, std::min(N, c + B->tune.cell_tile)});
         for (long long p = 0; p < np; p += B->tune.part_tile)
             part.push_back(Tile{k, 0, p, std::min(np, p + B->tune.part_tile)});
         int idx = 0;
         for (long long c = 0; c < N; c += ST) scan.push_back(Tile{k, idx++, c, std::min(N, c + ST)});
         brick_tiles(k, h->d.g.n, brick);
     }
+    B->n_cell_plain = (int)cell.size();
+    cell.insert(cell.end(), cellv.begin(), cellv.end());
     int rc;
     if ((rc = ensure_buf(B, &B->d_cell, &B->cap_cell, cell.size()))) return rc;
     if ((rc = ensure_buf(B, &B->d_part, &B->cap_part, part.size()))) return rc;
@@ -392,6 +406,27 @@ static int grid_of(int ntiles) { return std::max(1, std::min(ntiles, 152 * 8)); 
             F16CALL;                            \
         }                                       \
     } while (0)
+
+// K1 over the cell tiles of the boxes with a constant tau, then the per-cell
+// tau_e variant over those of the boxes with the Eilers / Smagorinsky
+// closures (one launch when the batch holds one kind); returns the launches
+static int enqueue_collide(Batch *B, int par) {
+    const BoxDev *T = B->d_table;
+    const Tuning &u = B->tune;
+    cudaStream_t s = B->stream;
+    int nl = 0;
+    for (int v = 0; v < 2; ++v) {
+        const int nt = v ? B->n_cell - B->n_cell_plain : B->n_cell_plain;
+        if (nt <= 0) continue;
+        const Tile *tl = B->d_cell + (v ? B->n_cell_plain : 0);
+        const bool vi = v == 1;
+        PREC_CALL(B, (launch_collide_stream<double, double, double>(T, tl, nt, par, u.k1v, vi, grid_of(nt), u.cell_block, s)),
+                  (launch_collide_stream<float, float, float>(T, tl, nt, par, u.k1v, vi, grid_of(nt), u.cell_block, s)),
+                  (launch_collide_stream<__half, float, float>(T, tl, nt, par, u.k1v, vi, grid_of(nt), u.cell_block, s)));
+        ++nl;
+    }
+    return nl;
+}
 
 static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub) {
     const BoxDev *T = B->d_table;
@@ -437,13 +472,18 @@ static void enqueue_step(Batch *B) {
     else
         launch_fields<float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
     tend(B, PH_MOM, 2);
+    const int nl = pl && B->any_lift;
     for (int k = 0; k < B->n_int; ++k) {
         tbegin(B);
+        if (nl) {
+            if (f64) launch_curl<double, double>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
+            else launch_curl<float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
+        }
         if (pl) {
             if (f64) launch_force_am<double>(T, B->d_part, B->n_part, gp, u.part_block, s);
             else launch_force_am<float>(T, B->d_part, B->n_part, gp, u.part_block, s);
         }
-        tend(B, PH_FAM, pl);
+        tend(B, PH_FAM, pl + nl);
         tbegin(B);
         if (f64) launch_reaction_am<double>(T, B->d_brick, B->n_brick, gb, 256, s);
         else launch_reaction_am<float>(T, B->d_brick, B->n_brick, gb, 256, s);
@@ -468,11 +508,9 @@ static void enqueue_step(Batch *B) {
         enqueue_sort_eps(B, B->n_dem & 1, 1);
     }
     tbegin(B);
-    PREC_CALL(B, (launch_collide_stream<double, double, double>(T, B->d_cell, B->n_cell, par, u.k1v, gc, u.cell_block, s)),
-              (launch_collide_stream<float, float, float>(T, B->d_cell, B->n_cell, par, u.k1v, gc, u.cell_block, s)),
-              (launch_collide_stream<__half, float, float>(T, B->d_cell, B->n_cell, par, u.k1v, gc, u.cell_block, s)));
+    const int nk1 = enqueue_collide(B, par);
     launch_end_step(B->d_table, (int)B->boxes.size(), s);
-    tend(B, PH_COLLIDE, 2);
+    tend(B, PH_COLLIDE, nk1 + 1);
     B->launches_step = B->launch_count;
 }
 
@@ -680,6 +718,7 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
     d.rho = A(N * B->fel);
     void **vec[] = {&d.fpf, &d.fam, &d.acc, &d.j, &d.uD, &d.uprev, &d.gradP, &d.DuDt};
     for (void **v : vec) *v = A(3 * N * B->fel);
+    d.curl = d.uD;
     for (int s = 0; s < 2; ++s) {
         d.pf[s] = (double *)A((size_t)NPF * cap * 8);
         d.pi[s] = (int *)A((size_t)NPI * cap * 4);
@@ -1085,11 +1124,7 @@ int dps_collide_stream(dps_handle h, int64_t n) {
     if (rc) return rc;
     if ((rc = push_layout(B))) return rc;
     for (int64_t s = 0; s < n; ++s) {
-        const int par = B->parity;
-        const int v = B->tune.k1v;
-        PREC_CALL(B, (launch_collide_stream<double, double, double>(B->d_table, B->d_cell, B->n_cell, par, v, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
-                  (launch_collide_stream<float, float, float>(B->d_table, B->d_cell, B->n_cell, par, v, grid_of(B->n_cell), B->tune.cell_block, B->stream)),
-                  (launch_collide_stream<__half, float, float>(B->d_table, B->d_cell, B->n_cell, par, v, grid_of(B->n_cell), B->tune.cell_block, B->stream)));
+        enqueue_collide(B, B->parity);
         B->parity ^= 1;
     }
     return check_boxes(B);

@@ -469,6 +469,10 @@ __device__ __forceinline__ void for_support(const Geom &g, const Support<FT> &S,
 
 // K5a: added mass, F_am = C_am rho_f V (Du_f/Dt|p - du_p/dt) (Table 1);
 // du_p/dt is the change of u_p over the previous subcycle (taken in FP64).
+// With lift, the shear lift F_l = 1.61 d^2 sqrt(mu rho_f / |w|) (u_f - u_p) x w
+// (Table 1; zero where w vanishes) is added to F_am and distributed with it:
+// u_f = (j + eps_f f_b/2)/(rho eps_f) at the subcycle start and its curl w
+// (written by k_curl) are interpolated at the particle.
 template <typename FT>
 __global__ void k_force_am(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
@@ -481,14 +485,45 @@ __global__ void k_force_am(const BoxDev *__restrict__ boxes, const Tile *__restr
         const long long cap = B.cap;
         const FT *DuDt = (const FT *)B.DuDt;
         const int have_usub = B.have_usub;
+        const int lift = ph.lift;
+        const FT *rho = (const FT *)B.rho, *j = (const FT *)B.j, *eps = (const FT *)B.eps;
+        const FT *curl = (const FT *)B.curl;
+        const FT hb[3] = {FT(0.5) * (FT)ph.fb[0], FT(0.5) * (FT)ph.fb[1], FT(0.5) * (FT)ph.fb[2]};
         for (long long p = tl.begin + threadIdx.x; p < tl.end; p += blockDim.x) {
             const Support<FT> S = support_of<FT>(B, pf, p);
-            FT Du[3] = {0, 0, 0};
-            for_support(g, S, [&](long long c, FT W) {
-                Du[0] += W * DuDt[c];
-                Du[1] += W * DuDt[N + c];
-                Du[2] += W * DuDt[2 * N + c];
-            });
+            FT Du[3] = {0, 0, 0}, Fl[3] = {0, 0, 0};
+            if (lift) {
+                FT uf[3] = {0, 0, 0}, w[3] = {0, 0, 0};
+                for_support(g, S, [&](long long c, FT W) {
+                    Du[0] += W * DuDt[c];
+                    Du[1] += W * DuDt[N + c];
+                    Du[2] += W * DuDt[2 * N + c];
+                    const FT e = eps[c];
+                    const FT sc = W / (rho[c] * e);
+                    uf[0] += (j[c] + e * hb[0]) * sc;
+                    uf[1] += (j[N + c] + e * hb[1]) * sc;
+                    uf[2] += (j[2 * N + c] + e * hb[2]) * sc;
+                    w[0] += W * curl[c];
+                    w[1] += W * curl[N + c];
+                    w[2] += W * curl[2 * N + c];
+                });
+                const FT wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                if (wn > FT(0)) {
+                    const double dp = pf[PD * cap + p];
+                    const FT du[3] = {uf[0] - (FT)pf[PU * cap + p], uf[1] - (FT)pf[PV * cap + p],
+                                      uf[2] - (FT)pf[PW * cap + p]};
+                    const FT k = FT(1.61 * dp * dp) * sqrt((FT)(ph.mu * ph.rho_f) / wn);
+                    Fl[0] = k * (du[1] * w[2] - du[2] * w[1]);
+                    Fl[1] = k * (du[2] * w[0] - du[0] * w[2]);
+                    Fl[2] = k * (du[0] * w[1] - du[1] * w[0]);
+                }
+            } else {
+                for_support(g, S, [&](long long c, FT W) {
+                    Du[0] += W * DuDt[c];
+                    Du[1] += W * DuDt[N + c];
+                    Du[2] += W * DuDt[2 * N + c];
+                });
+            }
             const double d = pf[PD * cap + p];
             const FT cV = (FT)(ph.C_am * ph.rho_f * PI_D / 6.0 * d * d * d);
 #pragma unroll
@@ -496,7 +531,7 @@ __global__ void k_force_am(const BoxDev *__restrict__ boxes, const Tile *__restr
                 const double u = pf[(PU + a) * cap + p];
                 const double dudt = have_usub ? (u - pf[(PUS0 + a) * cap + p]) / ph.dt_sub : 0.0;
                 pf[(PUS0 + a) * cap + p] = u;
-                const FT Fa = ph.added_mass ? cV * (Du[a] - (FT)dudt) : FT(0);
+                const FT Fa = (ph.added_mass ? cV * (Du[a] - (FT)dudt) : FT(0)) + Fl[a];
                 pf[(PFA0 + a) * cap + p] = (double)Fa;
                 if (sizeof(FT) == 4) B.f32p[a * cap + p] = (float)Fa;
             }

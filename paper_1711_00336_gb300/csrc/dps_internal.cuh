@@ -9,7 +9,9 @@
 //             plane opp(q) of the upstream cell x - c_q.
 //   fields    planes of ncell values of the field type FT (double for DPS_F64,
 //             float otherwise): eps_f, rho, j(3), u_D(3), u_prev(3), DuDt(3),
-//             gradP(3), f_pf applied (3), f_pf of the subcycle (3), f_pf sum (3)
+//             gradP(3), f_pf applied (3), f_pf of the subcycle (3), f_pf sum (3);
+//             with the lift force the u_D planes hold, during the subcycles,
+//             the curl of the subcycle-start fluid velocity
 //   particles SoA of doubles [field][cap] in cell-sorted order, two sets
 //             (main / alternate) for the sort gather and the DEM ping-pong.
 #pragma once
@@ -144,6 +146,8 @@ struct Phys {
     double skin_half2;   // (skin / 2)^2: largest displacement between two sorts
     int n_int, n_dem;
     int drag, pressure, added_mass, lubrication, contact, lub_limiter;
+    int lift;            // Table 1 shear lift (curl of u_f at the subcycle start)
+    int eilers, smag;    // per-cell tau_e (Eqs. visc_eilers, tau_t, tau_e)
 };
 
 // ---- PDF storage traits ---------------------------------------------------

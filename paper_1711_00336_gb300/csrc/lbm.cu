@@ -67,13 +67,55 @@ __device__ __forceinline__ void collide(CT f[Q], CT eps, CT Fx, CT Fy, CT Fz, CT
     rho_out = rho;
 }
 
+// Eq. tau_e for one cell: tau_* from the Eilers viscosity of eps_p = 1 - eps_f
+// (Eq. visc_eilers; eps_p/eps_cp capped at 0.9 where it diverges) plus the
+// Smagorinsky tau_t (Eqs. visc_turb, tau_t) from the non-equilibrium momentum
+// flux Q_ab = sum_q c_a c_b (f_q - f_q^eq) = Pi_ab - c_s^2 rho delta_ab -
+// rho u_a u_b / eps.  Qbar = sqrt(2 sum Q_ab Q_ab); tau_t solves
+// tau_t (tau_* + tau_t) = C_S^2 Qbar / (2 rho c_s^4) and is taken in the
+// cancellation-free form x / (2 (sqrt(tau_*^2 + x) + tau_*)).  With DEV the
+// second moments are of the deviations: Pi~_ab = Pi_ab - c_s^2 delta_ab, and
+// s = rho - 1.
+template <typename CT, bool DEV>
+__device__ __forceinline__ CT tau_cell(const CT f[Q], CT s, CT rho, CT ux, CT uy, CT uz, CT e, CT ie, CT tau,
+                                       int eilers, int smag) {
+    CT ts = tau;
+    if (eilers) {
+        CT r = (CT(1) - e) * CT(1.0 / 0.64);
+        r = r < CT(0) ? CT(0) : (r > CT(0.9) ? CT(0.9) : r);
+        const CT a = CT(1) + CT(1.25 * 0.64) * r / (CT(1) - r);
+        ts = CT(0.5) + (tau - CT(0.5)) * (a * a);
+    }
+    if (!smag) return ts;
+    CT P[6] = {0, 0, 0, 0, 0, 0};  // xx yy zz xy xz yz
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+        const CT p = f[k] + f[k + 9];
+        if (CX(k) != 0) P[0] += p;
+        if (CY(k) != 0) P[1] += p;
+        if (CZ(k) != 0) P[2] += p;
+        if (CX(k) * CY(k) != 0) P[3] += CT(CX(k) * CY(k)) * p;
+        if (CX(k) * CZ(k) != 0) P[4] += CT(CX(k) * CZ(k)) * p;
+        if (CY(k) * CZ(k) != 0) P[5] += CT(CY(k) * CZ(k)) * p;
+    }
+    const CT iso = CT(1.0 / 3.0) * (DEV ? s : rho);
+    const CT ri = rho * ie;
+    const CT qxx = P[0] - iso - ri * ux * ux, qyy = P[1] - iso - ri * uy * uy, qzz = P[2] - iso - ri * uz * uz;
+    const CT qxy = P[3] - ri * ux * uy, qxz = P[4] - ri * ux * uz, qyz = P[5] - ri * uy * uz;
+    const CT q2 = qxx * qxx + qyy * qyy + qzz * qzz + CT(2) * (qxy * qxy + qxz * qxz + qyz * qyz);
+    const CT x = CT(2 * 0.01 * 9) * sqrt(CT(2) * q2) / rho;  // 2 C_S^2 Qbar / (rho c_s^4)
+    return ts + x / (CT(2) * (sqrt(ts * ts + x) + ts));
+}
+
 // K1 body for one cell: load the 19 populations (AA parity PAR), relax them
 // (Eq. LBM_Equation, same algebra as collide()) and store each opposite pair
-// as soon as it is computed, which keeps few values live.
-template <typename ST, typename FT, typename CT, int PAR>
+// as soon as it is computed, which keeps few values live.  VISC: the box may
+// relax with a per-cell tau_e (vmode bit 0 Eilers, bit 1 Smagorinsky).
+template <typename ST, typename FT, typename CT, int PAR, bool VISC>
 __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const FT *__restrict__ eps,
                                                     const FT *__restrict__ fpf, const Geom &g, long long c, CT fbx,
-                                                    CT fby, CT fbz, CT omega, CT kf, int *status) {
+                                                    CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
+                                                    int *status) {
     constexpr bool DEV = Store<ST>::shifted;
     const long long N = g.ncell;
     NbDelta D;
@@ -105,6 +147,11 @@ __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const 
     const CT uy = (jy + CT(0.5) * Fy) * ir;
     const CT uz = (jz + CT(0.5) * Fz) * ir;
     const CT ie = CT(1) / e;
+    CT omega = omega_box, kf = kf_box;
+    if (VISC && vmode) {
+        omega = CT(1) / tau_cell<CT, DEV>(f, s, rho, ux, uy, uz, e, ie, tau, vmode & 1, vmode & 2);
+        kf = CT(1) - CT(0.5) * omega;
+    }
     const CT uu = ux * ux + uy * uy + uz * uz;
     const CT uF = ux * Fx + uy * Fy + uz * Fz;
     const CT om1 = CT(1) - omega;
@@ -135,7 +182,7 @@ template <> __device__ __forceinline__ double pick<double>(double d, float) { re
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 // K1: every cell tile of every box, AA parity PAR (common to the batch)
-template <typename ST, typename FT, typename CT, int PAR, int MINB>
+template <typename ST, typename FT, typename CT, int PAR, int MINB, bool VISC>
 __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__restrict__ boxes,
                                                            const Tile *__restrict__ tiles, int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
@@ -147,9 +194,11 @@ __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__re
         const CT fbx = pick<CT>(B.ph.fb[0], B.ph.fb_f[0]), fby = pick<CT>(B.ph.fb[1], B.ph.fb_f[1]),
                  fbz = pick<CT>(B.ph.fb[2], B.ph.fb_f[2]);
         const CT omega = pick<CT>(B.ph.omega, B.ph.omega_f), kf = pick<CT>(B.ph.kf, B.ph.kf_f);
+        const CT tau = (CT)B.ph.tau;
+        const int vmode = VISC ? (B.ph.eilers ? 1 : 0) | (B.ph.smag ? 2 : 0) : 0;
         int *st = B.status;
         for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
-            collide_stream_cell<ST, FT, CT, PAR>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, st);
+            collide_stream_cell<ST, FT, CT, PAR, VISC>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, tau, vmode, st);
     }
 }
 
@@ -257,6 +306,56 @@ __global__ void __launch_bounds__(256) k_fields(const BoxDev *__restrict__ boxes
     }
 }
 
+// Lift support (Table 1, Sec. 3.2.3): curl of the fluid velocity at the
+// subcycle start, u_f = (j + eps_f f_b / 2)/(rho eps_f) with the current eps_f,
+// by the lattice rule curl psi = c_s^-2 sum_q w_q c_q x psi(x + c_q) (walls:
+// neighbour coordinate clamped, as for the gradient).  u_f of a neighbour is
+// evaluated on the fly from rho, j and eps_f; boxes without lift are skipped.
+template <typename FT, typename CT>
+__global__ void __launch_bounds__(256) k_curl(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
+                                              int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &B = boxes[tl.box];
+        if (!B.ph.lift || B.np == 0) continue;
+        const Geom g = B.g;
+        const long long N = g.ncell;
+        const FT *rho = (const FT *)B.rho, *j = (const FT *)B.j, *eps = (const FT *)B.eps;
+        FT *curl = (FT *)B.curl;
+        const CT hb[3] = {CT(0.5) * (CT)B.ph.fb[0], CT(0.5) * (CT)B.ph.fb[1], CT(0.5) * (CT)B.ph.fb[2]};
+        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
+            int ix, iy, iz;
+            cell_coords(g, c, ix, iy, iz);
+            long long stride[3] = {1, g.n[0], (long long)g.n[0] * g.n[1]};
+            const int ii[3] = {ix, iy, iz};
+            long long dd[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int L = g.n[a];
+                dd[a][1] = 0;
+                dd[a][0] = ii[a] > 0 ? -stride[a] : (g.per[a] ? (long long)(L - 1) * stride[a] : 0);
+                dd[a][2] = ii[a] < L - 1 ? stride[a] : (g.per[a] ? -(long long)(L - 1) * stride[a] : 0);
+            }
+            CT r[3] = {0, 0, 0};
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const long long n = c + dd[0][CX(q) + 1] + dd[1][CY(q) + 1] + dd[2][CZ(q) + 1];
+                const CT e = (CT)eps[n];
+                const CT sc = CT(1) / ((CT)rho[n] * e);
+                const CT v0 = ((CT)j[n] + e * hb[0]) * sc;
+                const CT v1 = ((CT)j[N + n] + e * hb[1]) * sc;
+                const CT v2 = ((CT)j[2 * N + n] + e * hb[2]) * sc;
+                const CT w = CT(3) * (CT)WQ(q);
+                if (CY(q) != 0 || CZ(q) != 0) r[0] += w * (CT(CY(q)) * v2 - CT(CZ(q)) * v1);
+                if (CZ(q) != 0 || CX(q) != 0) r[1] += w * (CT(CZ(q)) * v0 - CT(CX(q)) * v2);
+                if (CX(q) != 0 || CY(q) != 0) r[2] += w * (CT(CX(q)) * v1 - CT(CY(q)) * v0);
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) curl[a * N + c] = (FT)r[a];
+        }
+    }
+}
+
 // ---- canonical PDF export / import (FP64 host view) -------------------------
 template <typename ST, int PAR>
 __global__ void k_pdf_export(const ST *__restrict__ pdf, Geom g, double *__restrict__ out) {
@@ -304,20 +403,24 @@ static int grid_for(long long n, int block) {
 }
 
 // variant: register budget of K1 (blocks of 128 threads per SM the compiler
-// must fit); chosen by the batch autotuner
+// must fit); chosen by the batch autotuner.  visc: some box of the batch
+// relaxes with a per-cell tau_e (one register budget for that variant).
 template <typename ST, typename FT, typename CT>
-void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, int parity, int variant, int grid,
-                           int block, cudaStream_t s) {
+void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, int parity, int variant, bool visc,
+                           int grid, int block, cudaStream_t s) {
     block = 128;
     if (sizeof(CT) == 8) variant = 0;  // FP64: one register-heavy variant
-#define DPS_K1(MB)                                                                             \
-    do {                                                                                       \
-        if (parity)                                                                            \
-            k_collide_stream<ST, FT, CT, 1, MB><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
-        else                                                                                   \
-            k_collide_stream<ST, FT, CT, 0, MB><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
+#define DPS_K1V(MB, V)                                                                            \
+    do {                                                                                          \
+        if (parity)                                                                               \
+            k_collide_stream<ST, FT, CT, 1, MB, V><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
+        else                                                                                      \
+            k_collide_stream<ST, FT, CT, 0, MB, V><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
     } while (0)
-    if (sizeof(CT) == 8)
+#define DPS_K1(MB) DPS_K1V(MB, false)
+    if (visc)
+        DPS_K1V(sizeof(CT) == 8 ? 2 : 3, true);
+    else if (sizeof(CT) == 8)
         DPS_K1(2);
     else if (variant == 1)
         DPS_K1(3);
@@ -326,6 +429,7 @@ void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, i
     else
         DPS_K1(4);
 #undef DPS_K1
+#undef DPS_K1V
 }
 
 template <typename ST, typename FT, typename CT>
@@ -341,6 +445,11 @@ void launch_moments(const BoxDev *boxes, const Tile *tiles, int ntiles, int pari
 template <typename FT, typename CT>
 void launch_fields(const BoxDev *boxes, const Tile *tiles, int ntiles, int grid, int block, cudaStream_t s) {
     k_fields<FT, CT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+}
+
+template <typename FT, typename CT>
+void launch_curl(const BoxDev *boxes, const Tile *tiles, int ntiles, int grid, int block, cudaStream_t s) {
+    k_curl<FT, CT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
 }
 
 template <typename ST>
@@ -360,13 +469,15 @@ void launch_pdf_import(void *pdf, long long N, const double *in, cudaStream_t s)
 
 // explicit instantiations for the three precision forms
 #define DPS_LBM_INST(ST, FT, CT)                                                                             \
-    template void launch_collide_stream<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t); \
+    template void launch_collide_stream<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, bool, int, int, cudaStream_t); \
     template void launch_moments<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 DPS_LBM_INST(double, double, double)
 DPS_LBM_INST(float, float, float)
 DPS_LBM_INST(__half, float, float)
 template void launch_fields<double, double>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template void launch_fields<float, float>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+template void launch_curl<double, double>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+template void launch_curl<float, float>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template void launch_pdf_export<double>(const void *, const Geom &, int, double *, cudaStream_t);
 template void launch_pdf_export<float>(const void *, const Geom &, int, double *, cudaStream_t);
 template void launch_pdf_export<__half>(const void *, const Geom &, int, double *, cudaStream_t);

@@ -88,6 +88,11 @@ struct dps_server_s {
                 st.queued--;
                 continue;
             }
+            // every box of the batch runs the same subcycle counts: a request
+            // with other counts waits until the running boxes retire
+            if (!running.empty() && (q->r.closure.n_int != running[0]->r.closure.n_int ||
+                                     q->r.closure.n_dem != running[0]->r.closure.n_dem))
+                break;
             size_t need = 0, fre = 0, tot = 0;
             dps_box_bytes(desc.precision, q->r.n, q->r.np, &need);
             cudaMemGetInfo(&fre, &tot);
@@ -168,14 +173,30 @@ struct dps_server_s {
             int rc = dps_batch_step(batch, chunk);
             std::vector<std::pair<Req *, int>> done;  // request, state
             if (rc != DPS_OK) {
-                // a failing box poisons the chunk: retire every running box as failed
-                for (Req *q : running) done.push_back({q, DPS_REQ_FAILED});
+                // boxes are independent: retire those whose status word flags
+                // the failure; if none does (a CUDA error), all of them
+                int flagged = 0;
+                for (Req *q : running) {
+                    dps_stats bs;
+                    if (rc == DPS_ERR_UNSTABLE && dps_batch_stats(batch, q->box, &bs) == DPS_OK && bs.status) {
+                        done.push_back({q, DPS_REQ_FAILED});
+                        flagged++;
+                    }
+                }
+                if (!flagged)
+                    for (Req *q : running) done.push_back({q, DPS_REQ_FAILED});
+                else
+                    rc = DPS_OK;  // the others completed the chunk
             } else {
                 std::lock_guard<std::mutex> g(mu);
                 st.cell_updates += cells * chunk;
             }
             if (rc == DPS_OK) {
                 for (Req *q : running) {
+                    if (std::find_if(done.begin(), done.end(), [&](const std::pair<Req *, int> &p) {
+                            return p.first == q;
+                        }) != done.end())
+                        continue;
                     q->res.steps += chunk;
                     double u[3];
                     dps_batch_particle_mean(batch, q->box, u);
@@ -208,7 +229,7 @@ struct dps_server_s {
                 }
             }
             for (auto &p : done) {
-                finish(p.first, p.second, p.second == DPS_REQ_FAILED ? rc : DPS_OK);
+                finish(p.first, p.second, p.second == DPS_REQ_FAILED ? (rc ? rc : DPS_ERR_UNSTABLE) : DPS_OK);
                 std::lock_guard<std::mutex> g(mu);
                 running.erase(std::find(running.begin(), running.end(), p.first));
             }

@@ -40,7 +40,8 @@ class Closure(ctypes.Structure):
                 ("mu_c", ctypes.c_double), ("T_c", ctypes.c_double), ("h_c", ctypes.c_double),
                 ("h_min", ctypes.c_double), ("C_am", ctypes.c_double), ("n_int", ctypes.c_int),
                 ("n_dem", ctypes.c_int), ("lub_limiter", ctypes.c_int), ("lub_cap", ctypes.c_double),
-                ("eps_min", ctypes.c_double), ("skin", ctypes.c_double)]
+                ("eps_min", ctypes.c_double), ("skin", ctypes.c_double), ("lift", ctypes.c_int),
+                ("eilers", ctypes.c_int), ("smagorinsky", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

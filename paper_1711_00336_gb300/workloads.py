@@ -81,10 +81,14 @@ def rsa(n, periodic, count, d, seed, margin=0.0, max_tries=200):
 
 def jittered_lattice(L, count, d, seed):
     """`count` spheres on a random subset of a cubic lattice filling a periodic
-    L^3 box, each displaced by at most (a - d)/2 per axis (no overlaps)."""
+    L^3 box, each displaced by at most (a - d)/2 per axis (no overlaps).  The
+    spacing a is at least 1.02 d where the sites suffice, so that lattice
+    neighbours do not start in exact contact."""
     rng = np.random.default_rng(seed)
-    m = int(math.floor(L / d))
-    while m ** 3 < count:
+    m = int(math.floor(L / (1.02 * d)))
+    if m ** 3 < count:
+        m = int(math.floor(L / d))
+    if m ** 3 < count:
         raise ValueError("volume fraction above the cubic-lattice limit")
     a = L / m
     sites = rng.choice(m ** 3, size=count, replace=False)

@@ -189,3 +189,44 @@ def test_serving_convergence_cancel_and_admission():
     assert np.array_equal(ra["up_mean"], rb["up_mean"])
     assert rc["state"] == "cancelled"
     assert rbig["state"] == "failed"
+
+
+def test_serving_failing_request_leaves_the_others_running():
+    """A request whose particles leave their neighbour-list skin (gravity far
+    too strong for its subcycle) fails alone; the request running beside it
+    completes with the result it has alone."""
+    dps = _dps()
+    kw = dict(max_steps=300, window=100, rel_tol=1e-9)
+    wl, c = _request(dps, 12, 0.1, 5)
+    S = dps.Server("f32", max_boxes=4, hbm_reserve_bytes=1 << 30, chunk_steps=50)
+    alone = S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"], c, **kw)
+    S.wait_idle(600)
+    r_alone = S.poll(alone)
+    S.close()
+    bad_c = dps.closure(g=(0.0, 0.0, -5.0), h_c=1.0, **KW)
+    S = dps.Server("f32", max_boxes=4, hbm_reserve_bytes=1 << 30, chunk_steps=50)
+    good = S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"], c, **kw)
+    bad = S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"], bad_c, **kw)
+    S.wait_idle(600)
+    rg, rb = S.poll(good), S.poll(bad)
+    S.close()
+    assert rb["state"] == "failed"
+    assert rg["state"] == "done" and rg["steps"] == 300
+    assert np.array_equal(rg["up_mean"], r_alone["up_mean"])
+
+
+def test_serving_groups_requests_by_subcycle_counts():
+    """Requests with other (n_int, n_DEM) wait until the running boxes retire
+    instead of sharing a batch; all of them complete."""
+    dps = _dps()
+    kw = dict(max_steps=200, window=100, rel_tol=1e-9)
+    wl, _ = _request(dps, 10, 0.1, 6)
+    cs = [dps.closure(g=wl["g"], h_c=1.0, **{**KW, "n_int": ni, "n_dem": nd}) for ni, nd in ((2, 3), (3, 2), (2, 3))]
+    S = dps.Server("f32", max_boxes=4, hbm_reserve_bytes=1 << 30, chunk_steps=50)
+    ids = [S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"], c, **kw) for c in cs]
+    S.wait_idle(600)
+    res = [S.poll(i) for i in ids]
+    st = S.stats()
+    S.close()
+    assert all(r["state"] == "done" and r["steps"] == 200 for r in res), res
+    assert st["failed"] == 0

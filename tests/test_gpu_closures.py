@@ -1,0 +1,119 @@
+"""GPU parity of the optional closures against the FP64 oracle: the per-cell
+relaxation time (Eilers viscosity, Eq. visc_eilers; Smagorinsky LES, Eqs.
+visc_turb, tau_t, tau_e) inside the collide-stream kernel, and the shear lift
+force of Table 1 with the lattice curl of Sec. 3.2.3.
+
+Tolerances as for the plain method: FP64 1e-12 relative to the magnitude of
+the compared quantity; the FP32 form 1e-4 (relative L2 of the velocity field)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1711_00336_gb300 import workloads
+
+from test_gpu_parity import BOXES, KW, _dps, _packed_particles, _perm, _run_pair, close
+
+pytestmark = pytest.mark.gpu
+
+VISC = [dict(eilers=1), dict(smagorinsky=1), dict(eilers=1, smagorinsky=1)]
+
+
+@pytest.mark.parametrize("vk", VISC, ids=["eilers", "smagorinsky", "both"])
+@pytest.mark.parametrize("n,per", BOXES[:3])
+@pytest.mark.parametrize("steps", [1, 2])
+def test_collide_stream_per_cell_tau(n, per, steps, vk):
+    dps = _dps()
+    perm = _perm()
+    nc = n[0] * n[1] * n[2]
+    _, w_orc, _ = O.lattice()
+    # populations 5 % off equilibrium: a non-equilibrium flux the LES sees
+    f0 = workloads.random_pdfs(w_orc, nc, seed=steps + 3 * nc, amp=0.05)
+    eps, fpf = workloads.random_fields(nc, seed=11 + nc, eps_range=(0.4, 1.0))
+    dom = dps.Domain(n, per, 0.58, "f64")
+    dom.set_closure(fb_mode=0, **vk)
+    dom.write_pdfs(f0[perm])
+    dom.write_fields(eps_f=eps, f_pf=fpf)
+    dom.collide_stream(steps)
+    got = dom.read_pdfs()
+    P = O.make_params(n, per, 0.58, **vk)
+    ref = f0
+    for _ in range(steps):
+        ref = O.collide_stream(P, ref, eps, fpf)
+    close(got, ref[perm], what="pdfs")
+    # the closure changes the result (the test is not vacuous)
+    plain = O.collide_stream(O.make_params(n, per, 0.58), f0, eps, fpf)
+    assert np.abs(O.collide_stream(P, f0, eps, fpf) - plain).max() > 1e-6
+    dom.close()
+
+
+def test_per_cell_tau_box_and_plain_box_in_one_batch():
+    """A batch mixing a box with the per-cell relaxation time and one without
+    steps each exactly as when it is alone (the plain box keeps its constant
+    relaxation rates inside the per-cell kernel variant)."""
+    dps = _dps()
+    n, per = (9, 8, 7), (1, 1, 0)
+    pr = _packed_particles(n, per, 20, seed=3)
+    cl = dict(g=(0, 0, -2e-3), n_int=2, n_dem=2, **KW)
+    res = {}
+    for mode in ("alone", "mixed"):
+        B = dps.Batch("f64")
+        ids = []
+        for vk in ({}, dict(eilers=1, smagorinsky=1)) if mode == "mixed" else ({},):
+            b = B.add_box(n, per, 0.7, len(pr["x"]))
+            B.add_particles(b, pr["x"], pr["d"], pr["rho_p"], u=pr["u"], w=pr["w"])
+            B.set_closure(b, dps.closure(**cl, **vk))
+            ids.append(b)
+        B.step(3)
+        res[mode] = B.read_particles(ids[0])
+        B.close()
+    for k in ("x", "u", "w"):
+        assert np.array_equal(res["alone"][k], res["mixed"][k]), k
+
+
+@pytest.mark.parametrize("n_int,n_dem", [(1, 2), (2, 3)])
+@pytest.mark.parametrize("n,per", [((12, 10, 14), (1, 1, 0)), ((9, 9, 9), (1, 1, 1))])
+def test_coupled_steps_with_all_closures_fp64(n, per, n_int, n_dem):
+    pr = _packed_particles(n, per, 40, seed=n_int * 7 + n_dem)
+    kw = {**KW, "T_c": 10.0 / (n_int * n_dem), "lift": 1, "eilers": 1, "smagorinsky": 1}
+    dom, ref = _run_pair(n, per, 0.62, pr, 3, n_int=n_int, n_dem=n_dem, **kw)
+    got, r = dom.read_particles(), ref.particles()
+    for k, fl_ in (("x", 0.0), ("u", 1e-3), ("w", 1e-3), ("F", 1e-6)):
+        close(got[k], r[k], what=k, floor=fl_)
+    fl, fr = dom.read_fields(("rho", "ubar", "eps_f", "f_pf")), ref.fields()
+    close(fl["rho"], fr["rho"], what="rho")
+    close(fl["ubar"], fr["ubar"], what="ubar", floor=1e-3)
+    close(fl["f_pf"], ref.fpf, what="f_pf", floor=1e-6)
+    dom.close()
+
+
+def test_lift_changes_the_trajectory_and_matches():
+    """Lift alone on a sheared suspension: the GPU follows the oracle, and
+    the lift visibly changes the particle forces."""
+    n, per = (10, 12, 10), (1, 1, 0)
+    pr = _packed_particles(n, per, 30, seed=21)
+    pr["u"] = pr["u"] * 0.0
+    pr["u"][:, 0] = 0.02  # particles dragged through fluid at rest: a shear layer forms
+    kw = {**KW, "T_c": 2.0}
+    dom, ref = _run_pair(n, per, 0.7, pr, 4, fb=(1e-5, 0, 0), n_int=1, n_dem=5, lift=1, **kw)
+    got, r = dom.read_particles(), ref.particles()
+    close(got["u"], r["u"], what="u", floor=1e-3)
+    close(got["F"], r["F"], what="F", floor=1e-6)
+    dom.close()
+    ref0 = O.Domain(O.make_params(n, per, 0.7, g=(0, 0, -2e-3), f_b=(1e-5, 0, 0), n_int=1, n_dem=5, **kw),
+                    x=pr["x"], u=pr["u"], w=pr["w"], d=pr["d"], rho_p=pr["rho_p"])
+    ref0.step(4)
+    assert np.abs(ref0.particles()["F"] - r["F"]).max() > 1e-9
+
+
+def test_closures_f32_form_field_tolerance():
+    """The FP32 form with every closure stays within the FP32 field
+    tolerance of the FP64 oracle over 20 coupled steps."""
+    n, per = (12, 10, 14), (1, 1, 0)
+    pr = _packed_particles(n, per, 40, seed=5)
+    kw = {**KW, "T_c": 2.0, "lift": 1, "eilers": 1, "smagorinsky": 1}
+    dom, ref = _run_pair(n, per, 0.62, pr, 20, n_int=2, n_dem=5, prec="f32", **kw)
+    ub, ubr = dom.read_fields(("ubar",))["ubar"], ref.fields()["ubar"]
+    assert np.linalg.norm(ub - ubr) / np.linalg.norm(ubr) < 1e-4
+    got, r = dom.read_particles(), ref.particles()
+    assert np.linalg.norm(got["u"] - r["u"]) / np.linalg.norm(r["u"]) < 1e-4
+    dom.close()
