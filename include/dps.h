@@ -84,7 +84,8 @@ typedef struct {
     int drag;                 /* Table 1 drag (Tenneti et al.) */
     int pressure;             /* Table 1 pressure-gradient force */
     int added_mass;           /* Table 1 added-mass force */
-    int lubrication;          /* Sec. 3.1.3 (Ball & Melrose) */
+    int lubrication;          /* Sec. 3.1.3 (Ball & Melrose), on pairs and walls that do not
+                                 overlap and whose gap is below h_c (floored at h_min) */
     int contact;              /* Sec. 3.1.1 spring-dashpot contact */
     double g[3];              /* gravity, acting on the particles only (Sec. 3.1.2) */
     int fb_mode;              /* body force on the fluid, applied as eps_f*f_b:

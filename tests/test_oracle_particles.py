@@ -268,3 +268,45 @@ def test_cell_list_structure_and_candidate_superset():
                     if a < 2:
                         db = min(db, nb[a] - db)
                     assert db <= 1
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.1.3 with Sec. 5: lubrication acts on approaching, non-overlapping
+# pairs only; a wet sphere still rebounds from a wall
+# --------------------------------------------------------------------------
+def test_lubrication_off_while_overlapping_on_just_before():
+    P = _dry_params(lubrication=1, contact=0, h_c=0.5, h_min=1e-5)
+    rel = [[0.01, 0, 0], [-0.01, 0, 0]]
+    for gap, expect_lub in ((-0.01, False), (0.0, True), (1e-7, True), (0.3, True), (0.6, False)):
+        x = np.array([[7.0, 8.0, 8.0], [8.0 + gap, 8.0, 8.0]])
+        dom = O.Domain(P, x=x, u=rel, d=[1.0, 1.0], rho_p=[2.5, 2.5])
+        _, _, Fl = dom.dem_forces(1e-3)
+        assert (np.abs(Fl).max() > 0) == expect_lub, gap
+        if expect_lub:
+            assert Fl[0, 0] < 0 and Fl[1, 0] > 0  # resists the approach
+
+
+def _wall_drop(lubrication, h_c=0.5, steps=120):
+    """A heavy sphere (d = 0.5, rho_p/rho_f = 32) thrown at the bottom wall of
+    a closed 12x12x24 box through fluid at rest (tau 0.505), Sec. 5 settings
+    e_n = 0.97, mu_c = 0.1, T_c = 0.5, n_int = 10, n_DEM = 50."""
+    P = O.make_params((12, 12, 24), (0, 0, 0), tau=0.505, g=(0, 0, -1e-4), e_n=0.97, mu_c=0.1, T_c=0.5,
+                      h_c=h_c, h_min=1e-5, C_am=0.5, n_int=10, n_dem=50, lubrication=lubrication)
+    dom = O.Domain(P, x=[[6.0, 6.0, 2.0]], u=[[0, 0, -0.03]], d=[0.5], rho_p=[32.0])
+    u = []
+    for _ in range(steps):
+        dom.step(1)
+        u.append(dom.u[0, 2])
+    u = np.array(u)
+    k = int(np.argmax(u > 0))  # first step moving up: the rebound
+    return -u[k - 1], u[k:].max()
+
+
+def test_wet_sphere_rebounds_less_than_dry():
+    """Sec. 5: lubrication lowers the rebound (Table 3, B4 vs B0) but a
+    rebound remains; without lubrication it is close to the dry e_n."""
+    u_in_dry, u_out_dry = _wall_drop(lubrication=0)
+    u_in_wet, u_out_wet = _wall_drop(lubrication=1)
+    e_dry, e_wet = u_out_dry / u_in_dry, u_out_wet / u_in_wet
+    assert 0.85 < e_dry < 1.0
+    assert 0.05 < e_wet < e_dry - 0.1
