@@ -199,6 +199,23 @@ def run_reference(args, wl, ncell):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (all_reduce MAX); x itself when alone."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, ncell, steps, t_ms):
+    """Whole-job MLUPS: every rank advances its own box of ncell cells by
+    `steps` steps (replicas, weak scaling); t_ms is the slowest rank's time."""
+    return world * ncell * steps / (t_ms * 1e-3) / 1e6
+
+
 def config_of(wl, ncell, prec):
     return {"workload": wl["name"], "cells": ncell, "particles": int(len(wl["x"])), "precision": prec,
             "n_int": 1, "n_dem": 10, "boundaries": "periodic x,y; walls z",
@@ -246,12 +263,8 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    t_all = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_all = float(t.item())
-    value = world * ncell * args.steps / (t_all * 1e-3) / 1e6
+    t_all = max_over_ranks(total_ms, world, "cuda")
+    value = job_mlups(world, ncell, args.steps, t_all)
     ms_step = t_all / args.steps
 
     # roofline of the dominant kernel, measured live over the timed region
@@ -449,7 +462,7 @@ def suite_batch(dps, steps=20, count=64):
         dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
         dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
         dom.set_closure(_settling_closure(dps, wl, wl["d"][0], n_int))
-        dom.step(4 * 12 + 2)  # same history as the batch: 12 tuning candidates x (1 + 3) steps, then 2
+        dom.step(4 * 13 + 2)  # same history as the batch: 13 tuning candidates x (1 + 3) steps, then 2
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         dom.step(steps)

@@ -53,7 +53,7 @@ template <typename FT>
 void launch_reaction_am(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
 void launch_reaction_drag(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
-void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
+void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, int, int, cudaStream_t);
 void launch_build_nlist(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 long long scan_scratch_words(long long);
 void exclusive_scan(const int *, long long, int *, int *, cudaStream_t);
@@ -126,8 +126,10 @@ struct Batch {
     size_t cap_cell = 0, cap_part = 0, cap_scan = 0, cap_brick = 0;
     Tuning tune;
     bool tuned = false;
+    bool shape_fixed = false;     // launch shapes set by the caller or the autotuner
     int n_int = 0, n_dem = 0;
     bool any_lift = false;        // some box applies the lift force (curl launch per subcycle)
+    int part_off[5] = {0, 0, 0, 0, 0};  // particle tiles grouped by DEM lanes class (1, 2, 4, 8)
     int n_cell_plain = 0;         // cell tiles of boxes with a constant tau (listed first);
                                   // the rest relax with a per-cell tau_e (K1 variant)
     bool layout_dirty = true;     // table/tiles must be rebuilt and uploaded
@@ -330,6 +332,18 @@ static int ensure_buf(Batch *B, Tile **p, size_t *cap, size_t need) {
     return DPS_OK;
 }
 
+// lanes per particle in the DEM substep of a box (class 0..3 = 1, 2, 4, 8
+// lanes): about one neighbour-list entry per lane or more, from the expected
+// list length (number density times the list sphere).  A property of the box
+// alone, so a box gets the same arithmetic alone and in any batch.
+static int dem_lanes_class(const BoxHost *h) {
+    if (!h->have_closure || h->d.np == 0) return 0;
+    const dps_closure &c = h->cl;
+    const double rl = h->dmax + (c.lubrication ? std::fmax(c.h_c, 0.0) : 0.0) + c.skin;
+    const double est = (double)h->d.np / (double)h->d.g.ncell * 4.18879 * rl * rl * rl;
+    return est >= 24.0 ? 3 : est >= 8.0 ? 2 : est >= 3.0 ? 1 : 0;
+}
+
 // rebuild the device table and the tile lists from the host boxes (the
 // device step state must have been pulled first)
 static int push_layout(Batch *B) {
@@ -350,6 +364,18 @@ static int push_layout(Batch *B) {
     std::vector<Tile> cell, part, scan, brick;
     const long long ST = scan_tile_cells();
     std::vector<Tile> cellv;  // cell tiles of the boxes with a per-cell tau_e
+    if (!B->shape_fixed) {
+        // default particle tiles: small enough that every SM gets a block when
+        // the batch holds few particles (a particle thread is latency- or
+        // FP64-bound, so spreading them over all SMs is what counts)
+        long long npt = 0;
+        for (BoxHost *h : B->boxes) npt += h->d.np;
+        int pt = 256;
+        while (pt > 32 && npt < 2LL * 152 * pt) pt /= 2;
+        B->tune.part_tile = pt;
+        B->tune.part_block = std::min(128, pt);
+    }
+    std::vector<Tile> partc[4];  // particle tiles by DEM lanes class
     B->any_lift = false;
     for (int k = 0; k < nb; ++k) {
         BoxHost *h = B->boxes[k];
@@ -360,14 +386,20 @@ static int push_layout(Batch *B) {
         const long long N = h->d.g.ncell, np = h->d.np;
         for (long long c = 0; c < N; c += B->tune.cell_tile)
             ct.push_back(Tile{k, 0, c, std::min(N, c + B->tune.cell_tile)});
+        const int lc = dem_lanes_class(h);
         for (long long p = 0; p < np; p += B->tune.part_tile)
-            part.push_back(Tile{k, 0, p, std::min(np, p + B->tune.part_tile)});
+            partc[lc].push_back(Tile{k, 0, p, std::min(np, p + B->tune.part_tile)});
         int idx = 0;
         for (long long c = 0; c < N; c += ST) scan.push_back(Tile{k, idx++, c, std::min(N, c + ST)});
         brick_tiles(k, h->d.g.n, brick);
     }
     B->n_cell_plain = (int)cell.size();
     cell.insert(cell.end(), cellv.begin(), cellv.end());
+    for (int c = 0; c < 4; ++c) {
+        B->part_off[c] = (int)part.size();
+        part.insert(part.end(), partc[c].begin(), partc[c].end());
+    }
+    B->part_off[4] = (int)part.size();
     int rc;
     if ((rc = ensure_buf(B, &B->d_cell, &B->cap_cell, cell.size()))) return rc;
     if ((rc = ensure_buf(B, &B->d_part, &B->cap_part, part.size()))) return rc;
@@ -501,10 +533,17 @@ static void enqueue_step(Batch *B) {
             launch_reaction_drag<float>(T, B->d_brick, B->n_brick, k == 0, k == B->n_int - 1, gb, 256, s);
         tend(B, PH_RDRAG, 1);
         tbegin(B);
+        int ndl = 0;
         if (pl)
             for (int sd = 0; sd < B->n_dem; ++sd)
-                launch_dem_substep(T, B->d_part, B->n_part, sd & 1, B->prec != DPS_F64, gp, u.part_block, s);
-        tend(B, PH_DEM, pl * B->n_dem);
+                for (int c = 0; c < 4; ++c) {
+                    const int nt = B->part_off[c + 1] - B->part_off[c];
+                    if (nt <= 0) continue;
+                    launch_dem_substep(T, B->d_part + B->part_off[c], nt, sd & 1, B->prec != DPS_F64, 1 << c,
+                                       grid_of(nt), u.part_block, s);
+                    ++ndl;
+                }
+        tend(B, PH_DEM, ndl);
         enqueue_sort_eps(B, B->n_dem & 1, 1);
     }
     tbegin(B);
@@ -1441,6 +1480,7 @@ int dps_batch_set_tuning(dps_batch b, const int cfg[5]) {
     int rc = pull_state(&b->B);
     if (rc) return rc;
     b->B.tune = Tuning{cfg[0], cfg[1], cfg[2], cfg[3], cfg[4]};
+    b->B.shape_fixed = true;
     b->B.layout_dirty = true;
     return DPS_OK;
 }
@@ -1458,10 +1498,11 @@ int dps_batch_get_tuning(dps_batch b, int cfg[5]) {
 // kernels, each timed over `steps` replays of the step graph
 static int autotune(Batch *B, int steps, double *best_ms) {
     static const int cell_c[][2] = {{128, 512}, {128, 2048}, {256, 1024}, {256, 4096}, {64, 256}, {128, 8192}};
-    static const int part_c[][2] = {{128, 128}, {128, 512}, {256, 256}, {64, 64}};
+    static const int part_c[][2] = {{128, 128}, {128, 512}, {256, 256}, {64, 64}, {32, 32}};
     if (steps < 1) steps = 1;
     int rc = ready(B);
     if (rc) return rc;
+    B->shape_fixed = true;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -8,7 +8,11 @@
 // Neighbour list: after every sort a Verlet list is built per particle from
 // the linked cells of the +-R cells around it, keeping every partner within
 // the interaction range plus the skin; the n_DEM substeps then loop over the
-// list only.  A particle that moves more than skin/2 before the next sort
+// list only.  A substep gives each particle a group of LANES consecutive
+// lanes of a warp: lane l takes the list entries l, l + LANES, ... and the
+// group's force and torque sums are combined by warp shuffles (a fixed xor
+// tree, so the result does not depend on the launch shape); lane 0 then adds
+// the walls and integrates.  A particle that moves more than skin/2 before the next sort
 // raises DPS_ERR_UNSTABLE.  Candidate distances are screened in FP32 (a float
 // copy of the positions, refreshed every substep, with a margin far above its
 // rounding) and every pair that passes is evaluated exactly: in FP64 for the
@@ -108,8 +112,10 @@ __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T di
             Tq[a] += T(0.5) * di * nF[a];
         }
     }
+    // lubrication on pairs that do not overlap, 0 <= h < h_c (in contact the
+    // spring-dashpot acts alone, which keeps the wet rebound of Sec. 5)
     const T h = dist - sumr;
-    if (ph.lubrication && h < ph.h_c) {
+    if (ph.lubrication && h >= T(0) && h < ph.h_c) {
         const T hh = fmax(h, ph.h_min);
         const T r = dmean / hh;          // <d>/h
         const T L = log(T(0.5) * r);     // ln(<d>/(2h))
@@ -134,13 +140,12 @@ __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T di
 
 // ---- neighbour list ----------------------------------------------------------------
 // list of particle i: partners j != i with |x_j - x_i| < (d_i+d_j)/2 + extra + skin
-// (screened in FP32 with a margin), stored k-major: nlist[k*cap + i]
+// (screened in FP32 with a margin), stored row by row: nlist[i*maxn + k]
 __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
                                                      int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &Bx = boxes[tl.box];
-        const long long cap = Bx.cap;
         const Geom g = Bx.g;
         const Phys &ph = Bx.ph;
         const float4 *xf = Bx.xf[0];
@@ -149,6 +154,7 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
         const int R = Bx.R, maxn = Bx.maxn;
         for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
             const float4 pi = xf[i];
+            int *lst = Bx.nlist + i * (long long)maxn;
             int b[3] = {containing_cell((double)pi.x, g.n[0]), containing_cell((double)pi.y, g.n[1]),
                         containing_cell((double)pi.z, g.n[2])};
             int lo[3], hi[3];
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
                             const float r = 0.5f * (pi.w + pj.w) + extra;
                             if (dx * dx + dy * dy + dz * dz < r * r) {
                                 if (cnt < maxn)
-                                    Bx.nlist[(long long)cnt * cap + i] = j;
+                                    lst[cnt] = j;
                                 else
                                     over = true;
                                 ++cnt;
@@ -208,19 +214,140 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
     }
 }
 
+// the exact FP64 pair of partner j (Sec. 3.1.1 / 3.1.3): separation from the
+// FP64 positions, then partner<double>.  Out of line in the mixed forms,
+// where it runs for the rare pairs near contact only, so that its registers
+// do not limit the occupancy of the FP32 pair loop.
+template <bool INL>
+__device__ __forceinline__ void pair64_body(const PairPar<double> &pd, const double *__restrict__ xin,
+                                            const double *__restrict__ pf, long long cap, const Geom &g, long long j,
+                                            const double xi[3], const double ui[3], const double wi[3], double di,
+                                            double mi, double rng_extra, double F[3], double T[3], unsigned &nlim) {
+    double dx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dx[a] = min_image(xin[a * cap + j] - xi[a], g.n[a], g.per[a]);
+    const double dist2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+    const double dj = pf[PD * cap + j];
+    const double sumr = 0.5 * (di + dj);
+    const double dist = sqrt(dist2);
+    if (!(dist < sumr + rng_extra) || dist == 0.0) return;
+    const double mj = pf[PRHO * cap + j] * PI_D / 6.0 * dj * dj * dj;
+    const double m_ij = mi * mj / (mi + mj);
+    const double dmean = 2.0 * di * dj / (di + dj);
+    const double inv = 1.0 / dist;
+    const double n[3] = {dx[0] * inv, dx[1] * inv, dx[2] * inv};
+    double uj[3], wjh[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        uj[a] = xin[(3 + a) * cap + j];
+        wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
+    }
+    partner<double>(pd, n, dist, sumr, ui, wi, di, uj, wjh, m_ij, dmean, F, T, nlim);
+}
+// the mixed forms' near-contact pair: loads the FP64 state of particle i itself
+__device__ __noinline__ void pair64_out(const BoxDev &Bx, const double *__restrict__ xin, long long i, long long j,
+                                        double F[3], double T[3], unsigned &nlim) {
+    const double *pf = Bx.pf[Bx.cur];
+    const long long cap = Bx.cap;
+    double xi[3], ui[3], wi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xi[a] = xin[a * cap + i];
+        ui[a] = xin[(3 + a) * cap + i];
+        wi[a] = xin[(6 + a) * cap + i];
+    }
+    const double di = pf[PD * cap + i];
+    const double mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
+    const double rng_extra = Bx.ph.lubrication ? fmax(Bx.ph.h_c, 0.0) : 0.0;
+    const PairPar<double> pd = pair_par<double>(Bx.ph);
+    const Geom g = Bx.g;
+    pair64_body<false>(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
+}
+
+// lane 0 of a particle's group: wall partners, then Eq. particle_motion
+// (semi-implicit Euler) and the outputs of the substep; out of line, once
+// per particle
+__device__ __noinline__ void finish_particle(const BoxDev &Bx, const PairPar<double> &pd, long long i, int src_tmp,
+                                             double F[3], double T[3], unsigned nlim) {
+    const double *xin = src_tmp ? Bx.xtmp : Bx.pf[Bx.cur];
+    double *xout = src_tmp ? Bx.pf[Bx.cur] : Bx.xtmp;
+    const float4 *fin = Bx.xf[src_tmp], *vin = Bx.vf[src_tmp];
+    float4 *fout = Bx.xf[1 - src_tmp], *vout = Bx.vf[1 - src_tmp], *oout = Bx.of[1 - src_tmp];
+    const double *pf = Bx.pf[Bx.cur];
+    const long long cap = Bx.cap;
+    const Geom g = Bx.g;
+    const Phys &ph = Bx.ph;
+    const double rng_extra = ph.lubrication ? fmax(ph.h_c, 0.0) : 0.0;
+    double xi[3], ui[3], wi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xi[a] = xin[a * cap + i];
+        ui[a] = xin[(3 + a) * cap + i];
+        wi[a] = xin[(6 + a) * cap + i];
+    }
+    const float4 pi = fin[i], vi = vin[i];
+    const double di = pf[PD * cap + i];
+    const double mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
+    // walls: the faces of every non-periodic axis (m_ij = m_i, <d> = 2 d_i)
+    const double zero[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (g.per[a]) continue;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const double dist = side == 0 ? xi[a] : g.n[a] - xi[a];
+            const double range = 0.5 * di + rng_extra;
+            if (!(dist < range)) continue;
+            double n[3] = {0, 0, 0};
+            n[a] = side == 0 ? -1.0 : 1.0;
+            partner<double>(pd, n, dist, 0.5 * di, ui, wi, di, zero, zero, mi, 2.0 * di, F, T, nlim);
+        }
+    }
+    // Eq. particle_motion, semi-implicit Euler with I = m d^2 / 10
+    const double I = mi * di * di / 10.0;
+    double d2 = 0.0, xn3[3], un3[3], wn3[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double Ft = pf[(PFH0 + a) * cap + i] + F[a];
+        const double un = ui[a] + ph.dt_dem * Ft / mi;
+        const double wn = wi[a] + ph.dt_dem * T[a] / I;
+        double xn = xi[a] + ph.dt_dem * un;
+        if (g.per[a]) {
+            const int L = g.n[a];
+            if (xn >= L) xn -= L;
+            else if (xn < 0.0) xn += L;
+            if (xn >= L || xn < 0.0) xn -= L * floor(xn / L);
+            if (xn >= L) xn -= L;
+        }
+        xn3[a] = xn;
+        un3[a] = un;
+        wn3[a] = wn;
+        xout[a * cap + i] = xn;
+        xout[(3 + a) * cap + i] = un;
+        xout[(6 + a) * cap + i] = wn;
+        const double dd = min_image(xn - pf[(PXS0 + a) * cap + i], g.n[a], g.per[a]);
+        d2 += dd * dd;
+    }
+    fout[i] = make_float4((float)xn3[0], (float)xn3[1], (float)xn3[2], pi.w);
+    vout[i] = make_float4((float)un3[0], (float)un3[1], (float)un3[2], vi.w);
+    oout[i] = make_float4((float)wn3[0], (float)wn3[1], (float)wn3[2], 0.f);
+    if (d2 > ph.skin_half2) atomicOr(Bx.status, ST_SKIN);
+    if (!(d2 < 1e30)) atomicOr(Bx.status, ST_NAN);
+    if (nlim) atomicAdd(&Bx.counters[CNT_LUB_LIMITED], (unsigned long long)nlim);
+}
+
 // ---- the substep ------------------------------------------------------------------
 // src_tmp = 0: read x/u/w (and the float positions) from the current set,
 // write the ping-pong buffers; src_tmp = 1: the other way round
-template <bool MIXED>
+template <bool MIXED, int LANES>
 __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
                                                      int ntiles, int src_tmp) {
+    const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &Bx = boxes[tl.box];
         const double *xin = src_tmp ? Bx.xtmp : Bx.pf[Bx.cur];
-        double *xout = src_tmp ? Bx.pf[Bx.cur] : Bx.xtmp;
         const float4 *fin = Bx.xf[src_tmp], *vin = Bx.vf[src_tmp], *oin = Bx.of[src_tmp];
-        float4 *fout = Bx.xf[1 - src_tmp], *vout = Bx.vf[1 - src_tmp], *oout = Bx.of[1 - src_tmp];
         const double *pf = Bx.pf[Bx.cur];
         const long long cap = Bx.cap;
         const Geom g = Bx.g;
@@ -230,121 +357,85 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
         const float Lf[3] = {(float)g.n[0], (float)g.n[1], (float)g.n[2]};
         const PairPar<double> pd = pair_par<double>(ph);
         const PairPar<float> pfl = pair_par<float>(ph);
-        for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
-            double xi[3], ui[3], wi[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                xi[a] = xin[a * cap + i];
-                ui[a] = xin[(3 + a) * cap + i];
-                wi[a] = xin[(6 + a) * cap + i];
-            }
-            const float4 pi = fin[i], vi = vin[i], oi = oin[i];
-            const double di = pf[PD * cap + i];
-            const double mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
+        // the trip count is uniform over the block: every lane reaches the shuffles
+        for (long long base = tl.begin; base < tl.end; base += ngrp) {
+            const long long i = base + grp;
+            const bool act = i < tl.end;
             double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
             float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};  // FP32 pairs of the mixed forms
             unsigned nlim = 0;
-            const int nn = Bx.nlist_n[i];
-            for (int k = 0; k < nn; ++k) {
-                const int j = Bx.nlist[(long long)k * cap + i];
-                const float4 pj = fin[j];
-                const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
-                const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
-                const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
-                const float sumr_f = 0.5f * (pi.w + pj.w);
-                const float fr = sumr_f + rng_extra_f + SCREEN_MARGIN;
-                const float d2f = fx * fx + fy * fy + fz * fz;
-                if (!(d2f < fr * fr)) continue;
-                if (MIXED) {
-                    // away from contact: the whole pair in FP32 from the float copies
-                    const float distf = sqrtf(d2f);
-                    if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
-                        if (!(distf < sumr_f + rng_extra_f)) continue;
-                        const float4 vj = vin[j], oj = oin[j];
-                        const float inv = 1.0f / distf;
-                        const float n[3] = {fx * inv, fy * inv, fz * inv};
-                        const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
-                        const float uj[3] = {vj.x, vj.y, vj.z};
-                        const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
-                        const float m_ij = vi.w * vj.w / (vi.w + vj.w);
-                        const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
-                        partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf, nlim);
-                        continue;
+            if (act) {
+                // FP64 state of i: in registers for the FP64 form only
+                double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, wi[3] = {0, 0, 0}, di = 0, mi = 0;
+                if (!MIXED) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        xi[a] = xin[a * cap + i];
+                        ui[a] = xin[(3 + a) * cap + i];
+                        wi[a] = xin[(6 + a) * cap + i];
                     }
+                    di = pf[PD * cap + i];
+                    mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
                 }
-                // exact separation and forces in FP64
-                double dx[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) dx[a] = min_image(xin[a * cap + j] - xi[a], g.n[a], g.per[a]);
-                const double dist2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
-                const double dj = pf[PD * cap + j];
-                const double sumr = 0.5 * (di + dj);
-                const double dist = sqrt(dist2);
-                if (!(dist < sumr + rng_extra) || dist == 0.0) continue;
-                const double mj = pf[PRHO * cap + j] * PI_D / 6.0 * dj * dj * dj;
-                const double m_ij = mi * mj / (mi + mj);
-                const double dmean = 2.0 * di * dj / (di + dj);
-                const double inv = 1.0 / dist;
-                const double n[3] = {dx[0] * inv, dx[1] * inv, dx[2] * inv};
-                double uj[3], wjh[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    uj[a] = xin[(3 + a) * cap + j];
-                    wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
+                const float4 pi = fin[i], vi = vin[i], oi = oin[i];
+                const int nn = Bx.nlist_n[i];
+                const int *row = Bx.nlist + i * (long long)Bx.maxn;
+                for (int k = lane; k < nn; k += LANES) {
+                    const int j = row[k];
+                    const float4 pj = fin[j];
+                    const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
+                    const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
+                    const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
+                    const float sumr_f = 0.5f * (pi.w + pj.w);
+                    const float fr = sumr_f + rng_extra_f + SCREEN_MARGIN;
+                    const float d2f = fx * fx + fy * fy + fz * fz;
+                    if (!(d2f < fr * fr)) continue;
+                    if (MIXED) {
+                        // away from contact: the whole pair in FP32 from the float copies
+                        const float distf = sqrtf(d2f);
+                        if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
+                            if (!(distf < sumr_f + rng_extra_f)) continue;
+                            const float4 vj = vin[j], oj = oin[j];
+                            const float inv = 1.0f / distf;
+                            const float n[3] = {fx * inv, fy * inv, fz * inv};
+                            const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
+                            const float uj[3] = {vj.x, vj.y, vj.z};
+                            const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
+                            const float m_ij = vi.w * vj.w / (vi.w + vj.w);
+                            const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
+                            partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf, nlim);
+                            continue;
+                        }
+                    }
+                    // exact separation and forces in FP64
+                    if (MIXED)
+                        pair64_out(Bx, xin, i, j, F, T, nlim);
+                    else
+                        pair64_body<true>(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
                 }
-                partner<double>(pd, n, dist, sumr, ui, wi, di, uj, wjh, m_ij, dmean, F, T, nlim);
             }
+            if (LANES > 1) {
+#pragma unroll
+                for (int o = LANES / 2; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
+                        T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
+                        if (MIXED) {
+                            Ff[a] += __shfl_xor_sync(0xffffffffu, Ff[a], o);
+                            Tf[a] += __shfl_xor_sync(0xffffffffu, Tf[a], o);
+                        }
+                    }
+                    nlim += __shfl_xor_sync(0xffffffffu, nlim, o);
+                }
+            }
+            if (!act || lane != 0) continue;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 F[a] += (double)Ff[a];
                 T[a] += (double)Tf[a];
             }
-            // walls: the faces of every non-periodic axis (m_ij = m_i, <d> = 2 d_i)
-            const double zero[3] = {0, 0, 0};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (g.per[a]) continue;
-#pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const double dist = side == 0 ? xi[a] : g.n[a] - xi[a];
-                    const double range = 0.5 * di + rng_extra;
-                    if (!(dist < range)) continue;
-                    double n[3] = {0, 0, 0};
-                    n[a] = side == 0 ? -1.0 : 1.0;
-                    partner<double>(pd, n, dist, 0.5 * di, ui, wi, di, zero, zero, mi, 2.0 * di, F, T, nlim);
-                }
-            }
-            // Eq. particle_motion, semi-implicit Euler with I = m d^2 / 10
-            const double I = mi * di * di / 10.0;
-            double d2 = 0.0, xn3[3], un3[3], wn3[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double Ft = pf[(PFH0 + a) * cap + i] + F[a];
-                const double un = ui[a] + ph.dt_dem * Ft / mi;
-                const double wn = wi[a] + ph.dt_dem * T[a] / I;
-                double xn = xi[a] + ph.dt_dem * un;
-                if (g.per[a]) {
-                    const int L = g.n[a];
-                    if (xn >= L) xn -= L;
-                    else if (xn < 0.0) xn += L;
-                    if (xn >= L || xn < 0.0) xn -= L * floor(xn / L);
-                    if (xn >= L) xn -= L;
-                }
-                xn3[a] = xn;
-                un3[a] = un;
-                wn3[a] = wn;
-                xout[a * cap + i] = xn;
-                xout[(3 + a) * cap + i] = un;
-                xout[(6 + a) * cap + i] = wn;
-                const double dd = min_image(xn - pf[(PXS0 + a) * cap + i], g.n[a], g.per[a]);
-                d2 += dd * dd;
-            }
-            fout[i] = make_float4((float)xn3[0], (float)xn3[1], (float)xn3[2], pi.w);
-            vout[i] = make_float4((float)un3[0], (float)un3[1], (float)un3[2], vi.w);
-            oout[i] = make_float4((float)wn3[0], (float)wn3[1], (float)wn3[2], 0.f);
-            if (d2 > ph.skin_half2) atomicOr(Bx.status, ST_SKIN);
-            if (!(d2 < 1e30)) atomicOr(Bx.status, ST_NAN);
-            if (nlim) atomicAdd(&Bx.counters[CNT_LUB_LIMITED], (unsigned long long)nlim);
+            finish_particle(Bx, pd, i, src_tmp, F, T, nlim);
         }
     }
 }
@@ -353,12 +444,22 @@ void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int 
     k_build_nlist<<<grid, block, 0, s>>>(boxes, tiles, ntiles);
 }
 
-void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int src_tmp, int mixed, int grid,
-                        int block, cudaStream_t s) {
-    if (mixed)
-        k_dem_substep<true><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp);
-    else
-        k_dem_substep<false><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp);
+// lanes: 1, 2, 4 or 8 lanes per particle (block a multiple of 32)
+void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int src_tmp, int mixed, int lanes,
+                        int grid, int block, cudaStream_t s) {
+#define DPS_DEM(M, L) k_dem_substep<M, L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp)
+    if (mixed) {
+        if (lanes >= 8) DPS_DEM(true, 8);
+        else if (lanes == 4) DPS_DEM(true, 4);
+        else if (lanes == 2) DPS_DEM(true, 2);
+        else DPS_DEM(true, 1);
+    } else {
+        if (lanes >= 8) DPS_DEM(false, 8);
+        else if (lanes == 4) DPS_DEM(false, 4);
+        else if (lanes == 2) DPS_DEM(false, 2);
+        else DPS_DEM(false, 1);
+    }
+#undef DPS_DEM
 }
 
 }  // namespace dps
