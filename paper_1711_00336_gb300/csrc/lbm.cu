@@ -112,25 +112,102 @@ __device__ __forceinline__ CT tau_cell(const CT f[Q], CT s, CT rho, CT ux, CT uy
 // as soon as it is computed, which keeps few values live.  VISC: the box may
 // relax with a per-cell tau_e (vmode bit 0 Eilers, bit 1 Smagorinsky).
 template <typename ST, typename FT, typename CT, int PAR, bool VISC>
+__device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], const NbDelta &D, bool in,
+                                                 const Geom &g, CT e, CT fpx, CT fpy, CT fpz, long long N, long long c,
+                                                 CT fbx, CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
+                                                 int *status);
+
+template <typename ST, typename FT, typename CT, int PAR, bool VISC>
 __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const FT *__restrict__ eps,
                                                     const FT *__restrict__ fpf, const Geom &g, long long c, CT fbx,
                                                     CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
                                                     int *status) {
-    constexpr bool DEV = Store<ST>::shifted;
     const long long N = g.ncell;
     NbDelta D;
+    bool in = false;
+    CT f[Q];
     if (PAR) {
         int ix, iy, iz;
         cell_coords(g, c, ix, iy, iz);
-        D = neighbour_deltas(g, ix, iy, iz);
+        in = interior_cell(g, ix, iy, iz);
+        if (in) {
+            load_pdfs_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c, (unsigned)g.n[0],
+                                       (unsigned)g.n[0] * (unsigned)g.n[1], f);
+        } else {
+            D = neighbour_deltas(g, ix, iy, iz);
+            load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
+        }
+    } else {
+        load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
     }
-    CT f[Q];
-    load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
-    const CT e = (CT)eps[c];
+    relax_store_cell<ST, FT, CT, PAR, VISC>(pdf, f, D, in, g, (CT)eps[c], (CT)fpf[c], (CT)fpf[N + c],
+                                            (CT)fpf[2 * N + c], N, c, fbx, fby, fbz, omega_box, kf_box, tau, vmode,
+                                            status);
+}
+
+// two cells per thread (c and c + stride): the loads of both are issued before
+// either is relaxed, which doubles the bytes in flight per warp
+template <typename ST, typename FT, typename CT, int PAR, bool VISC>
+__device__ __forceinline__ void collide_stream_cell2(ST *__restrict__ pdf, const FT *__restrict__ eps,
+                                                     const FT *__restrict__ fpf, const Geom &g, long long c,
+                                                     long long c2, bool two, CT fbx, CT fby, CT fbz, CT omega_box,
+                                                     CT kf_box, CT tau, int vmode, int *status) {
+    const long long N = g.ncell;
+    const unsigned nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
+    NbDelta D, D2;
+    bool in = false, in2 = false;
+    CT f[Q], f2[Q];
+    if (PAR) {
+        int ix, iy, iz;
+        cell_coords(g, c, ix, iy, iz);
+        in = interior_cell(g, ix, iy, iz);
+        if (in) {
+            load_pdfs_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c, nx, nxy, f);
+        } else {
+            D = neighbour_deltas(g, ix, iy, iz);
+            load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
+        }
+        if (two) {
+            cell_coords(g, c2, ix, iy, iz);
+            in2 = interior_cell(g, ix, iy, iz);
+            if (in2) {
+                load_pdfs_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c2, nx, nxy, f2);
+            } else {
+                D2 = neighbour_deltas(g, ix, iy, iz);
+                load_pdfs<ST, CT, PAR>(pdf, N, c2, D2, f2);
+            }
+        }
+    } else {
+        load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
+        if (two) load_pdfs<ST, CT, PAR>(pdf, N, c2, D2, f2);
+    }
+    const CT e = (CT)eps[c], e2 = two ? (CT)eps[c2] : CT(1);
+    const CT a0 = (CT)fpf[c], a1 = (CT)fpf[N + c], a2 = (CT)fpf[2 * N + c];
+    CT b0 = 0, b1 = 0, b2 = 0;
+    if (two) {
+        b0 = (CT)fpf[c2];
+        b1 = (CT)fpf[N + c2];
+        b2 = (CT)fpf[2 * N + c2];
+    }
+    relax_store_cell<ST, FT, CT, PAR, VISC>(pdf, f, D, in, g, e, a0, a1, a2, N, c, fbx, fby, fbz, omega_box, kf_box,
+                                            tau, vmode, status);
+    if (two)
+        relax_store_cell<ST, FT, CT, PAR, VISC>(pdf, f2, D2, in2, g, e2, b0, b1, b2, N, c2, fbx, fby, fbz,
+                                                omega_box, kf_box, tau, vmode, status);
+}
+
+// relaxation (Eq. LBM_Equation) and parity-aware stores of one cell whose
+// populations f, eps_f and f_pf are already loaded
+template <typename ST, typename FT, typename CT, int PAR, bool VISC>
+__device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], const NbDelta &D, bool in,
+                                                 const Geom &g, CT e, CT fpx, CT fpy, CT fpz, long long N, long long c,
+                                                 CT fbx, CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
+                                                 int *status) {
+    constexpr bool DEV = Store<ST>::shifted;
     // f_ext = f_pf + eps_f f_b (Eq. Forcing)
-    const CT Fx = (CT)fpf[c] + e * fbx;
-    const CT Fy = (CT)fpf[N + c] + e * fby;
-    const CT Fz = (CT)fpf[2 * N + c] + e * fbz;
+    const CT Fx = fpx + e * fbx;
+    const CT Fy = fpy + e * fby;
+    const CT Fz = fpz + e * fbz;
     CT s = f[0], jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
@@ -173,7 +250,12 @@ __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const 
         if (CZ(k) != 0) { cu += CZ(k) * uz; cF += CZ(k) * Fz; }
         const CT E = w * (e0 + f0 + cu * (k1 * cu + k2 * cF));
         const CT O = w * (k3 * cu + k4 * cF);
-        store_pair<ST, CT, PAR>(pdf, N, c, D, k, om1 * f[k] + (E + O), om1 * f[k + 9] + (E - O));
+        if (PAR && in)
+            store_pair_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c, (unsigned)g.n[0],
+                                        (unsigned)g.n[0] * (unsigned)g.n[1], k, om1 * f[k] + (E + O),
+                                        om1 * f[k + 9] + (E - O));
+        else
+            store_pair<ST, CT, PAR>(pdf, N, c, D, k, om1 * f[k] + (E + O), om1 * f[k + 9] + (E - O));
     }
 }
 
@@ -182,7 +264,7 @@ template <> __device__ __forceinline__ double pick<double>(double d, float) { re
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 // K1: every cell tile of every box, AA parity PAR (common to the batch)
-template <typename ST, typename FT, typename CT, int PAR, int MINB, bool VISC>
+template <typename ST, typename FT, typename CT, int PAR, int MINB, bool VISC, int CPT>
 __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__restrict__ boxes,
                                                            const Tile *__restrict__ tiles, int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
@@ -197,8 +279,17 @@ __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__re
         const CT tau = (CT)B.ph.tau;
         const int vmode = VISC ? (B.ph.eilers ? 1 : 0) | (B.ph.smag ? 2 : 0) : 0;
         int *st = B.status;
-        for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
-            collide_stream_cell<ST, FT, CT, PAR, VISC>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, tau, vmode, st);
+        if (CPT == 1) {
+            for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
+                collide_stream_cell<ST, FT, CT, PAR, VISC>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, tau, vmode,
+                                                           st);
+        } else {
+            for (long long c = tl.begin + threadIdx.x; c < tl.end; c += 2 * blockDim.x) {
+                const long long c2 = c + blockDim.x;
+                collide_stream_cell2<ST, FT, CT, PAR, VISC>(pdf, eps, fpf, g, c, c2, c2 < tl.end, fbx, fby, fbz,
+                                                            omega, kf, tau, vmode, st);
+            }
+        }
     }
 }
 
@@ -403,31 +494,39 @@ static int grid_for(long long n, int block) {
 }
 
 // variant: register budget of K1 (blocks of 128 threads per SM the compiler
-// must fit); chosen by the batch autotuner.  visc: some box of the batch
+// must fit) and cells per thread (variants 3, 4: two); chosen by the batch
+// autotuner.  visc: some box of the batch
 // relaxes with a per-cell tau_e (one register budget for that variant).
 template <typename ST, typename FT, typename CT>
 void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, int parity, int variant, bool visc,
                            int grid, int block, cudaStream_t s) {
     block = 128;
     if (sizeof(CT) == 8) variant = 0;  // FP64: one register-heavy variant
-#define DPS_K1V(MB, V)                                                                            \
-    do {                                                                                          \
-        if (parity)                                                                               \
-            k_collide_stream<ST, FT, CT, 1, MB, V><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
-        else                                                                                      \
-            k_collide_stream<ST, FT, CT, 0, MB, V><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
+#define DPS_K1V(MB, V, CPT)                                                                            \
+    do {                                                                                               \
+        if (parity)                                                                                    \
+            k_collide_stream<ST, FT, CT, 1, MB, V, CPT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
+        else                                                                                           \
+            k_collide_stream<ST, FT, CT, 0, MB, V, CPT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
     } while (0)
-#define DPS_K1(MB) DPS_K1V(MB, false)
-    if (visc)
-        DPS_K1V(sizeof(CT) == 8 ? 2 : 3, true);
-    else if (sizeof(CT) == 8)
-        DPS_K1(2);
+#define DPS_K1(MB, CPT) DPS_K1V(MB, false, CPT)
+    if constexpr (sizeof(CT) == 8) {
+        if (visc)
+            DPS_K1V(2, true, 1);
+        else
+            DPS_K1(2, 1);
+    } else if (visc)
+        DPS_K1V(3, true, 1);
     else if (variant == 1)
-        DPS_K1(3);
+        DPS_K1(3, 1);
     else if (variant == 2)
-        DPS_K1(5);
+        DPS_K1(5, 1);
+    else if (variant == 3)
+        DPS_K1(3, 2);
+    else if (variant == 4)
+        DPS_K1(4, 2);
     else
-        DPS_K1(4);
+        DPS_K1(4, 1);
 #undef DPS_K1
 #undef DPS_K1V
 }

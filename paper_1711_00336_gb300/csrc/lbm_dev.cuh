@@ -103,6 +103,36 @@ __device__ __forceinline__ void store_pair(ST *__restrict__ pdf, long long N, lo
     }
 }
 
+// interior cells (no neighbour across a face of the box, periodic or wall):
+// the odd-parity neighbours are at the fixed offsets c -+ (c_x + c_y nx +
+// c_z nx ny), with no wrap or bounce-back to resolve
+__device__ __forceinline__ bool interior_cell(const Geom &g, int ix, int iy, int iz) {
+    return ix > 0 && ix < g.n[0] - 1 && iy > 0 && iy < g.n[1] - 1 && iz > 0 && iz < g.n[2] - 1;
+}
+
+__device__ __forceinline__ unsigned lattice_offset(int q, unsigned nx, unsigned nxy) {
+    return (unsigned)CX(q) + (unsigned)CY(q) * nx + (unsigned)CZ(q) * nxy;  // modulo 2^32
+}
+
+// odd parity, interior cell: f_q(x) sits in plane opp(q) of x - c_q
+template <typename ST, typename CT>
+__device__ __forceinline__ void load_pdfs_interior(const ST *__restrict__ pdf, unsigned N, unsigned c, unsigned nx,
+                                                   unsigned nxy, CT f[Q]) {
+    f[0] = Store<ST>::load(pdf + c);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) f[q] = Store<ST>::load(pdf + ((unsigned)OPP(q) * N + c - lattice_offset(q, nx, nxy)));
+}
+
+// odd parity, interior cell: the post-collision pair (k, k+9) goes to the
+// downstream cells x + c_k (plane k) and x - c_k (plane k+9)
+template <typename ST, typename CT>
+__device__ __forceinline__ void store_pair_interior(ST *__restrict__ pdf, unsigned N, unsigned c, unsigned nx,
+                                                    unsigned nxy, int k, CT vk, CT vo) {
+    const unsigned d = lattice_offset(k, nx, nxy);
+    Store<ST>::store(pdf + ((unsigned)k * N + c + d), vk);
+    Store<ST>::store(pdf + ((unsigned)(k + 9) * N + c - d), vo);
+}
+
 template <typename CT>
 __device__ __forceinline__ void moments(const CT f[Q], CT &rho, CT &jx, CT &jy, CT &jz) {
     // pair sums: direction q and its opposite q+9

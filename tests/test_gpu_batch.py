@@ -102,7 +102,7 @@ def test_autotune_keeps_a_valid_shape_and_removal_leaves_others_untouched():
     assert ms > 0
     cfg = B.tuning()
     assert cfg[0] % 32 == 0 and cfg[2] % 32 == 0
-    steps_done = (1 + 2) * (6 + 2 + 5)  # capture step + timed steps of each of the 13 candidates
+    steps_done = (1 + 2) * (6 + 4 + 5)  # capture step + timed steps of each of the 15 candidates
     B.remove_box(ids[1])
     B.step(3)
     r, _ = _alone(dps, wls[0], "f32", steps_done + 3)
