@@ -481,10 +481,12 @@ def suite_batch(dps, steps=20, count=64):
     return line
 
 
-def suite_serve(dps, n_req=24, rate=20.0, cap=2000, seed=11):
-    """Poisson-arriving settling requests (edge log-uniform 32..160, eps
-    U(0.01, 0.45), d = 1, FP32) on the continuous-batching server; every 20th
-    request is rerun alone with the plain FP64 method."""
+def suite_serve(dps, n_req=12, rate=20.0, cap=400, window=100, seed=11):
+    """A bounded trace of the serving workload: n_req Poisson-arriving
+    settling requests (edge log-uniform 32..160, eps U(0.01, 0.45), d = 1,
+    FP32) on the continuous-batching server, each run until its windowed mean
+    particle velocity changes by < 0.1 % between windows or the step cap;
+    every 20th request is rerun alone with the plain FP64 method."""
     rng = np.random.default_rng(seed)
     reqs = []
     for k in range(n_req):
@@ -501,7 +503,8 @@ def suite_serve(dps, n_req=24, rate=20.0, cap=2000, seed=11):
         if ta > now:
             time.sleep(ta - now)
         ids.append(S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"],
-                            _settling_closure(dps, wl, 1.0, n_int), max_steps=cap, window=500, rel_tol=1e-3))
+                            _settling_closure(dps, wl, 1.0, n_int), max_steps=cap, window=window,
+                            rel_tol=1e-3))
     S.wait_idle(3600)
     res = [S.poll(i) for i in ids]
     st = S.stats()
@@ -514,7 +517,7 @@ def suite_serve(dps, n_req=24, rate=20.0, cap=2000, seed=11):
         dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
         dom.set_closure(_settling_closure(dps, wl, 1.0, n_int))
         steps = res[k]["steps"]
-        w, acc = 500, np.zeros(3)
+        w, acc = window, np.zeros(3)
         dom.step(steps - w)
         for _ in range(w // 50):
             dom.step(50)
@@ -522,7 +525,7 @@ def suite_serve(dps, n_req=24, rate=20.0, cap=2000, seed=11):
         dom.close()
         um = acc / (w // 50)
         errs.append(abs(res[k]["up_mean"][2] - um[2]) / abs(um[2]))
-    line = {"suite": "serve", "requests": n_req, "rate_per_s": rate, "cap_steps": cap,
+    line = {"suite": "serve", "requests": n_req, "rate_per_s": rate, "cap_steps": cap, "window": window,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "aggregate_MLUPS": st["cell_updates"] / st["busy_s"] / 1e6 if st["busy_s"] > 0 else None,
             "completed": st["completed"], "failed": st["failed"], "peak_boxes": st["peak_boxes"],

@@ -4,7 +4,8 @@ visc_turb, tau_t, tau_e) inside the collide-stream kernel, and the shear lift
 force of Table 1 with the lattice curl of Sec. 3.2.3.
 
 Tolerances as for the plain method: FP64 1e-12 relative to the magnitude of
-the compared quantity; the FP32 form 1e-4 (relative L2 of the velocity field)."""
+the compared quantity (1e-10 for the lift force at vanishing vorticity, see
+the test); the FP32 form 1e-4 (relative L2 of the velocity field)."""
 import numpy as np
 import pytest
 
@@ -96,8 +97,12 @@ def test_lift_changes_the_trajectory_and_matches():
     kw = {**KW, "T_c": 2.0}
     dom, ref = _run_pair(n, per, 0.7, pr, 4, fb=(1e-5, 0, 0), n_int=1, n_dem=5, lift=1, **kw)
     got, r = dom.read_particles(), ref.particles()
-    close(got["u"], r["u"], what="u", floor=1e-3)
-    close(got["F"], r["F"], what="F", floor=1e-6)
+    # the shear layer starts from rest: where the vorticity w is still tiny the
+    # lattice curl (a difference of nearly equal velocities) carries a relative
+    # rounding error ~1e-16 |u|/|w|, and F_l ~ sqrt(|w|) passes it on, so the
+    # lift case is held to 1e-10 instead of 1e-12
+    close(got["u"], r["u"], rtol=1e-10, what="u", floor=1e-3)
+    close(got["F"], r["F"], rtol=1e-10, what="F", floor=1e-6)
     dom.close()
     ref0 = O.Domain(O.make_params(n, per, 0.7, g=(0, 0, -2e-3), f_b=(1e-5, 0, 0), n_int=1, n_dem=5, **kw),
                     x=pr["x"], u=pr["u"], w=pr["w"], d=pr["d"], rho_p=pr["rho_p"])
