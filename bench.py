@@ -231,8 +231,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--forms", default="f32,f16s", help="extra precision forms to time (comma list, '' for none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--suite", default="", help="precision,accuracy,batch,serve,rebound: measure the forms "
-                    "or the sphere-wall rebound instead")
+    ap.add_argument("--suite", default="", help="precision,accuracy,batch,serve,rebound,hindered: measure the "
+                    "forms, the sphere-wall rebound or hindered settling instead")
     args = ap.parse_args()
     if args.suite:
         run_suite(args)
@@ -590,6 +590,80 @@ def suite_rebound(dps, tau=0.501, rho_p=25.0, d=0.5):
     return out
 
 
+def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4), n_tst=30, prec="f32"):
+    """Sec. 4: hindered settling in a triply periodic 32^3 d_p box at the
+    paper's regime (water and glass of Baldock et al. scaled to lattice units
+    with d_p/dx = 1/2: rho_p/rho_f = 2.5, Re_T ~ 17), e_n = 0.88, mu_c = 0.25,
+    T_c = dt/2, h_c = d_p, n_int = 10, n_DEM = 50, all force models on and the
+    Sec. 4.1 body force on the fluid (fb_mode 2).  Each run lasts 30 t_St
+    (t_St = rho_p d^2/(18 mu)); <u_pS> = <u_p> - <u_f> is averaged over its
+    last 10 t_St and divided by the single sphere's u_pT from the eps = 0 run;
+    the Richardson-Zaki value (1 - eps)^kappa(Re_T) is printed beside it.
+    At eps = 0.3 the cases of Table 2 (A1 no lift, A2 no lubrication, A3 no
+    LES, A4 no Eilers, A5 n_int = 1) follow.  Runs in the FP32 form."""
+    L = int(round(32 * d))
+    d_phys, nu_phys, g_phys = 0.35e-3, 1e-6, 9.81
+    dx = d_phys / d
+    mu = (tau - 0.5) / 3.0
+    dt = mu * dx * dx / nu_phys
+    g = g_phys * dt * dt / dx
+    rho_p = 2.5
+    t_st = rho_p * d * d / (18.0 * mu)
+    steps = int(round(n_tst * t_st))
+    sample = max(1, int(round(t_st / 2)))
+
+    def run(eps, tag, **kw):
+        V = math.pi / 6 * d ** 3
+        if eps == 0.0:
+            x = np.array([[L / 2, L / 2, L / 2]])
+        else:
+            wl = workloads.settling_box(L=L, eps=eps, d=d, seed=int(eps * 1000) + 5)
+            x = wl["x"]
+        n = len(x)
+        c = dict(g=(0.0, 0.0, -g), fb_mode=2, e_n=0.88, mu_c=0.25, T_c=0.5, h_c=d, h_min=1e-5, C_am=0.5,
+                 n_int=10, n_dem=50, lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5, lift=1, eilers=1,
+                 smagorinsky=1)
+        c.update(kw)
+        dom = dps.Domain((L, L, L), (1, 1, 1), tau, prec, max_particles=n)
+        dom.add_particles(x, np.full(n, d), np.full(n, rho_p))
+        dom.set_closure(**c)
+        t0 = time.perf_counter()
+        acc, cnt, done = 0.0, 0, 0
+        while done < steps:
+            k = min(sample, steps - done)
+            dom.step(k)
+            done += k
+            if done > steps - 10 * t_st:
+                acc += float(dom.stats()["u_pS"][2])
+                cnt += 1
+        wall = time.perf_counter() - t0
+        dom.close()
+        return {"suite": "hindered", "case": tag, "eps": eps, "particles": n, "u_pS_z": acc / max(cnt, 1),
+                "steps": steps, "wall_s": wall}
+
+    out = []
+    single = run(0.0, "single")
+    u_T = -single["u_pS_z"]
+    Re_T = u_T * d / mu
+    kappa = 4.65 if Re_T < 0.2 else (4.35 * Re_T ** -0.03 if Re_T < 1 else (4.45 * Re_T ** -0.1 if Re_T < 500
+                                                                              else 2.39))
+    single.update({"u_pT": u_T, "Re_T": Re_T, "g_lattice": g, "tau": tau, "box": [L, L, L], "d": d})
+    print(json.dumps(single), flush=True)
+    cases = [(e, f"eps{e}", {}) for e in eps_list if e > 0]
+    cases += [(0.3, "A1_no_lift", {"lift": 0}), (0.3, "A2_no_lubrication", {"lubrication": 0}),
+              (0.3, "A3_no_LES", {"smagorinsky": 0}), (0.3, "A4_no_Eilers", {"eilers": 0}),
+              (0.3, "A5_n_int_1", {"n_int": 1, "n_dem": 500})]
+    paper = {"eps0.3": 0.288, "A1_no_lift": 0.297, "A2_no_lubrication": 0.288, "A3_no_LES": 0.288,
+             "A4_no_Eilers": 0.289, "A5_n_int_1": 0.288}
+    for eps, tag, kw in cases:
+        r = run(eps, tag, **kw)
+        r.update({"ratio": -r["u_pS_z"] / u_T, "richardson_zaki": (1 - eps) ** kappa, "Re_T": Re_T,
+                  "paper_table2": paper.get(tag)})
+        out.append(r)
+        print(json.dumps(r), flush=True)
+    return out
+
+
 def run_suite(args):
     import torch
     torch.cuda.set_device(0)
@@ -606,6 +680,8 @@ def run_suite(args):
         suite_serve(dps)
     if "rebound" in which:
         suite_rebound(dps)
+    if "hindered" in which:
+        suite_hindered(dps)
 
 
 if __name__ == "__main__":
