@@ -104,7 +104,7 @@ enum { PH_MOM = 0, PH_FAM, PH_RAM, PH_FDRAG, PH_RDRAG, PH_DEM, PH_SORT, PH_EPS, 
 struct Tuning {
     int cell_block = 128, cell_tile = 1024;   // threads per block, cells per tile
     int part_block = 128, part_tile = 256;    // threads per block, particles per tile
-    int k1v = 0;                              // collide-stream register-budget variant
+    int k1v = 3;                              // collide-stream variant (FP32/FP16: 2 cells per thread)
 };
 
 struct Batch {

@@ -507,12 +507,12 @@ __global__ void k_force_am(const BoxDev *__restrict__ boxes, const Tile *__restr
                     w[1] += W * curl[N + c];
                     w[2] += W * curl[2 * N + c];
                 });
-                const FT wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                const FT wn = m_sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
                 if (wn > FT(0)) {
                     const double dp = pf[PD * cap + p];
                     const FT du[3] = {uf[0] - (FT)pf[PU * cap + p], uf[1] - (FT)pf[PV * cap + p],
                                       uf[2] - (FT)pf[PW * cap + p]};
-                    const FT k = FT(1.61 * dp * dp) * sqrt((FT)(ph.mu * ph.rho_f) / wn);
+                    const FT k = FT(1.61 * dp * dp) * m_sqrt((FT)(ph.mu * ph.rho_f) / wn);
                     Fl[0] = k * (du[1] * w[2] - du[2] * w[1]);
                     Fl[1] = k * (du[2] * w[0] - du[0] * w[2]);
                     Fl[2] = k * (du[0] * w[1] - du[1] * w[0]);
@@ -597,7 +597,7 @@ __global__ void k_force_drag(const BoxDev *__restrict__ boxes, const Tile *__res
                 du[a] = uf[a] - (FT)pf[(PU + a) * cap + p];
                 dun += du[a] * du[a];
             }
-            dun = sqrt(dun);
+            dun = m_sqrt(dun);
             const FT mu = (FT)ph.mu, dd = (FT)d;
             const FT Re = ef * (FT)ph.rho_f * dd * dun / mu;
             const FT coef = ph.drag ? FT(3.0 * PI_D) * dd * mu * (FT(1) - ep) * drag_cd(Re, ep) : FT(0);

@@ -96,11 +96,11 @@ __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T di
             ut[a] = ur[a] - urn * n[a];
             Fn[a] = -k_n * delta * n[a] - xi * (urn * n[a]);
         }
-        const T Fn_abs = sqrt(Fn[0] * Fn[0] + Fn[1] * Fn[1] + Fn[2] * Fn[2]);
-        const T ut_abs = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+        const T Fn_abs = m_sqrt(Fn[0] * Fn[0] + Fn[1] * Fn[1] + Fn[2] * Fn[2]);
+        const T ut_abs = m_sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
         T Ft[3] = {0, 0, 0};
         if (ut_abs > T(0)) {
-            const T mag = fmin(ph.mu_c * Fn_abs, xi * ut_abs) / ut_abs;
+            const T mag = m_min(ph.mu_c * Fn_abs, xi * ut_abs) / ut_abs;
 #pragma unroll
             for (int a = 0; a < 3; ++a) Ft[a] = -mag * ut[a];
         }
@@ -116,14 +116,14 @@ __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T di
     // spring-dashpot acts alone, which keeps the wet rebound of Sec. 5)
     const T h = dist - sumr;
     if (ph.lubrication && h >= T(0) && h < ph.h_c) {
-        const T hh = fmax(h, ph.h_min);
+        const T hh = m_max(h, ph.h_min);
         const T r = dmean / hh;          // <d>/h
-        const T L = log(T(0.5) * r);     // ln(<d>/(2h))
+        const T L = m_log(T(0.5) * r);     // ln(<d>/(2h))
         T a_sq = T(1.5 * PI_D) * ph.mu * dmean * (T(0.25) * r + T(18.0 / 40.0) * L + T(9.0 / 84.0) * L / r);
         // a_sh (2/(h+<d>))^2 = (pi/2) mu <d> ln(<d>/(2h))
         T a_sh = T(0.5 * PI_D) * ph.mu * dmean * L;
-        a_sq = fmax(a_sq, T(0));
-        a_sh = fmax(a_sh, T(0));
+        a_sq = m_max(a_sq, T(0));
+        a_sh = m_max(a_sh, T(0));
         if (ph.lub_limiter) {
             const T cap = m_ij * ph.capfac;
             if (a_sq > cap) { a_sq = cap; ++nlim; }
@@ -304,13 +304,13 @@ __device__ __noinline__ void finish_particle(const BoxDev &Bx, const PairPar<dou
         }
     }
     // Eq. particle_motion, semi-implicit Euler with I = m d^2 / 10
-    const double I = mi * di * di / 10.0;
+    const double dt_m = ph.dt_dem / mi, dt_I = ph.dt_dem * 10.0 / (mi * di * di);
     double d2 = 0.0, xn3[3], un3[3], wn3[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double Ft = pf[(PFH0 + a) * cap + i] + F[a];
-        const double un = ui[a] + ph.dt_dem * Ft / mi;
-        const double wn = wi[a] + ph.dt_dem * T[a] / I;
+        const double un = ui[a] + dt_m * Ft;
+        const double wn = wi[a] + dt_I * T[a];
         double xn = xi[a] + ph.dt_dem * un;
         if (g.per[a]) {
             const int L = g.n[a];
@@ -364,6 +364,7 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
             double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
             float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};  // FP32 pairs of the mixed forms
             unsigned nlim = 0;
+            bool near = false;  // this lane evaluated an FP64 pair (mixed forms)
             if (act) {
                 // FP64 state of i: in registers for the FP64 form only
                 double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, wi[3] = {0, 0, 0}, di = 0, mi = 0;
@@ -408,19 +409,25 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                         }
                     }
                     // exact separation and forces in FP64
-                    if (MIXED)
+                    if (MIXED) {
+                        near = true;
                         pair64_out(Bx, xin, i, j, F, T, nlim);
-                    else
+                    } else
                         pair64_body<true>(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
                 }
             }
             if (LANES > 1) {
+                // FP64 sums: always in the FP64 form; in the mixed forms only
+                // when some lane of the warp met a pair near contact
+                const bool red64 = !MIXED || __any_sync(0xffffffffu, near);
 #pragma unroll
                 for (int o = LANES / 2; o > 0; o >>= 1) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
-                        T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
+                        if (red64) {
+                            F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
+                            T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
+                        }
                         if (MIXED) {
                             Ff[a] += __shfl_xor_sync(0xffffffffu, Ff[a], o);
                             Tf[a] += __shfl_xor_sync(0xffffffffu, Tf[a], o);

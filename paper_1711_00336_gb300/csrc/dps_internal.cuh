@@ -150,6 +150,19 @@ struct Phys {
     int eilers, smag;    // per-cell tau_e (Eqs. visc_eilers, tau_t, tau_e)
 };
 
+// ---- precision-preserving math -----------------------------------------------
+// The kernels are templated on their arithmetic type; these overloads call the
+// single-precision functions for float, so FP32 arithmetic never widens to
+// FP64 (whose pipe is a small fraction of the FP32 rate on this GPU).
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double m_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float m_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double m_max(double a, double b) { return fmax(a, b); }
+
 // ---- PDF storage traits ---------------------------------------------------
 // FP64 stores f_q itself; the low-precision forms store the deviation
 // f_q - w_q rho_0 (shifted populations) and do all arithmetic on deviations,

@@ -103,8 +103,8 @@ __device__ __forceinline__ CT tau_cell(const CT f[Q], CT s, CT rho, CT ux, CT uy
     const CT qxx = P[0] - iso - ri * ux * ux, qyy = P[1] - iso - ri * uy * uy, qzz = P[2] - iso - ri * uz * uz;
     const CT qxy = P[3] - ri * ux * uy, qxz = P[4] - ri * ux * uz, qyz = P[5] - ri * uy * uz;
     const CT q2 = qxx * qxx + qyy * qyy + qzz * qzz + CT(2) * (qxy * qxy + qxz * qxz + qyz * qyz);
-    const CT x = CT(2 * 0.01 * 9) * sqrt(CT(2) * q2) / rho;  // 2 C_S^2 Qbar / (rho c_s^4)
-    return ts + x / (CT(2) * (sqrt(ts * ts + x) + ts));
+    const CT x = CT(2 * 0.01 * 9) * m_sqrt(CT(2) * q2) / rho;  // 2 C_S^2 Qbar / (rho c_s^4)
+    return ts + x / (CT(2) * (m_sqrt(ts * ts + x) + ts));
 }
 
 // K1 body for one cell: load the 19 populations (AA parity PAR), relax them
@@ -196,6 +196,19 @@ __device__ __forceinline__ void collide_stream_cell2(ST *__restrict__ pdf, const
                                                 omega_box, kf_box, tau, vmode, status);
 }
 
+// Correctly rounded single operations: the relaxation below spells out every
+// multiply, add and fused multiply-add, so each K1 variant (register budget,
+// cells per thread) rounds exactly alike and a box's result does not depend on
+// the launch shape the autotuner picks.
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+
 // relaxation (Eq. LBM_Equation) and parity-aware stores of one cell whose
 // populations f, eps_f and f_pf are already loaded
 template <typename ST, typename FT, typename CT, int PAR, bool VISC>
@@ -205,57 +218,58 @@ __device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], 
                                                  int *status) {
     constexpr bool DEV = Store<ST>::shifted;
     // f_ext = f_pf + eps_f f_b (Eq. Forcing)
-    const CT Fx = fpx + e * fbx;
-    const CT Fy = fpy + e * fby;
-    const CT Fz = fpz + e * fbz;
+    const CT Fx = r_fma(e, fbx, fpx);
+    const CT Fy = r_fma(e, fby, fpy);
+    const CT Fz = r_fma(e, fbz, fpz);
     CT s = f[0], jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
-        s += f[k] + f[k + 9];
-        const CT d = f[k] - f[k + 9];
-        if (CX(k) != 0) jx += CX(k) * d;
-        if (CY(k) != 0) jy += CY(k) * d;
-        if (CZ(k) != 0) jz += CZ(k) * d;
+        s = r_add(s, r_add(f[k], f[k + 9]));
+        const CT d = r_sub(f[k], f[k + 9]);
+        if (CX(k) != 0) jx = CX(k) > 0 ? r_add(jx, d) : r_sub(jx, d);
+        if (CY(k) != 0) jy = CY(k) > 0 ? r_add(jy, d) : r_sub(jy, d);
+        if (CZ(k) != 0) jz = CZ(k) > 0 ? r_add(jz, d) : r_sub(jz, d);
     }
-    const CT rho = DEV ? CT(1) + s : s;
+    const CT rho = DEV ? r_add(CT(1), s) : s;
     if (!(rho > CT(0)) || !(rho < CT(1e30))) atomicOr(status, ST_NAN);
     const CT ir = CT(1) / rho;
-    const CT ux = (jx + CT(0.5) * Fx) * ir;  // Eq. MacVel
-    const CT uy = (jy + CT(0.5) * Fy) * ir;
-    const CT uz = (jz + CT(0.5) * Fz) * ir;
+    const CT ux = r_mul(r_fma(CT(0.5), Fx, jx), ir);  // Eq. MacVel
+    const CT uy = r_mul(r_fma(CT(0.5), Fy, jy), ir);
+    const CT uz = r_mul(r_fma(CT(0.5), Fz, jz), ir);
     const CT ie = CT(1) / e;
     CT omega = omega_box, kf = kf_box;
     if (VISC && vmode) {
         omega = CT(1) / tau_cell<CT, DEV>(f, s, rho, ux, uy, uz, e, ie, tau, vmode & 1, vmode & 2);
-        kf = CT(1) - CT(0.5) * omega;
+        kf = r_fma(CT(-0.5), omega, CT(1));
     }
-    const CT uu = ux * ux + uy * uy + uz * uz;
-    const CT uF = ux * Fx + uy * Fy + uz * Fz;
-    const CT om1 = CT(1) - omega;
-    const CT b2 = CT(-1.5) * uu * ie;
-    const CT e0 = DEV ? omega * (s + rho * b2) : omega * rho * (CT(1) + b2);
-    const CT f0 = CT(-3) * kf * uF * ie;
-    const CT k1 = omega * rho * CT(4.5) * ie, k2 = CT(9) * kf * ie;
-    const CT k3 = CT(3) * omega * rho, k4 = CT(3) * kf;
+    const CT uu = r_fma(ux, ux, r_fma(uy, uy, r_mul(uz, uz)));
+    const CT uF = r_fma(ux, Fx, r_fma(uy, Fy, r_mul(uz, Fz)));
+    const CT om1 = r_sub(CT(1), omega);
+    const CT b2 = r_mul(r_mul(CT(-1.5), uu), ie);
+    const CT e0 = DEV ? r_mul(omega, r_fma(rho, b2, s)) : r_mul(r_mul(omega, rho), r_add(CT(1), b2));
+    const CT f0 = r_mul(r_mul(r_mul(CT(-3), kf), uF), ie);
+    const CT ef = r_add(e0, f0);
+    const CT k1 = r_mul(r_mul(r_mul(omega, rho), CT(4.5)), ie), k2 = r_mul(r_mul(CT(9), kf), ie);
+    const CT k3 = r_mul(r_mul(CT(3), omega), rho), k4 = r_mul(CT(3), kf);
     {
-        const CT v = om1 * f[0] + (CT)WQ(0) * (e0 + f0);
+        const CT v = r_fma(om1, f[0], r_mul((CT)WQ(0), ef));
         Store<ST>::store(pdf + (unsigned)c, v);
     }
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
         const CT w = (CT)WQ(k);
         CT cu = 0, cF = 0;
-        if (CX(k) != 0) { cu += CX(k) * ux; cF += CX(k) * Fx; }
-        if (CY(k) != 0) { cu += CY(k) * uy; cF += CY(k) * Fy; }
-        if (CZ(k) != 0) { cu += CZ(k) * uz; cF += CZ(k) * Fz; }
-        const CT E = w * (e0 + f0 + cu * (k1 * cu + k2 * cF));
-        const CT O = w * (k3 * cu + k4 * cF);
+        if (CX(k) != 0) { cu = CX(k) > 0 ? r_add(cu, ux) : r_sub(cu, ux); cF = CX(k) > 0 ? r_add(cF, Fx) : r_sub(cF, Fx); }
+        if (CY(k) != 0) { cu = CY(k) > 0 ? r_add(cu, uy) : r_sub(cu, uy); cF = CY(k) > 0 ? r_add(cF, Fy) : r_sub(cF, Fy); }
+        if (CZ(k) != 0) { cu = CZ(k) > 0 ? r_add(cu, uz) : r_sub(cu, uz); cF = CZ(k) > 0 ? r_add(cF, Fz) : r_sub(cF, Fz); }
+        const CT E = r_mul(w, r_fma(cu, r_fma(k1, cu, r_mul(k2, cF)), ef));
+        const CT O = r_mul(w, r_fma(k3, cu, r_mul(k4, cF)));
+        const CT vk = r_fma(om1, f[k], r_add(E, O)), vo = r_fma(om1, f[k + 9], r_sub(E, O));
         if (PAR && in)
             store_pair_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c, (unsigned)g.n[0],
-                                        (unsigned)g.n[0] * (unsigned)g.n[1], k, om1 * f[k] + (E + O),
-                                        om1 * f[k + 9] + (E - O));
+                                        (unsigned)g.n[0] * (unsigned)g.n[1], k, vk, vo);
         else
-            store_pair<ST, CT, PAR>(pdf, N, c, D, k, om1 * f[k] + (E + O), om1 * f[k + 9] + (E - O));
+            store_pair<ST, CT, PAR>(pdf, N, c, D, k, vk, vo);
     }
 }
 

@@ -76,7 +76,8 @@ def test_launch_shape_does_not_change_results():
     dps = _dps()
     wl = _boxes()[1]
     res = []
-    for cfg in ([128, 1024, 128, 256, 0], [64, 256, 64, 64, 1], [256, 4096, 256, 512, 2]):
+    for cfg in ([128, 1024, 128, 256, 0], [64, 256, 64, 64, 1], [256, 4096, 256, 512, 2], [128, 2048, 32, 32, 3],
+                [256, 1024, 128, 128, 4]):
         B = dps.Batch("f32")
         b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
         B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
@@ -85,7 +86,8 @@ def test_launch_shape_does_not_change_results():
         B.step(4)
         res.append(B.read_particles(b)["u"])
         B.close()
-    assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
+    for r in res[1:]:
+        assert np.array_equal(res[0], r)
 
 
 def test_autotune_keeps_a_valid_shape_and_removal_leaves_others_untouched():

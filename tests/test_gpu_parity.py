@@ -288,3 +288,24 @@ def test_bad_arguments_raise():
     with pytest.raises(dps.DPSError):
         dom.set_closure(n_int=0)
     dom.close()
+
+
+@pytest.mark.parametrize("eps,d", [(0.05, 1.0), (0.12, 1.0), (0.3, 1.0), (0.35, 1.2)])
+def test_dense_box_lane_groups_match_the_oracle(eps, d):
+    """Dense periodic boxes give each particle 2, 4 or 8 lanes in the DEM
+    substep (long neighbour lists); the FP64 result still follows the oracle
+    pair by pair."""
+    dps = _dps()
+    L = 8
+    wl = workloads.settling_box(L=L, eps=eps, d=d, seed=3)
+    n = len(wl["x"])
+    rng = np.random.default_rng(5)
+    pr = dict(x=wl["x"], d=wl["d"], rho_p=wl["rho_p"], u=0.01 * rng.standard_normal((n, 3)),
+              w=0.01 * rng.standard_normal((n, 3)))
+    kw = {**KW, "h_c": d, "T_c": 1.0}
+    dom, ref = _run_pair((L, L, L), (1, 1, 1), 0.7, pr, 2, n_int=2, n_dem=5, **kw)
+    got, r = dom.read_particles(), ref.particles()
+    for k, fl_ in (("x", 0.0), ("u", 1e-3), ("w", 1e-3), ("F", 1e-6)):
+        close(got[k], r[k], what=k, floor=fl_)
+    close(dom.read_fields(("ubar",))["ubar"], ref.fields()["ubar"], what="ubar", floor=1e-3)
+    dom.close()
