@@ -209,13 +209,12 @@ __device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a
 __device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
 
-// relaxation (Eq. LBM_Equation) and parity-aware stores of one cell whose
-// populations f, eps_f and f_pf are already loaded
-template <typename ST, typename FT, typename CT, int PAR, bool VISC>
-__device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], const NbDelta &D, bool in,
-                                                 const Geom &g, CT e, CT fpx, CT fpy, CT fpz, long long N, long long c,
-                                                 CT fbx, CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
-                                                 int *status) {
+// relaxation (Eq. LBM_Equation) of one cell whose populations f, eps_f and
+// f_pf are loaded: f is overwritten with the post-collision populations.
+// `flag`: report a non-finite or non-positive density.
+template <typename ST, typename CT, bool VISC>
+__device__ __forceinline__ void relax_cell(CT f[Q], CT e, CT fpx, CT fpy, CT fpz, CT fbx, CT fby, CT fbz,
+                                           CT omega_box, CT kf_box, CT tau, int vmode, bool flag, int *status) {
     constexpr bool DEV = Store<ST>::shifted;
     // f_ext = f_pf + eps_f f_b (Eq. Forcing)
     const CT Fx = r_fma(e, fbx, fpx);
@@ -231,7 +230,7 @@ __device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], 
         if (CZ(k) != 0) jz = CZ(k) > 0 ? r_add(jz, d) : r_sub(jz, d);
     }
     const CT rho = DEV ? r_add(CT(1), s) : s;
-    if (!(rho > CT(0)) || !(rho < CT(1e30))) atomicOr(status, ST_NAN);
+    if (flag && (!(rho > CT(0)) || !(rho < CT(1e30)))) atomicOr(status, ST_NAN);
     const CT ir = CT(1) / rho;
     const CT ux = r_mul(r_fma(CT(0.5), Fx, jx), ir);  // Eq. MacVel
     const CT uy = r_mul(r_fma(CT(0.5), Fy, jy), ir);
@@ -251,10 +250,7 @@ __device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], 
     const CT ef = r_add(e0, f0);
     const CT k1 = r_mul(r_mul(r_mul(omega, rho), CT(4.5)), ie), k2 = r_mul(r_mul(CT(9), kf), ie);
     const CT k3 = r_mul(r_mul(CT(3), omega), rho), k4 = r_mul(CT(3), kf);
-    {
-        const CT v = r_fma(om1, f[0], r_mul((CT)WQ(0), ef));
-        Store<ST>::store(pdf + (unsigned)c, v);
-    }
+    f[0] = r_fma(om1, f[0], r_mul((CT)WQ(0), ef));
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
         const CT w = (CT)WQ(k);
@@ -265,11 +261,139 @@ __device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], 
         const CT E = r_mul(w, r_fma(cu, r_fma(k1, cu, r_mul(k2, cF)), ef));
         const CT O = r_mul(w, r_fma(k3, cu, r_mul(k4, cF)));
         const CT vk = r_fma(om1, f[k], r_add(E, O)), vo = r_fma(om1, f[k + 9], r_sub(E, O));
+        f[k] = vk;
+        f[k + 9] = vo;
+    }
+}
+
+// relaxation and parity-aware stores of one cell
+template <typename ST, typename FT, typename CT, int PAR, bool VISC>
+__device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], const NbDelta &D, bool in,
+                                                 const Geom &g, CT e, CT fpx, CT fpy, CT fpz, long long N, long long c,
+                                                 CT fbx, CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
+                                                 int *status) {
+    relax_cell<ST, CT, VISC>(f, e, fpx, fpy, fpz, fbx, fby, fbz, omega_box, kf_box, tau, vmode, true, status);
+    Store<ST>::store(pdf + (unsigned)c, f[0]);
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
         if (PAR && in)
             store_pair_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c, (unsigned)g.n[0],
-                                        (unsigned)g.n[0] * (unsigned)g.n[1], k, vk, vo);
+                                        (unsigned)g.n[0] * (unsigned)g.n[1], k, f[k], f[k + 9]);
         else
-            store_pair<ST, CT, PAR>(pdf, N, c, D, k, vk, vo);
+            store_pair<ST, CT, PAR>(pdf, N, c, D, k, f[k], f[k + 9]);
+    }
+}
+
+// ---- odd AA parity, warp-cooperative (low-precision forms) ------------------------
+// A warp takes 32 consecutive cells.  A population crossing x moves between
+// neighbouring lanes by a warp shuffle, so each lane loads and stores its own
+// x position of a plane (aligned and coalesced, where the plain odd step
+// touches every x-shifted plane one element off).  Lanes next to a face of the
+// box (wrap or bounce-back), on boundary rows in y or z, and at the ends of
+// the warp access memory directly.  Every plane element is still read and
+// written by one thread only (the one of the cell the AA pattern assigns it
+// to, or its x neighbour in the same warp).
+struct OddLane {
+    int ix, iy, iz;
+    unsigned lane;
+    bool act, yz, xlo, xhi, next_act;  // active, y/z interior row, x > 0, x < nx - 1, lane + 1 active
+};
+
+__device__ __forceinline__ OddLane odd_lane(const Geom &g, long long c, bool act) {
+    OddLane L;
+    L.lane = threadIdx.x & 31;
+    L.act = act;
+    L.ix = L.iy = L.iz = 0;
+    if (act) cell_coords(g, c, L.ix, L.iy, L.iz);
+    L.yz = L.iy > 0 && L.iy < g.n[1] - 1 && L.iz > 0 && L.iz < g.n[2] - 1;
+    L.xlo = L.ix > 0;
+    L.xhi = L.ix < g.n[0] - 1;
+    L.next_act = __shfl_down_sync(0xffffffffu, (int)act, 1) != 0 && L.lane < 31;
+    return L;
+}
+
+// linear delta to the neighbour (ix,iy,iz) + (dx,dy,dz), INV across a wall
+__device__ __forceinline__ int nb_offset(const Geom &g, const OddLane &L, int dx, int dy, int dz) {
+    const int ii[3] = {L.ix, L.iy, L.iz}, dd[3] = {dx, dy, dz};
+    const int stride[3] = {1, g.n[0], g.n[0] * g.n[1]};
+    int off = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (dd[a] == 0) continue;
+        const int t = ii[a] + dd[a];
+        if (t >= 0 && t < g.n[a]) off += dd[a] * stride[a];
+        else if (g.per[a]) off += (t < 0 ? g.n[a] - 1 : -(g.n[a] - 1)) * stride[a];
+        else return INV;
+    }
+    return off;
+}
+
+template <typename ST, typename CT>
+__device__ __forceinline__ void odd_warp_load(const ST *__restrict__ pdf, const Geom &g, unsigned N, unsigned c,
+                                              const OddLane &L, CT f[Q]) {
+    const unsigned nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
+    f[0] = L.act ? Store<ST>::load(pdf + c) : CT(0);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const unsigned yz = (unsigned)CY(q) * nx + (unsigned)CZ(q) * nxy;
+        const unsigned pl = (unsigned)OPP(q) * N;
+        CT v = CT(0);
+        bool direct = L.act;
+        if (CX(q) != 0) {
+            // upstream x - c_x is loaded by the x neighbour lane at its own x
+            const bool give = L.act && L.yz && (CX(q) > 0 ? (L.xhi && L.next_act) : (L.xlo && L.lane > 0));
+            const CT a = give ? Store<ST>::load(pdf + (pl + c - yz)) : CT(0);
+            const CT r = CX(q) > 0 ? __shfl_up_sync(0xffffffffu, a, 1) : __shfl_down_sync(0xffffffffu, a, 1);
+            const bool fast = L.act && L.yz && (CX(q) > 0 ? L.xlo : L.xhi);
+            const bool edge = CX(q) > 0 ? (L.lane == 0) : !L.next_act;
+            if (fast && !edge) {
+                v = r;
+                direct = false;
+            }
+        }
+        if (direct) {
+            if (L.yz && (CX(q) == 0 || (CX(q) > 0 ? L.xlo : L.xhi))) {
+                v = Store<ST>::load(pdf + (pl + c - (unsigned)CX(q) - yz));
+            } else {
+                const int dm = nb_offset(g, L, -CX(q), -CY(q), -CZ(q));
+                v = dm != INV ? Store<ST>::load(pdf + (pl + c + (unsigned)dm))
+                              : Store<ST>::load(pdf + ((unsigned)q * N + c));
+            }
+        }
+        f[q] = v;
+    }
+}
+
+template <typename ST, typename CT>
+__device__ __forceinline__ void odd_warp_store(ST *__restrict__ pdf, const Geom &g, unsigned N, unsigned c,
+                                               const OddLane &L, const CT f[Q]) {
+    const unsigned nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
+    if (L.act) Store<ST>::store(pdf + c, f[0]);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const unsigned yz = (unsigned)CY(q) * nx + (unsigned)CZ(q) * nxy;
+        const unsigned pl = (unsigned)q * N;
+        bool direct = L.act;
+        if (CX(q) != 0) {
+            // downstream x + c_x is stored by the x neighbour lane at its own x
+            const bool fast = L.act && L.yz && (CX(q) > 0 ? L.xhi : L.xlo);
+            const CT r = CX(q) > 0 ? __shfl_up_sync(0xffffffffu, f[q], 1) : __shfl_down_sync(0xffffffffu, f[q], 1);
+            const int pf = CX(q) > 0 ? __shfl_up_sync(0xffffffffu, (int)fast, 1)
+                                     : __shfl_down_sync(0xffffffffu, (int)fast, 1);
+            const bool recv = L.act && pf && (CX(q) > 0 ? L.lane > 0 : L.lane < 31);
+            if (recv) Store<ST>::store(pdf + (pl + c + yz), r);
+            const bool edge = CX(q) > 0 ? !L.next_act : (L.lane == 0);
+            if (fast && !edge) direct = false;
+        }
+        if (direct) {
+            if (L.yz && (CX(q) == 0 || (CX(q) > 0 ? L.xhi : L.xlo))) {
+                Store<ST>::store(pdf + (pl + c + (unsigned)CX(q) + yz), f[q]);
+            } else {
+                const int dp = nb_offset(g, L, CX(q), CY(q), CZ(q));
+                if (dp != INV) Store<ST>::store(pdf + (pl + c + (unsigned)dp), f[q]);
+                else Store<ST>::store(pdf + ((unsigned)OPP(q) * N + c), f[q]);  // bounce-back
+            }
+        }
     }
 }
 
@@ -293,7 +417,36 @@ __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__re
         const CT tau = (CT)B.ph.tau;
         const int vmode = VISC ? (B.ph.eilers ? 1 : 0) | (B.ph.smag ? 2 : 0) : 0;
         int *st = B.status;
-        if (CPT == 1) {
+        if constexpr (PAR == 1 && Store<ST>::shifted) {
+            // odd parity of the low-precision forms: warp-cooperative, CPT
+            // consecutive warp-blocks of cells per iteration
+            const long long N = g.ncell;
+            const long long lane = threadIdx.x & 31;
+            const long long stride = (long long)blockDim.x * CPT;
+            for (long long base = tl.begin + ((long long)threadIdx.x - lane); base < tl.end; base += stride) {
+                const long long ca = base + lane, cb = base + blockDim.x + lane;
+                const OddLane La = odd_lane(g, ca, ca < tl.end);
+                CT fa[Q], fb[Q];
+                odd_warp_load<ST, CT>(pdf, g, (unsigned)N, (unsigned)ca, La, fa);
+                OddLane Lb;
+                if (CPT == 2) {
+                    Lb = odd_lane(g, cb, cb < tl.end);
+                    odd_warp_load<ST, CT>(pdf, g, (unsigned)N, (unsigned)cb, Lb, fb);
+                }
+                {
+                    const long long c = La.act ? ca : tl.begin;
+                    relax_cell<ST, CT, VISC>(fa, (CT)eps[c], (CT)fpf[c], (CT)fpf[N + c], (CT)fpf[2 * N + c], fbx, fby,
+                                             fbz, omega, kf, tau, vmode, La.act, st);
+                    odd_warp_store<ST, CT>(pdf, g, (unsigned)N, (unsigned)ca, La, fa);
+                }
+                if (CPT == 2) {
+                    const long long c = Lb.act ? cb : tl.begin;
+                    relax_cell<ST, CT, VISC>(fb, (CT)eps[c], (CT)fpf[c], (CT)fpf[N + c], (CT)fpf[2 * N + c], fbx, fby,
+                                             fbz, omega, kf, tau, vmode, Lb.act, st);
+                    odd_warp_store<ST, CT>(pdf, g, (unsigned)N, (unsigned)cb, Lb, fb);
+                }
+            }
+        } else if (CPT == 1) {
             for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
                 collide_stream_cell<ST, FT, CT, PAR, VISC>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, tau, vmode,
                                                            st);
@@ -519,11 +672,14 @@ void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, i
 #define DPS_K1V(MB, V, CPT)                                                                            \
     do {                                                                                               \
         if (parity)                                                                                    \
-            k_collide_stream<ST, FT, CT, 1, MB, V, CPT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
+            k_collide_stream<ST, FT, CT, 1, MB, V, CPT_ODD(CPT)><<<grid, block, 0, s>>>(boxes, tiles, ntiles); \
         else                                                                                           \
             k_collide_stream<ST, FT, CT, 0, MB, V, CPT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
     } while (0)
 #define DPS_K1(MB, CPT) DPS_K1V(MB, false, CPT)
+// the warp-cooperative odd parity of the low-precision forms holds one cell
+// per thread (two would spill)
+#define CPT_ODD(CPT) (Store<ST>::shifted ? 1 : (CPT))
     if constexpr (sizeof(CT) == 8) {
         if (visc)
             DPS_K1V(2, true, 1);
@@ -543,6 +699,7 @@ void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, i
         DPS_K1(4, 1);
 #undef DPS_K1
 #undef DPS_K1V
+#undef CPT_ODD
 }
 
 template <typename ST, typename FT, typename CT>

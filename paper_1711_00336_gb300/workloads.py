@@ -10,7 +10,9 @@ Workloads (lattice units, Sec. 3.2.2):
                   sequential insertion (non-overlapping, seed 12345).
   settling_box    triply periodic L^3, spheres of diameter d at a solid volume
                   fraction eps: random sequential insertion below 0.3, above it a
-                  random subset of a jittered cubic lattice (non-overlapping).
+                  random subset of a jittered cubic lattice (non-overlapping);
+                  tau 0.55, rho_p/rho_f 2.5, gravity for a Stokes Reynolds
+                  number of 0.1.
 """
 import math
 
@@ -111,7 +113,7 @@ def settling_count(L, eps, d):
     return int(round(eps * L ** 3 / (math.pi / 6 * d ** 3)))
 
 
-def settling_box(L=64, eps=0.2, d=1.5, seed=1, tau=0.65, Re=0.1):
+def settling_box(L=64, eps=0.2, d=1.5, seed=1, tau=0.55, Re=0.1):
     count = settling_count(L, eps, d)
     if eps <= 0.3 and count <= 60000:
         x = rsa((L, L, L), (1, 1, 1), count, d, seed)
