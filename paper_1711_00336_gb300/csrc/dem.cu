@@ -264,11 +264,10 @@ __device__ __noinline__ void pair64_out(const BoxDev &Bx, const double *__restri
     pair64_body<false>(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
 }
 
-// lane 0 of a particle's group: wall partners, then Eq. particle_motion
-// (semi-implicit Euler) and the outputs of the substep; out of line, once
-// per particle
-__device__ __noinline__ void finish_particle(const BoxDev &Bx, const PairPar<double> &pd, long long i, int src_tmp,
-                                             double F[3], double T[3], unsigned nlim) {
+// one thread per particle: wall partners, then Eq. particle_motion
+// (semi-implicit Euler) and the outputs of the substep
+__device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<double> &pd, long long i,
+                                               int src_tmp, double F[3], double T[3], unsigned nlim) {
     const double *xin = src_tmp ? Bx.xtmp : Bx.pf[Bx.cur];
     double *xout = src_tmp ? Bx.pf[Bx.cur] : Bx.xtmp;
     const float4 *fin = Bx.xf[src_tmp], *vin = Bx.vf[src_tmp];
@@ -339,9 +338,16 @@ __device__ __noinline__ void finish_particle(const BoxDev &Bx, const PairPar<dou
 // ---- the substep ------------------------------------------------------------------
 // src_tmp = 0: read x/u/w (and the float positions) from the current set,
 // write the ping-pong buffers; src_tmp = 1: the other way round
+// particles per chunk of a tile: phase A (pair sums by lane groups) leaves
+// each particle's force and torque in shared memory, phase B integrates one
+// particle per thread, so the FP64 tail keeps every lane of a warp busy
+constexpr int DEM_CHUNK = 256;
+
 template <bool MIXED, int LANES>
 __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
                                                      int ntiles, int src_tmp) {
+    __shared__ double sFT[6][DEM_CHUNK];
+    __shared__ unsigned sN[DEM_CHUNK];
     const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
@@ -357,92 +363,107 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
         const float Lf[3] = {(float)g.n[0], (float)g.n[1], (float)g.n[2]};
         const PairPar<double> pd = pair_par<double>(ph);
         const PairPar<float> pfl = pair_par<float>(ph);
-        // the trip count is uniform over the block: every lane reaches the shuffles
-        for (long long base = tl.begin; base < tl.end; base += ngrp) {
-            const long long i = base + grp;
-            const bool act = i < tl.end;
-            double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-            float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};  // FP32 pairs of the mixed forms
-            unsigned nlim = 0;
-            bool near = false;  // this lane evaluated an FP64 pair (mixed forms)
-            if (act) {
-                // FP64 state of i: in registers for the FP64 form only
-                double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, wi[3] = {0, 0, 0}, di = 0, mi = 0;
-                if (!MIXED) {
+        for (long long cb = tl.begin; cb < tl.end; cb += DEM_CHUNK) {
+            const long long ce = cb + DEM_CHUNK < tl.end ? cb + DEM_CHUNK : tl.end;
+            // phase A: the trip count is uniform over the block, so every lane
+            // reaches the shuffles
+            for (long long base = cb; base < ce; base += ngrp) {
+                const long long i = base + grp;
+                const bool act = i < ce;
+                double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+                float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};  // FP32 pairs of the mixed forms
+                unsigned nlim = 0;
+                bool near = false;  // this lane evaluated an FP64 pair (mixed forms)
+                if (act) {
+                    // FP64 state of i: in registers for the FP64 form only
+                    double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, wi[3] = {0, 0, 0}, di = 0, mi = 0;
+                    if (!MIXED) {
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        xi[a] = xin[a * cap + i];
-                        ui[a] = xin[(3 + a) * cap + i];
-                        wi[a] = xin[(6 + a) * cap + i];
-                    }
-                    di = pf[PD * cap + i];
-                    mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
-                }
-                const float4 pi = fin[i], vi = vin[i], oi = oin[i];
-                const int nn = Bx.nlist_n[i];
-                const int *row = Bx.nlist + i * (long long)Bx.maxn;
-                for (int k = lane; k < nn; k += LANES) {
-                    const int j = row[k];
-                    const float4 pj = fin[j];
-                    const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
-                    const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
-                    const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
-                    const float sumr_f = 0.5f * (pi.w + pj.w);
-                    const float fr = sumr_f + rng_extra_f + SCREEN_MARGIN;
-                    const float d2f = fx * fx + fy * fy + fz * fz;
-                    if (!(d2f < fr * fr)) continue;
-                    if (MIXED) {
-                        // away from contact: the whole pair in FP32 from the float copies
-                        const float distf = sqrtf(d2f);
-                        if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
-                            if (!(distf < sumr_f + rng_extra_f)) continue;
-                            const float4 vj = vin[j], oj = oin[j];
-                            const float inv = 1.0f / distf;
-                            const float n[3] = {fx * inv, fy * inv, fz * inv};
-                            const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
-                            const float uj[3] = {vj.x, vj.y, vj.z};
-                            const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
-                            const float m_ij = vi.w * vj.w / (vi.w + vj.w);
-                            const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
-                            partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf, nlim);
-                            continue;
+                        for (int a = 0; a < 3; ++a) {
+                            xi[a] = xin[a * cap + i];
+                            ui[a] = xin[(3 + a) * cap + i];
+                            wi[a] = xin[(6 + a) * cap + i];
                         }
+                        di = pf[PD * cap + i];
+                        mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
                     }
-                    // exact separation and forces in FP64
-                    if (MIXED) {
-                        near = true;
-                        pair64_out(Bx, xin, i, j, F, T, nlim);
-                    } else
-                        pair64_body<true>(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
-                }
-            }
-            if (LANES > 1) {
-                // FP64 sums: always in the FP64 form; in the mixed forms only
-                // when some lane of the warp met a pair near contact
-                const bool red64 = !MIXED || __any_sync(0xffffffffu, near);
-#pragma unroll
-                for (int o = LANES / 2; o > 0; o >>= 1) {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        if (red64) {
-                            F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
-                            T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
-                        }
+                    const float4 pi = fin[i], vi = vin[i], oi = oin[i];
+                    const int nn = Bx.nlist_n[i];
+                    const int *row = Bx.nlist + i * (long long)Bx.maxn;
+                    for (int k = lane; k < nn; k += LANES) {
+                        const int j = row[k];
+                        const float4 pj = fin[j];
+                        const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
+                        const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
+                        const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
+                        const float sumr_f = 0.5f * (pi.w + pj.w);
+                        const float fr = sumr_f + rng_extra_f + SCREEN_MARGIN;
+                        const float d2f = fx * fx + fy * fy + fz * fz;
+                        if (!(d2f < fr * fr)) continue;
                         if (MIXED) {
-                            Ff[a] += __shfl_xor_sync(0xffffffffu, Ff[a], o);
-                            Tf[a] += __shfl_xor_sync(0xffffffffu, Tf[a], o);
+                            // away from contact: the whole pair in FP32 from the float copies
+                            const float distf = sqrtf(d2f);
+                            if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
+                                if (!(distf < sumr_f + rng_extra_f)) continue;
+                                const float4 vj = vin[j], oj = oin[j];
+                                const float inv = 1.0f / distf;
+                                const float n[3] = {fx * inv, fy * inv, fz * inv};
+                                const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
+                                const float uj[3] = {vj.x, vj.y, vj.z};
+                                const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
+                                const float m_ij = vi.w * vj.w / (vi.w + vj.w);
+                                const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
+                                partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf,
+                                               nlim);
+                                continue;
+                            }
                         }
+                        // exact separation and forces in FP64
+                        if (MIXED) {
+                            near = true;
+                            pair64_out(Bx, xin, i, j, F, T, nlim);
+                        } else
+                            pair64_body<true>(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
                     }
-                    nlim += __shfl_xor_sync(0xffffffffu, nlim, o);
+                }
+                if (LANES > 1) {
+                    // FP64 sums: always in the FP64 form; in the mixed forms only
+                    // when some lane of the warp met a pair near contact
+                    const bool red64 = !MIXED || __any_sync(0xffffffffu, near);
+#pragma unroll
+                    for (int o = LANES / 2; o > 0; o >>= 1) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            if (red64) {
+                                F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
+                                T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
+                            }
+                            if (MIXED) {
+                                Ff[a] += __shfl_xor_sync(0xffffffffu, Ff[a], o);
+                                Tf[a] += __shfl_xor_sync(0xffffffffu, Tf[a], o);
+                            }
+                        }
+                        nlim += __shfl_xor_sync(0xffffffffu, nlim, o);
+                    }
+                }
+                if (act && lane == 0) {
+                    const int s = (int)(i - cb);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        sFT[a][s] = F[a] + (double)Ff[a];
+                        sFT[3 + a][s] = T[a] + (double)Tf[a];
+                    }
+                    sN[s] = nlim;
                 }
             }
-            if (!act || lane != 0) continue;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                F[a] += (double)Ff[a];
-                T[a] += (double)Tf[a];
+            __syncthreads();
+            // phase B: walls and integration, one particle per thread
+            for (long long i = cb + threadIdx.x; i < ce; i += blockDim.x) {
+                const int s = (int)(i - cb);
+                double F[3] = {sFT[0][s], sFT[1][s], sFT[2][s]}, T[3] = {sFT[3][s], sFT[4][s], sFT[5][s]};
+                finish_particle(Bx, pd, i, src_tmp, F, T, sN[s]);
             }
-            finish_particle(Bx, pd, i, src_tmp, F, T, nlim);
+            __syncthreads();
         }
     }
 }

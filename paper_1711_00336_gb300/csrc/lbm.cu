@@ -332,35 +332,50 @@ template <typename ST, typename CT>
 __device__ __forceinline__ void odd_warp_load(const ST *__restrict__ pdf, const Geom &g, unsigned N, unsigned c,
                                               const OddLane &L, CT f[Q]) {
     const unsigned nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
-    f[0] = L.act ? Store<ST>::load(pdf + c) : CT(0);
+    // pass 1: every load a lane can make at its own x (issued together)
+    CT a[Q];
+    a[0] = L.act ? Store<ST>::load(pdf + c) : CT(0);
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         const unsigned yz = (unsigned)CY(q) * nx + (unsigned)CZ(q) * nxy;
         const unsigned pl = (unsigned)OPP(q) * N;
-        CT v = CT(0);
-        bool direct = L.act;
-        if (CX(q) != 0) {
-            // upstream x - c_x is loaded by the x neighbour lane at its own x
-            const bool give = L.act && L.yz && (CX(q) > 0 ? (L.xhi && L.next_act) : (L.xlo && L.lane > 0));
-            const CT a = give ? Store<ST>::load(pdf + (pl + c - yz)) : CT(0);
-            const CT r = CX(q) > 0 ? __shfl_up_sync(0xffffffffu, a, 1) : __shfl_down_sync(0xffffffffu, a, 1);
+        // c_x = 0: the lane's own upstream; c_x != 0: the x neighbour lane's upstream
+        const bool own = CX(q) == 0 ? (L.act && L.yz)
+                                    : (L.act && L.yz && (CX(q) > 0 ? (L.xhi && L.next_act) : (L.xlo && L.lane > 0)));
+        a[q] = own ? Store<ST>::load(pdf + (pl + c - yz)) : CT(0);
+    }
+    // pass 2: x-shifted populations from the neighbour lane
+    unsigned pending = 0;  // directions still to load directly
+    f[0] = a[0];
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        if (CX(q) == 0) {
+            f[q] = a[q];
+            if (L.act && !L.yz) pending |= 1u << q;
+        } else {
+            const CT r = CX(q) > 0 ? __shfl_up_sync(0xffffffffu, a[q], 1) : __shfl_down_sync(0xffffffffu, a[q], 1);
             const bool fast = L.act && L.yz && (CX(q) > 0 ? L.xlo : L.xhi);
             const bool edge = CX(q) > 0 ? (L.lane == 0) : !L.next_act;
-            if (fast && !edge) {
-                v = r;
-                direct = false;
-            }
+            f[q] = r;
+            if (L.act && !(fast && !edge)) pending |= 1u << q;
         }
-        if (direct) {
+    }
+    // pass 3: lanes at the warp ends, next to a face of the box or on y/z
+    // boundary rows load directly (issued together)
+    if (pending) {
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            if (!(pending & (1u << q))) continue;
+            const unsigned yz = (unsigned)CY(q) * nx + (unsigned)CZ(q) * nxy;
+            const unsigned pl = (unsigned)OPP(q) * N;
             if (L.yz && (CX(q) == 0 || (CX(q) > 0 ? L.xlo : L.xhi))) {
-                v = Store<ST>::load(pdf + (pl + c - (unsigned)CX(q) - yz));
+                f[q] = Store<ST>::load(pdf + (pl + c - (unsigned)CX(q) - yz));
             } else {
                 const int dm = nb_offset(g, L, -CX(q), -CY(q), -CZ(q));
-                v = dm != INV ? Store<ST>::load(pdf + (pl + c + (unsigned)dm))
-                              : Store<ST>::load(pdf + ((unsigned)q * N + c));
+                f[q] = dm != INV ? Store<ST>::load(pdf + (pl + c + (unsigned)dm))
+                                 : Store<ST>::load(pdf + ((unsigned)q * N + c));
             }
         }
-        f[q] = v;
     }
 }
 
