@@ -270,7 +270,7 @@ int dps_batch_stats(dps_batch b, int box, dps_stats *s);
 int dps_batch_particle_mean(dps_batch b, int box, double u[3]);
 int dps_batch_num_boxes(dps_batch b, int *n);
 /* launch shape: cfg = {cell threads/block, cells/tile, particle threads/block,
- * particles/tile, collide-stream variant 0 ... 4 (register budget and cells
+ * particles/tile, collide-stream variant 0 ... 5 (register budget and cells
  * per thread of the low-precision forms; ignored in FP64)} */
 int dps_batch_set_tuning(dps_batch b, const int cfg[5]);
 int dps_batch_get_tuning(dps_batch b, int cfg[5]);

@@ -1476,7 +1476,7 @@ int dps_batch_set_tuning(dps_batch b, const int cfg[5]) {
         if (cfg[k] < 32 || cfg[k] > (1 << 20)) FAILB(&b->B, DPS_ERR_ARG, "invalid launch shape");
     if (cfg[0] > 256 || cfg[2] > 256 || (cfg[0] & 31) || (cfg[2] & 31))
         FAILB(&b->B, DPS_ERR_ARG, "threads per block must be a multiple of 32, at most 256");
-    if (cfg[4] < 0 || cfg[4] > 4) FAILB(&b->B, DPS_ERR_ARG, "collide-stream variant must be 0 ... 4");
+    if (cfg[4] < 0 || cfg[4] > 5) FAILB(&b->B, DPS_ERR_ARG, "collide-stream variant must be 0 ... 5");
     int rc = pull_state(&b->B);
     if (rc) return rc;
     b->B.tune = Tuning{cfg[0], cfg[1], cfg[2], cfg[3], cfg[4]};
@@ -1532,7 +1532,7 @@ static int autotune(Batch *B, int steps, double *best_ms) {
         if (ms < bms) { bms = ms; best = t; }
     }
     if (!rc && B->prec != DPS_F64)
-        for (int v = 0; v < 5; ++v) {
+        for (int v = 0; v < 6; ++v) {
             if (v == best.k1v) continue;
             Tuning t = best;
             t.k1v = v;

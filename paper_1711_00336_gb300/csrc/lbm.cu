@@ -284,134 +284,6 @@ __device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], 
     }
 }
 
-// ---- odd AA parity, warp-cooperative (low-precision forms) ------------------------
-// A warp takes 32 consecutive cells.  A population crossing x moves between
-// neighbouring lanes by a warp shuffle, so each lane loads and stores its own
-// x position of a plane (aligned and coalesced, where the plain odd step
-// touches every x-shifted plane one element off).  Lanes next to a face of the
-// box (wrap or bounce-back), on boundary rows in y or z, and at the ends of
-// the warp access memory directly.  Every plane element is still read and
-// written by one thread only (the one of the cell the AA pattern assigns it
-// to, or its x neighbour in the same warp).
-struct OddLane {
-    int ix, iy, iz;
-    unsigned lane;
-    bool act, yz, xlo, xhi, next_act;  // active, y/z interior row, x > 0, x < nx - 1, lane + 1 active
-};
-
-__device__ __forceinline__ OddLane odd_lane(const Geom &g, long long c, bool act) {
-    OddLane L;
-    L.lane = threadIdx.x & 31;
-    L.act = act;
-    L.ix = L.iy = L.iz = 0;
-    if (act) cell_coords(g, c, L.ix, L.iy, L.iz);
-    L.yz = L.iy > 0 && L.iy < g.n[1] - 1 && L.iz > 0 && L.iz < g.n[2] - 1;
-    L.xlo = L.ix > 0;
-    L.xhi = L.ix < g.n[0] - 1;
-    L.next_act = __shfl_down_sync(0xffffffffu, (int)act, 1) != 0 && L.lane < 31;
-    return L;
-}
-
-// linear delta to the neighbour (ix,iy,iz) + (dx,dy,dz), INV across a wall
-__device__ __forceinline__ int nb_offset(const Geom &g, const OddLane &L, int dx, int dy, int dz) {
-    const int ii[3] = {L.ix, L.iy, L.iz}, dd[3] = {dx, dy, dz};
-    const int stride[3] = {1, g.n[0], g.n[0] * g.n[1]};
-    int off = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (dd[a] == 0) continue;
-        const int t = ii[a] + dd[a];
-        if (t >= 0 && t < g.n[a]) off += dd[a] * stride[a];
-        else if (g.per[a]) off += (t < 0 ? g.n[a] - 1 : -(g.n[a] - 1)) * stride[a];
-        else return INV;
-    }
-    return off;
-}
-
-template <typename ST, typename CT>
-__device__ __forceinline__ void odd_warp_load(const ST *__restrict__ pdf, const Geom &g, unsigned N, unsigned c,
-                                              const OddLane &L, CT f[Q]) {
-    const unsigned nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
-    // pass 1: every load a lane can make at its own x (issued together)
-    CT a[Q];
-    a[0] = L.act ? Store<ST>::load(pdf + c) : CT(0);
-#pragma unroll
-    for (int q = 1; q < Q; ++q) {
-        const unsigned yz = (unsigned)CY(q) * nx + (unsigned)CZ(q) * nxy;
-        const unsigned pl = (unsigned)OPP(q) * N;
-        // c_x = 0: the lane's own upstream; c_x != 0: the x neighbour lane's upstream
-        const bool own = CX(q) == 0 ? (L.act && L.yz)
-                                    : (L.act && L.yz && (CX(q) > 0 ? (L.xhi && L.next_act) : (L.xlo && L.lane > 0)));
-        a[q] = own ? Store<ST>::load(pdf + (pl + c - yz)) : CT(0);
-    }
-    // pass 2: x-shifted populations from the neighbour lane
-    unsigned pending = 0;  // directions still to load directly
-    f[0] = a[0];
-#pragma unroll
-    for (int q = 1; q < Q; ++q) {
-        if (CX(q) == 0) {
-            f[q] = a[q];
-            if (L.act && !L.yz) pending |= 1u << q;
-        } else {
-            const CT r = CX(q) > 0 ? __shfl_up_sync(0xffffffffu, a[q], 1) : __shfl_down_sync(0xffffffffu, a[q], 1);
-            const bool fast = L.act && L.yz && (CX(q) > 0 ? L.xlo : L.xhi);
-            const bool edge = CX(q) > 0 ? (L.lane == 0) : !L.next_act;
-            f[q] = r;
-            if (L.act && !(fast && !edge)) pending |= 1u << q;
-        }
-    }
-    // pass 3: lanes at the warp ends, next to a face of the box or on y/z
-    // boundary rows load directly (issued together)
-    if (pending) {
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            if (!(pending & (1u << q))) continue;
-            const unsigned yz = (unsigned)CY(q) * nx + (unsigned)CZ(q) * nxy;
-            const unsigned pl = (unsigned)OPP(q) * N;
-            if (L.yz && (CX(q) == 0 || (CX(q) > 0 ? L.xlo : L.xhi))) {
-                f[q] = Store<ST>::load(pdf + (pl + c - (unsigned)CX(q) - yz));
-            } else {
-                const int dm = nb_offset(g, L, -CX(q), -CY(q), -CZ(q));
-                f[q] = dm != INV ? Store<ST>::load(pdf + (pl + c + (unsigned)dm))
-                                 : Store<ST>::load(pdf + ((unsigned)q * N + c));
-            }
-        }
-    }
-}
-
-template <typename ST, typename CT>
-__device__ __forceinline__ void odd_warp_store(ST *__restrict__ pdf, const Geom &g, unsigned N, unsigned c,
-                                               const OddLane &L, const CT f[Q]) {
-    const unsigned nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
-    if (L.act) Store<ST>::store(pdf + c, f[0]);
-#pragma unroll
-    for (int q = 1; q < Q; ++q) {
-        const unsigned yz = (unsigned)CY(q) * nx + (unsigned)CZ(q) * nxy;
-        const unsigned pl = (unsigned)q * N;
-        bool direct = L.act;
-        if (CX(q) != 0) {
-            // downstream x + c_x is stored by the x neighbour lane at its own x
-            const bool fast = L.act && L.yz && (CX(q) > 0 ? L.xhi : L.xlo);
-            const CT r = CX(q) > 0 ? __shfl_up_sync(0xffffffffu, f[q], 1) : __shfl_down_sync(0xffffffffu, f[q], 1);
-            const int pf = CX(q) > 0 ? __shfl_up_sync(0xffffffffu, (int)fast, 1)
-                                     : __shfl_down_sync(0xffffffffu, (int)fast, 1);
-            const bool recv = L.act && pf && (CX(q) > 0 ? L.lane > 0 : L.lane < 31);
-            if (recv) Store<ST>::store(pdf + (pl + c + yz), r);
-            const bool edge = CX(q) > 0 ? !L.next_act : (L.lane == 0);
-            if (fast && !edge) direct = false;
-        }
-        if (direct) {
-            if (L.yz && (CX(q) == 0 || (CX(q) > 0 ? L.xhi : L.xlo))) {
-                Store<ST>::store(pdf + (pl + c + (unsigned)CX(q) + yz), f[q]);
-            } else {
-                const int dp = nb_offset(g, L, CX(q), CY(q), CZ(q));
-                if (dp != INV) Store<ST>::store(pdf + (pl + c + (unsigned)dp), f[q]);
-                else Store<ST>::store(pdf + ((unsigned)OPP(q) * N + c), f[q]);  // bounce-back
-            }
-        }
-    }
-}
-
 template <typename CT> __device__ __forceinline__ CT pick(double d, float f);
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
@@ -432,36 +304,7 @@ __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__re
         const CT tau = (CT)B.ph.tau;
         const int vmode = VISC ? (B.ph.eilers ? 1 : 0) | (B.ph.smag ? 2 : 0) : 0;
         int *st = B.status;
-        if constexpr (PAR == 1 && Store<ST>::shifted) {
-            // odd parity of the low-precision forms: warp-cooperative, CPT
-            // consecutive warp-blocks of cells per iteration
-            const long long N = g.ncell;
-            const long long lane = threadIdx.x & 31;
-            const long long stride = (long long)blockDim.x * CPT;
-            for (long long base = tl.begin + ((long long)threadIdx.x - lane); base < tl.end; base += stride) {
-                const long long ca = base + lane, cb = base + blockDim.x + lane;
-                const OddLane La = odd_lane(g, ca, ca < tl.end);
-                CT fa[Q], fb[Q];
-                odd_warp_load<ST, CT>(pdf, g, (unsigned)N, (unsigned)ca, La, fa);
-                OddLane Lb;
-                if (CPT == 2) {
-                    Lb = odd_lane(g, cb, cb < tl.end);
-                    odd_warp_load<ST, CT>(pdf, g, (unsigned)N, (unsigned)cb, Lb, fb);
-                }
-                {
-                    const long long c = La.act ? ca : tl.begin;
-                    relax_cell<ST, CT, VISC>(fa, (CT)eps[c], (CT)fpf[c], (CT)fpf[N + c], (CT)fpf[2 * N + c], fbx, fby,
-                                             fbz, omega, kf, tau, vmode, La.act, st);
-                    odd_warp_store<ST, CT>(pdf, g, (unsigned)N, (unsigned)ca, La, fa);
-                }
-                if (CPT == 2) {
-                    const long long c = Lb.act ? cb : tl.begin;
-                    relax_cell<ST, CT, VISC>(fb, (CT)eps[c], (CT)fpf[c], (CT)fpf[N + c], (CT)fpf[2 * N + c], fbx, fby,
-                                             fbz, omega, kf, tau, vmode, Lb.act, st);
-                    odd_warp_store<ST, CT>(pdf, g, (unsigned)N, (unsigned)cb, Lb, fb);
-                }
-            }
-        } else if (CPT == 1) {
+        if (CPT == 1) {
             for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
                 collide_stream_cell<ST, FT, CT, PAR, VISC>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, tau, vmode,
                                                            st);
@@ -687,14 +530,11 @@ void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, i
 #define DPS_K1V(MB, V, CPT)                                                                            \
     do {                                                                                               \
         if (parity)                                                                                    \
-            k_collide_stream<ST, FT, CT, 1, MB, V, CPT_ODD(CPT)><<<grid, block, 0, s>>>(boxes, tiles, ntiles); \
+            k_collide_stream<ST, FT, CT, 1, MB, V, CPT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
         else                                                                                           \
             k_collide_stream<ST, FT, CT, 0, MB, V, CPT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
     } while (0)
 #define DPS_K1(MB, CPT) DPS_K1V(MB, false, CPT)
-// the warp-cooperative odd parity of the low-precision forms holds one cell
-// per thread (two would spill)
-#define CPT_ODD(CPT) (Store<ST>::shifted ? 1 : (CPT))
     if constexpr (sizeof(CT) == 8) {
         if (visc)
             DPS_K1V(2, true, 1);
@@ -710,11 +550,12 @@ void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, i
         DPS_K1(3, 2);
     else if (variant == 4)
         DPS_K1(4, 2);
+    else if (variant == 5)
+        DPS_K1(2, 2);
     else
         DPS_K1(4, 1);
 #undef DPS_K1
 #undef DPS_K1V
-#undef CPT_ODD
 }
 
 template <typename ST, typename FT, typename CT>

@@ -77,7 +77,7 @@ def test_launch_shape_does_not_change_results():
     wl = _boxes()[1]
     res = []
     for cfg in ([128, 1024, 128, 256, 0], [64, 256, 64, 64, 1], [256, 4096, 256, 512, 2], [128, 2048, 32, 32, 3],
-                [256, 1024, 128, 128, 4]):
+                [256, 1024, 128, 128, 4], [128, 1024, 64, 256, 5]):
         B = dps.Batch("f32")
         b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
         B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
@@ -104,7 +104,7 @@ def test_autotune_keeps_a_valid_shape_and_removal_leaves_others_untouched():
     assert ms > 0
     cfg = B.tuning()
     assert cfg[0] % 32 == 0 and cfg[2] % 32 == 0
-    steps_done = (1 + 2) * (6 + 4 + 5)  # capture step + timed steps of each of the 15 candidates
+    steps_done = (1 + 2) * (6 + 5 + 5)  # capture step + timed steps of each of the 16 candidates
     B.remove_box(ids[1])
     B.step(3)
     r, _ = _alone(dps, wls[0], "f32", steps_done + 3)
