@@ -45,6 +45,42 @@ def algorithmic_bytes_collide(prec):
     return 2 * 19 * s + 4 * sf
 
 
+# FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA lanes) x 2.07 GHz maximum SM clock
+FP64_PEAK_GFLOPS = 152 * 4 * 2.07
+# algorithmic FP64 flops (a division, square root or logarithm counted as one)
+K1_FLOPS_F64 = 249        # per cell: moments 42, velocity and invariants 36, 9 pairs x 16 + 13 more
+DEM_FLOPS_PARTICLE = 38   # per particle and substep: mass, semi-implicit Euler of u, w, x, skin check
+DEM_FLOPS_PAIR = 75       # per interacting partner: separation 9, masses / normal 17, Ball-Melrose force 49
+# DRAM bytes per launch from one ncu capture of the same kernel and workload
+# (profiles/dem_substep_fp64_wall_suspension.md); None where no capture of the
+# current kernel exists
+TRAFFIC = {("dem_substep", "f64"): 1.424896e6}
+
+
+def lubrication_partners(x, d, n, periodic, h_c):
+    """Mean number of partners (spheres, and walls on the non-periodic axes)
+    within the lubrication range of a particle: the pairs a DEM substep
+    evaluates beyond the neighbour-list screening."""
+    x = np.asarray(x, float)
+    N = len(x)
+    L = np.asarray(n, float)
+    cnt = 0
+    for a0 in range(0, N, 512):
+        dx = x[a0:a0 + 512, None, :] - x[None, :, :]
+        for a in range(3):
+            if periodic[a]:
+                dx[..., a] -= L[a] * np.round(dx[..., a] / L[a])
+        dist = np.sqrt((dx * dx).sum(-1))
+        gap = dist - 0.5 * (d[a0:a0 + 512, None] + d[None, :])
+        ok = gap < h_c
+        ok[np.arange(ok.shape[0]), np.arange(a0, a0 + ok.shape[0])] = False
+        cnt += int(ok.sum())
+    for a in range(3):
+        if not periodic[a]:
+            cnt += int((x[:, a] - 0.5 * d < h_c).sum() + (L[a] - x[:, a] - 0.5 * d < h_c).sum())
+    return cnt / max(N, 1)
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -134,6 +170,7 @@ def time_device(dps, wl, prec, steps, warmup, flush, timing=True):
     phase = dom.get_timing(reset=True) if timing else None
     lps = dom.launches_per_step()
     st = dom.stats()
+    st["x_final"] = dom.read_particles()["x"]
     dom.close()
     return total, times, phase, lps, st
 
@@ -269,29 +306,55 @@ def main():
     ms_step = t_all / args.steps
 
     # roofline of the dominant kernel, measured live over the timed region
+    # (per-phase CUDA events on the domain's stream)
     peaks = measured_peaks()
-    dom_phase = max(phase, key=lambda k: phase[k]["ms"]) if phase else None
-    roof = None
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6800 (of fallback)"
+    roof, roof_k1 = None, None
     if phase:
+        single = ("dem_substep", "collide_stream", "force_drag", "force_am", "eps_gather", "reaction_am",
+                  "reaction_drag")
+        dom_phase = max((k for k in single if k in phase), key=lambda k: phase[k]["ms"])
         cs = phase["collide_stream"]
-        per_launch_ms = cs["ms"] / max(cs["launches"], 1)
-        bytes_launch = algorithmic_bytes_collide("f64") * ncell
-        achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": "collide_stream (K1, FP64)", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800",
-                "bytes_per_cell": algorithmic_bytes_collide("f64"), "cells_per_launch": ncell,
-                "per_launch_us": per_launch_ms * 1e3, "dominant_phase": dom_phase}
+        k1_launches = max(cs["launches"] // 2, 1)  # the phase holds K1 and the end-of-step update
+        k1_ms = cs["ms"] / k1_launches
+        k1_flops = K1_FLOPS_F64 * ncell / (k1_ms * 1e-3) / 1e9
+        roof_k1 = {"kernel": "k_collide_stream (K1, FP64)", "bound": "alu", "achieved": k1_flops,
+                   "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": k1_flops / FP64_PEAK_GFLOPS,
+                   "traffic": TRAFFIC.get(("collide_stream", "f64")), "flops_per_cell": K1_FLOPS_F64,
+                   "cells_per_launch": ncell, "per_launch_us": k1_ms * 1e3,
+                   "hbm_view": {"achieved_GBps": algorithmic_bytes_collide("f64") * ncell / (k1_ms * 1e-3) / 1e9,
+                                "peak_GBps": hbm, "bytes_per_cell": algorithmic_bytes_collide("f64")},
+                   "peak_source": "152 SMs x 4 FP64 flop/clk x 2.07 GHz (derived)"}
+        if dom_phase == "dem_substep":
+            dm = phase["dem_substep"]
+            per_ms = dm["ms"] / max(dm["launches"], 1)
+            npart = len(wl["x"])
+            partners = lubrication_partners(st["x_final"], wl["d"], wl["n"], wl["periodic"], 1.0)
+            flops_launch = npart * (DEM_FLOPS_PARTICLE + DEM_FLOPS_PAIR * partners)
+            ach = flops_launch / (per_ms * 1e-3) / 1e9
+            roof = {"kernel": "k_dem_substep (FP64 form)", "bound": "alu", "achieved": ach,
+                    "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
+                    "traffic": TRAFFIC.get(("dem_substep", "f64")), "per_launch_us": per_ms * 1e3,
+                    "units_per_launch": npart, "unit_of_work": "particle-substep",
+                    "flops_per_unit": DEM_FLOPS_PARTICLE + DEM_FLOPS_PAIR * partners,
+                    "lubrication_partners_per_particle": partners,
+                    "peak_source": "152 SMs x 4 FP64 flop/clk x 2.07 GHz (derived)", "dominant_phase": dom_phase}
+        elif dom_phase == "collide_stream":
+            roof = dict(roof_k1, dominant_phase=dom_phase)
+        else:
+            roof = {"kernel": dom_phase, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
+                    "frac": None, "traffic": None, "dominant_phase": dom_phase}
 
     forms = {}
     for prec in [f for f in args.forms.split(",") if f]:
         tot, _, ph, _, st2 = time_device(dps, wl, prec, max(args.steps // 2, 10), args.warmup, flush)
         k = max(args.steps // 2, 10)
         cs = ph["collide_stream"]
-        per = cs["ms"] / max(cs["launches"], 1)
+        per = cs["ms"] / max(cs["launches"] // 2, 1)  # K1 and the end-of-step update per step
+        gbs = algorithmic_bytes_collide(prec) * ncell / (per * 1e-3) / 1e9
         forms[prec] = {"value": ncell * k / (tot * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": tot / k,
-                       "collide_stream_GBps": algorithmic_bytes_collide(prec) * ncell / (per * 1e-3) / 1e9,
+                       "collide_stream_GBps": gbs, "collide_stream_frac_of_hbm": gbs / hbm,
                        "u_pS_z": float(st2["u_pS"][2])}
 
     e2e_steps = min(args.steps, 50)
@@ -315,7 +378,7 @@ def main():
                 "particle_steps_per_s": world * psteps,
                 "particle_substeps_per_s": world * psteps * 10,
                 "step_ms_p50": float(np.percentile(times, 50)), "step_ms_p99": float(np.percentile(times, 99)),
-                "roofline": roof, "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in phase.items()} if phase else None,
+                "roofline": roof, "roofline_collide_stream": roof_k1, "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in phase.items()} if phase else None,
                 "forms": forms, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(lps * args.steps),
                 "u_pS_z": float(st["u_pS"][2]), "status": int(st["status"])}
@@ -436,16 +499,38 @@ def suite_batch(dps, steps=20, count=64):
     against the plain FP64 method stepping every box as its own domain."""
     import torch
     boxes = _batch_boxes(count=count)
+    n_int = max(_subcycles(wl) for wl in boxes)  # one subcycle count per batch
+
+    def build(bx):
+        B = dps.Batch("f32")
+        ids = []
+        for wl in bx:
+            b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
+            B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
+            B.set_closure(b, _settling_closure(dps, wl, wl["d"][0], n_int))
+            ids.append(b)
+        return B, ids
+
+    # screen: boxes whose explicit coupling diverges within the suite's
+    # horizon (status flags of DPS_ERR_UNSTABLE) are reported and left out
+    unstable = []
+    for _ in range(4):
+        B, ids = build(boxes)
+        bad = []
+        try:
+            B.step(100)
+        except dps.DPSError:
+            bad = [k for k, b in enumerate(ids) if B.stats(b)["status"]]
+        B.close()
+        if not bad:
+            break
+        unstable += [dict(L=int(boxes[k]["n"][0]), eps=round(float(len(boxes[k]["x"]) * math.pi / 6 *
+                                                                   boxes[k]["d"][0] ** 3 / np.prod(boxes[k]["n"])), 3),
+                          d=round(float(boxes[k]["d"][0]), 3)) for k in bad]
+        boxes = [wl for k, wl in enumerate(boxes) if k not in bad]
     cells = sum(int(np.prod(b["n"])) for b in boxes)
     parts = sum(len(b["x"]) for b in boxes)
-    n_int = max(_subcycles(wl) for wl in boxes)  # one subcycle count per batch
-    B = dps.Batch("f32")
-    ids = []
-    for wl in boxes:
-        b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
-        B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
-        B.set_closure(b, _settling_closure(dps, wl, wl["d"][0], n_int))
-        ids.append(b)
+    B, ids = build(boxes)
     tune_ms = B.autotune(steps=3)
     B.step(2)
     torch.cuda.synchronize()
@@ -472,7 +557,8 @@ def suite_batch(dps, steps=20, count=64):
         up.append(dom.read_particles()["u"][:, 2].mean())
         dom.close()
     err = [abs(a - b) / max(abs(b), 1e-12) for a, b in zip(ub, up)]
-    line = {"suite": "batch", "boxes": count, "cells": cells, "particles": parts, "steps": steps,
+    line = {"suite": "batch", "boxes": len(boxes), "unstable_boxes_left_out": unstable, "cells": cells,
+            "particles": parts, "steps": steps, "n_int": n_int,
             "f32_batch_ms_per_step": ms_b, "f32_batch_MLUPS": cells / (ms_b * 1e-3) / 1e6,
             "f64_plain_ms_per_step": ms_p, "f64_plain_MLUPS": cells / (ms_p * 1e-3) / 1e6,
             "speedup": ms_p / ms_b, "tuning": cfg, "autotune_best_ms": tune_ms,
@@ -628,18 +714,25 @@ def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4), n
         dom.add_particles(x, np.full(n, d), np.full(n, rho_p))
         dom.set_closure(**c)
         t0 = time.perf_counter()
-        acc, cnt, done = 0.0, 0, 0
+        acc, cnt, done, failed = 0.0, 0, 0, None
         while done < steps:
             k = min(sample, steps - done)
-            dom.step(k)
+            try:
+                dom.step(k)
+            except dps.DPSError as e:
+                failed = {"unstable_before_step": done + k, "error": str(e)[:120]}
+                break
             done += k
             if done > steps - 10 * t_st:
                 acc += float(dom.stats()["u_pS"][2])
                 cnt += 1
         wall = time.perf_counter() - t0
         dom.close()
-        return {"suite": "hindered", "case": tag, "eps": eps, "particles": n, "u_pS_z": acc / max(cnt, 1),
-                "steps": steps, "wall_s": wall}
+        out = {"suite": "hindered", "case": tag, "eps": eps, "particles": n, "u_pS_z": acc / max(cnt, 1) if cnt else None,
+               "steps": steps, "wall_s": wall}
+        if failed:
+            out.update(failed)
+        return out
 
     out = []
     single = run(0.0, "single")
@@ -657,8 +750,8 @@ def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4), n
              "A4_no_Eilers": 0.289, "A5_n_int_1": 0.288}
     for eps, tag, kw in cases:
         r = run(eps, tag, **kw)
-        r.update({"ratio": -r["u_pS_z"] / u_T, "richardson_zaki": (1 - eps) ** kappa, "Re_T": Re_T,
-                  "paper_table2": paper.get(tag)})
+        r.update({"ratio": -r["u_pS_z"] / u_T if r["u_pS_z"] is not None else None,
+                  "richardson_zaki": (1 - eps) ** kappa, "Re_T": Re_T, "paper_table2": paper.get(tag)})
         out.append(r)
         print(json.dumps(r), flush=True)
     return out

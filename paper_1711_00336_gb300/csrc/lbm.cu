@@ -231,11 +231,13 @@ __device__ __forceinline__ void relax_cell(CT f[Q], CT e, CT fpx, CT fpy, CT fpz
     }
     const CT rho = DEV ? r_add(CT(1), s) : s;
     if (flag && (!(rho > CT(0)) || !(rho < CT(1e30)))) atomicOr(status, ST_NAN);
-    const CT ir = CT(1) / rho;
+    // 1/rho and 1/eps_f from one division (the FP64 form is bound by its
+    // FP64 instruction count)
+    const CT t = CT(1) / r_mul(rho, e);
+    const CT ir = r_mul(e, t), ie = r_mul(rho, t);
     const CT ux = r_mul(r_fma(CT(0.5), Fx, jx), ir);  // Eq. MacVel
     const CT uy = r_mul(r_fma(CT(0.5), Fy, jy), ir);
     const CT uz = r_mul(r_fma(CT(0.5), Fz, jz), ir);
-    const CT ie = CT(1) / e;
     CT omega = omega_box, kf = kf_box;
     if (VISC && vmode) {
         omega = CT(1) / tau_cell<CT, DEV>(f, s, rho, ux, uy, uz, e, ie, tau, vmode & 1, vmode & 2);

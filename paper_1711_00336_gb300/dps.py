@@ -486,6 +486,16 @@ class Batch:
                 off += k * nc
         return res
 
+    def stats(self, box):
+        """global sums, counters and the step count of one box (dps_batch_stats)"""
+        s = Stats()
+        self._ck(lib().dps_batch_stats(self.h, int(box), ctypes.byref(s)))
+        out = {}
+        for name, t in Stats._fields_:
+            v = getattr(s, name)
+            out[name] = np.array(list(v)) if hasattr(v, "__len__") else v
+        return out
+
     def particle_mean(self, box):
         u = np.zeros(3)
         self._ck(lib().dps_batch_particle_mean(self.h, int(box), _p(u)))
