@@ -533,6 +533,7 @@ def suite_batch(dps, steps=20, count=64):
     B, ids = build(boxes)
     tune_ms = B.autotune(steps=3)
     B.step(2)
+    history = int(B.stats(ids[0])["step"])  # steps every box has taken (tuning candidates + 2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     B.step(steps)
@@ -548,7 +549,7 @@ def suite_batch(dps, steps=20, count=64):
         dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
         dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
         dom.set_closure(_settling_closure(dps, wl, wl["d"][0], n_int))
-        dom.step(4 * 16 + 2)  # same history as the batch: 16 tuning candidates x (1 + 3) steps, then 2
+        dom.step(history)  # the same history as the batch
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         dom.step(steps)
