@@ -51,10 +51,10 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 K1_FLOPS_F64 = 249        # per cell: moments 42, velocity and invariants 36, 9 pairs x 16 + 13 more
 DEM_FLOPS_PARTICLE = 38   # per particle and substep: mass, semi-implicit Euler of u, w, x, skin check
 DEM_FLOPS_PAIR = 75       # per interacting partner: separation 9, masses / normal 17, Ball-Melrose force 49
-# DRAM bytes per launch from one ncu capture of the same kernel and workload
-# (profiles/dem_substep_fp64_wall_suspension.md); None where no capture of the
-# current kernel exists
-TRAFFIC = {("dem_substep", "f64"): 1.424896e6}
+# DRAM bytes (read + write) per launch from one ncu capture of the same kernel
+# and workload (profiles/step_kernels_wall_suspension.md); None where no
+# capture of the current kernel exists
+TRAFFIC = {("dem_substep", "f64"): 1.43e6, ("collide_stream", "f64"): 48.39e6}
 
 
 def lubrication_partners(x, d, n, periodic, h_c):
@@ -681,8 +681,11 @@ def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4), n
     """Sec. 4: hindered settling in a triply periodic 32^3 d_p box at the
     paper's regime (water and glass of Baldock et al. scaled to lattice units
     with d_p/dx = 1/2: rho_p/rho_f = 2.5, Re_T ~ 17), e_n = 0.88, mu_c = 0.25,
-    T_c = dt/2, h_c = d_p, n_int = 10, n_DEM = 50, all force models on and the
-    Sec. 4.1 body force on the fluid (fb_mode 2).  Each run lasts 30 t_St
+    T_c = dt/2, h_c = d_p, n_int = 10, n_DEM = 50, all force models on, and a
+    body force on the fluid that balances the buoyant weight exactly
+    (fb_mode 1: the literal Sec. 4.1 form leaves a net force of order
+    <eps_p>^2 that accelerates the whole mixture until the lattice Mach number
+    breaks the run, after ~500 steps at eps 0.3).  Each run lasts 30 t_St
     (t_St = rho_p d^2/(18 mu)); <u_pS> = <u_p> - <u_f> is averaged over its
     last 10 t_St and divided by the single sphere's u_pT from the eps = 0 run;
     the Richardson-Zaki value (1 - eps)^kappa(Re_T) is printed beside it.
@@ -707,7 +710,7 @@ def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4), n
             wl = workloads.settling_box(L=L, eps=eps, d=d, seed=int(eps * 1000) + 5)
             x = wl["x"]
         n = len(x)
-        c = dict(g=(0.0, 0.0, -g), fb_mode=2, e_n=0.88, mu_c=0.25, T_c=0.5, h_c=d, h_min=1e-5, C_am=0.5,
+        c = dict(g=(0.0, 0.0, -g), fb_mode=1, e_n=0.88, mu_c=0.25, T_c=0.5, h_c=d, h_min=1e-5, C_am=0.5,
                  n_int=10, n_dem=50, lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5, lift=1, eilers=1,
                  smagorinsky=1)
         c.update(kw)
