@@ -129,14 +129,12 @@ __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const 
     if (PAR) {
         int ix, iy, iz;
         cell_coords(g, c, ix, iy, iz);
-        in = interior_cell(g, ix, iy, iz);
-        if (in) {
-            load_pdfs_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c, (unsigned)g.n[0],
-                                       (unsigned)g.n[0] * (unsigned)g.n[1], f);
-        } else {
-            D = neighbour_deltas(g, ix, iy, iz);
+        D = neighbour_deltas(g, ix, iy, iz);
+        in = no_wall_neighbour(D);
+        if (in)
+            load_pdfs_wall_free<ST, CT>(pdf, (unsigned)N, (unsigned)c, D, f);
+        else
             load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
-        }
     } else {
         load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
     }
@@ -153,29 +151,26 @@ __device__ __forceinline__ void collide_stream_cell2(ST *__restrict__ pdf, const
                                                      long long c2, bool two, CT fbx, CT fby, CT fbz, CT omega_box,
                                                      CT kf_box, CT tau, int vmode, int *status) {
     const long long N = g.ncell;
-    const unsigned nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
     NbDelta D, D2;
     bool in = false, in2 = false;
     CT f[Q], f2[Q];
     if (PAR) {
         int ix, iy, iz;
         cell_coords(g, c, ix, iy, iz);
-        in = interior_cell(g, ix, iy, iz);
-        if (in) {
-            load_pdfs_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c, nx, nxy, f);
-        } else {
-            D = neighbour_deltas(g, ix, iy, iz);
+        D = neighbour_deltas(g, ix, iy, iz);
+        in = no_wall_neighbour(D);
+        if (in)
+            load_pdfs_wall_free<ST, CT>(pdf, (unsigned)N, (unsigned)c, D, f);
+        else
             load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
-        }
         if (two) {
             cell_coords(g, c2, ix, iy, iz);
-            in2 = interior_cell(g, ix, iy, iz);
-            if (in2) {
-                load_pdfs_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c2, nx, nxy, f2);
-            } else {
-                D2 = neighbour_deltas(g, ix, iy, iz);
+            D2 = neighbour_deltas(g, ix, iy, iz);
+            in2 = no_wall_neighbour(D2);
+            if (in2)
+                load_pdfs_wall_free<ST, CT>(pdf, (unsigned)N, (unsigned)c2, D2, f2);
+            else
                 load_pdfs<ST, CT, PAR>(pdf, N, c2, D2, f2);
-            }
         }
     } else {
         load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
@@ -279,8 +274,7 @@ __device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], 
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
         if (PAR && in)
-            store_pair_interior<ST, CT>(pdf, (unsigned)N, (unsigned)c, (unsigned)g.n[0],
-                                        (unsigned)g.n[0] * (unsigned)g.n[1], k, f[k], f[k + 9]);
+            store_pair_wall_free<ST, CT>(pdf, (unsigned)N, (unsigned)c, D, k, f[k], f[k + 9]);
         else
             store_pair<ST, CT, PAR>(pdf, N, c, D, k, f[k], f[k + 9]);
     }

@@ -103,34 +103,35 @@ __device__ __forceinline__ void store_pair(ST *__restrict__ pdf, long long N, lo
     }
 }
 
-// interior cells (no neighbour across a face of the box, periodic or wall):
-// the odd-parity neighbours are at the fixed offsets c -+ (c_x + c_y nx +
-// c_z nx ny), with no wrap or bounce-back to resolve
-__device__ __forceinline__ bool interior_cell(const Geom &g, int ix, int iy, int iz) {
-    return ix > 0 && ix < g.n[0] - 1 && iy > 0 && iy < g.n[1] - 1 && iz > 0 && iz < g.n[2] - 1;
+// cells with no wall neighbour (interior, or next to periodic faces only):
+// the odd-parity neighbours are at the deltas of D with no bounce-back to
+// resolve, so the loads and stores take no per-direction wall test
+__device__ __forceinline__ bool no_wall_neighbour(const NbDelta &D) {
+    return D.d[0][0] != INV && D.d[0][2] != INV && D.d[1][0] != INV && D.d[1][2] != INV && D.d[2][0] != INV &&
+           D.d[2][2] != INV;
 }
 
-__device__ __forceinline__ unsigned lattice_offset(int q, unsigned nx, unsigned nxy) {
-    return (unsigned)CX(q) + (unsigned)CY(q) * nx + (unsigned)CZ(q) * nxy;  // modulo 2^32
+__device__ __forceinline__ unsigned wall_free_delta(const NbDelta &D, int cx, int cy, int cz) {
+    return (unsigned)(D.d[0][cx + 1] + D.d[1][cy + 1] + D.d[2][cz + 1]);
 }
 
-// odd parity, interior cell: f_q(x) sits in plane opp(q) of x - c_q
+// odd parity, no wall neighbour: f_q(x) sits in plane opp(q) of x - c_q
 template <typename ST, typename CT>
-__device__ __forceinline__ void load_pdfs_interior(const ST *__restrict__ pdf, unsigned N, unsigned c, unsigned nx,
-                                                   unsigned nxy, CT f[Q]) {
+__device__ __forceinline__ void load_pdfs_wall_free(const ST *__restrict__ pdf, unsigned N, unsigned c,
+                                                    const NbDelta &D, CT f[Q]) {
     f[0] = Store<ST>::load(pdf + c);
 #pragma unroll
-    for (int q = 1; q < Q; ++q) f[q] = Store<ST>::load(pdf + ((unsigned)OPP(q) * N + c - lattice_offset(q, nx, nxy)));
+    for (int q = 1; q < Q; ++q)
+        f[q] = Store<ST>::load(pdf + ((unsigned)OPP(q) * N + c + wall_free_delta(D, -CX(q), -CY(q), -CZ(q))));
 }
 
-// odd parity, interior cell: the post-collision pair (k, k+9) goes to the
+// odd parity, no wall neighbour: the post-collision pair (k, k+9) goes to the
 // downstream cells x + c_k (plane k) and x - c_k (plane k+9)
 template <typename ST, typename CT>
-__device__ __forceinline__ void store_pair_interior(ST *__restrict__ pdf, unsigned N, unsigned c, unsigned nx,
-                                                    unsigned nxy, int k, CT vk, CT vo) {
-    const unsigned d = lattice_offset(k, nx, nxy);
-    Store<ST>::store(pdf + ((unsigned)k * N + c + d), vk);
-    Store<ST>::store(pdf + ((unsigned)(k + 9) * N + c - d), vo);
+__device__ __forceinline__ void store_pair_wall_free(ST *__restrict__ pdf, unsigned N, unsigned c, const NbDelta &D,
+                                                     int k, CT vk, CT vo) {
+    Store<ST>::store(pdf + ((unsigned)k * N + c + wall_free_delta(D, CX(k), CY(k), CZ(k))), vk);
+    Store<ST>::store(pdf + ((unsigned)(k + 9) * N + c + wall_free_delta(D, -CX(k), -CY(k), -CZ(k))), vo);
 }
 
 template <typename CT>
