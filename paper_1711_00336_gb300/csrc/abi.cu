@@ -341,7 +341,12 @@ static int dem_lanes_class(const BoxHost *h) {
     const dps_closure &c = h->cl;
     const double rl = h->dmax + (c.lubrication ? std::fmax(c.h_c, 0.0) : 0.0) + c.skin;
     const double est = (double)h->d.np / (double)h->d.g.ncell * 4.18879 * rl * rl * rl;
-    return est >= 24.0 ? 3 : est >= 8.0 ? 2 : est >= 3.0 ? 1 : 0;
+    int cls = est >= 24.0 ? 3 : est >= 8.0 ? 2 : est >= 3.0 ? 1 : 0;
+    // few particles: a warp costs the longest list among its particles and
+    // there are few warps per SM, so spread every particle over more lanes
+    // (about two warps per SM scheduler at np x lanes / 32)
+    for (long long lanes = 1LL << cls; cls < 3 && h->d.np * lanes < 38912; lanes <<= 1) ++cls;
+    return cls;
 }
 
 // rebuild the device table and the tile lists from the host boxes (the
@@ -539,8 +544,10 @@ static void enqueue_step(Batch *B) {
                 for (int c = 0; c < 4; ++c) {
                     const int nt = B->part_off[c + 1] - B->part_off[c];
                     if (nt <= 0) continue;
+                    // a block holds all lane groups of a particle tile (at most 256 threads)
+                    const int blk = std::min(256, std::max(u.part_block, u.part_tile << c));
                     launch_dem_substep(T, B->d_part + B->part_off[c], nt, sd & 1, B->prec != DPS_F64, 1 << c,
-                                       grid_of(nt), u.part_block, s);
+                                       grid_of(nt), blk, s);
                     ++ndl;
                 }
         tend(B, PH_DEM, ndl);
@@ -673,9 +680,9 @@ static int run_steps(Batch *B, long long n) {
 // ---- boxes ------------------------------------------------------------------------------
 static int batch_init(Batch *B, int precision, void *stream, dps_alloc_fn a, dps_free_fn f, void *ctx) {
     B->prec = precision;
-    // collide-stream default: two cells per thread for FP32, one for FP16
-    // (measured at 256^3: 4.6 and 2.6 TB/s)
-    B->tune.k1v = precision == DPS_F16S ? 1 : 3;
+    // collide-stream default: two cells per thread, 3 or 4 blocks per SM
+    // (measured at 256^3: 5.4 TB/s for FP32, 3.0 TB/s for FP16)
+    B->tune.k1v = precision == DPS_F16S ? 4 : 3;
     B->pdf_elem = precision == DPS_F64 ? 8 : (precision == DPS_F32 ? 4 : 2);
     B->fel = precision == DPS_F64 ? 8 : 4;
     B->alloc = a;
