@@ -344,8 +344,8 @@ static int dem_lanes_class(const BoxHost *h) {
     int cls = est >= 24.0 ? 3 : est >= 8.0 ? 2 : est >= 3.0 ? 1 : 0;
     // few particles: a warp costs the longest list among its particles and
     // there are few warps per SM, so spread every particle over more lanes
-    // (about two warps per SM scheduler at np x lanes / 32)
-    for (long long lanes = 1LL << cls; cls < 3 && h->d.np * lanes < 38912; lanes <<= 1) ++cls;
+    // (about one warp per SM scheduler at np x lanes / 32)
+    for (long long lanes = 1LL << cls; cls < 3 && h->d.np * lanes < 19456; lanes <<= 1) ++cls;
     return cls;
 }
 
