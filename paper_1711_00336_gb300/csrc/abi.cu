@@ -54,7 +54,7 @@ void launch_reaction_am(const BoxDev *, const Tile *, int, int, int, cudaStream_
 template <typename FT>
 void launch_reaction_drag(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
 void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, int, int, cudaStream_t);
-void launch_build_nlist(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+void launch_build_nlist(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 long long scan_scratch_words(long long);
 void exclusive_scan(const int *, long long, int *, int *, cudaStream_t);
 template <typename ST>
@@ -479,8 +479,16 @@ static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub) {
         launch_bsort_gather(T, B->d_part, B->n_part, xsel, grid_of(B->n_part), u.part_block, B->stream);
     }
     launch_bsort_flip(B->d_table, nb, mark_usub, B->stream);
-    if (pl) launch_build_nlist(T, B->d_part, B->n_part, grid_of(B->n_part), u.part_block, B->stream);
-    tend(B, PH_SORT, 3 + 5 * pl + 1);
+    int nlists = 0;
+    if (pl)
+        for (int c = 0; c < 4; ++c) {  // lanes per particle as in the DEM substep
+            const int nt = B->part_off[c + 1] - B->part_off[c];
+            if (nt <= 0) continue;
+            const int blk = std::min(256, std::max(u.part_block, u.part_tile << c));
+            launch_build_nlist(T, B->d_part + B->part_off[c], nt, 1 << c, grid_of(nt), blk, B->stream);
+            ++nlists;
+        }
+    tend(B, PH_SORT, 3 + 4 * pl + 1 + nlists);
     tbegin(B);
     if (B->fel == 8)
         launch_eps<double>(T, B->d_brick, B->n_brick, grid_of(B->n_brick), 256, B->stream);

@@ -140,9 +140,15 @@ __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T di
 
 // ---- neighbour list ----------------------------------------------------------------
 // list of particle i: partners j != i with |x_j - x_i| < (d_i+d_j)/2 + extra + skin
-// (screened in FP32 with a margin), stored row by row: nlist[i*maxn + k]
+// (screened in FP32 with a margin), stored row by row: nlist[i*maxn + k].
+// LANES lanes share a particle: lane l scans the cell rows l, l + LANES, ...
+// of the (2R+1)^2 rows around it, counts its partners, takes its offset from
+// an exclusive sum over the lanes, then scans again and writes them, so the
+// list is in lane-major row order whatever the launch shape.
+template <int LANES>
 __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
                                                      int ntiles) {
+    const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &Bx = boxes[tl.box];
@@ -152,64 +158,83 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
         const float extra = (float)((ph.lubrication ? fmax(ph.h_c, 0.0) : 0.0) + ph.skin) + SCREEN_MARGIN;
         const float Lf[3] = {(float)g.n[0], (float)g.n[1], (float)g.n[2]};
         const int R = Bx.R, maxn = Bx.maxn;
-        for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
-            const float4 pi = xf[i];
-            int *lst = Bx.nlist + i * (long long)maxn;
-            int b[3] = {containing_cell((double)pi.x, g.n[0]), containing_cell((double)pi.y, g.n[1]),
-                        containing_cell((double)pi.z, g.n[2])};
-            int lo[3], hi[3];
+        // the trip count is uniform over the block: every lane reaches the shuffles
+        for (long long base = tl.begin; base < tl.end; base += ngrp) {
+            const long long i = base + grp;
+            const bool act = i < tl.end;
+            float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+            int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+            if (act) {
+                pi = xf[i];
+                const int b[3] = {containing_cell((double)pi.x, g.n[0]), containing_cell((double)pi.y, g.n[1]),
+                                  containing_cell((double)pi.z, g.n[2])};
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (g.per[a] && 2 * R + 1 >= g.n[a]) {
-                    lo[a] = 0;
-                    hi[a] = g.n[a] - 1;
-                } else if (g.per[a]) {
-                    lo[a] = b[a] - R;
-                    hi[a] = b[a] + R;
-                } else {
-                    lo[a] = max(b[a] - R, 0);
-                    hi[a] = min(b[a] + R, g.n[a] - 1);
-                }
-            }
-            int cnt = 0;
-            bool over = false;
-            for (int zz = lo[2]; zz <= hi[2]; ++zz) {
-                const int z = zz < 0 ? zz + g.n[2] : (zz >= g.n[2] ? zz - g.n[2] : zz);
-                for (int yy = lo[1]; yy <= hi[1]; ++yy) {
-                    const int y = yy < 0 ? yy + g.n[1] : (yy >= g.n[1] ? yy - g.n[1] : yy);
-                    const long long row = cell_index(g, 0, y, z);
-                    int xs0[2], xs1[2], nseg;
-                    if (lo[0] >= 0 && hi[0] <= g.n[0] - 1) {
-                        xs0[0] = lo[0]; xs1[0] = hi[0]; nseg = 1;
-                    } else if (lo[0] < 0) {
-                        xs0[0] = 0; xs1[0] = hi[0];
-                        xs0[1] = lo[0] + g.n[0]; xs1[1] = g.n[0] - 1; nseg = 2;
+                for (int a = 0; a < 3; ++a) {
+                    if (g.per[a] && 2 * R + 1 >= g.n[a]) {
+                        lo[a] = 0;
+                        hi[a] = g.n[a] - 1;
+                    } else if (g.per[a]) {
+                        lo[a] = b[a] - R;
+                        hi[a] = b[a] + R;
                     } else {
-                        xs0[0] = lo[0]; xs1[0] = g.n[0] - 1;
-                        xs0[1] = 0; xs1[1] = hi[0] - g.n[0]; nseg = 2;
-                    }
-                    for (int sgi = 0; sgi < nseg; ++sgi) {
-                        const int s = Bx.cell_start[row + xs0[sgi]], e = Bx.cell_start[row + xs1[sgi] + 1];
-                        for (int j = s; j < e; ++j) {
-                            if (j == i) continue;
-                            const float4 pj = xf[j];
-                            const float dx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
-                            const float dy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
-                            const float dz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
-                            const float r = 0.5f * (pi.w + pj.w) + extra;
-                            if (dx * dx + dy * dy + dz * dz < r * r) {
-                                if (cnt < maxn)
-                                    lst[cnt] = j;
-                                else
-                                    over = true;
-                                ++cnt;
-                            }
-                        }
+                        lo[a] = max(b[a] - R, 0);
+                        hi[a] = min(b[a] + R, g.n[a] - 1);
                     }
                 }
             }
-            Bx.nlist_n[i] = min(cnt, maxn);
-            if (over) atomicOr(Bx.status, ST_NLIST);
+            const int ny = hi[1] - lo[1] + 1, nrows = act ? ny * (hi[2] - lo[2] + 1) : 0;
+            // partners of particle i in cell row r, in the order of the sorted particles
+            auto scan_row = [&](int r, auto &&fn) {
+                const int yy = lo[1] + r % ny, zz = lo[2] + r / ny;
+                const int z = zz < 0 ? zz + g.n[2] : (zz >= g.n[2] ? zz - g.n[2] : zz);
+                const int y = yy < 0 ? yy + g.n[1] : (yy >= g.n[1] ? yy - g.n[1] : yy);
+                const long long row = cell_index(g, 0, y, z);
+                int xs0[2], xs1[2], nseg;
+                if (lo[0] >= 0 && hi[0] <= g.n[0] - 1) {
+                    xs0[0] = lo[0]; xs1[0] = hi[0]; nseg = 1;
+                } else if (lo[0] < 0) {
+                    xs0[0] = 0; xs1[0] = hi[0];
+                    xs0[1] = lo[0] + g.n[0]; xs1[1] = g.n[0] - 1; nseg = 2;
+                } else {
+                    xs0[0] = lo[0]; xs1[0] = g.n[0] - 1;
+                    xs0[1] = 0; xs1[1] = hi[0] - g.n[0]; nseg = 2;
+                }
+                for (int sgi = 0; sgi < nseg; ++sgi) {
+                    const int s0 = Bx.cell_start[row + xs0[sgi]], e0 = Bx.cell_start[row + xs1[sgi] + 1];
+                    for (int j = s0; j < e0; ++j) {
+                        if (j == i) continue;
+                        const float4 pj = xf[j];
+                        const float dx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
+                        const float dy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
+                        const float dz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
+                        const float rr = 0.5f * (pi.w + pj.w) + extra;
+                        if (dx * dx + dy * dy + dz * dz < rr * rr) fn(j);
+                    }
+                }
+            };
+            int cnt = 0;
+            for (int r = lane; r < nrows; r += LANES) scan_row(r, [&](int) { ++cnt; });
+            // exclusive sum of the counts over the lanes of the group
+            int off = cnt;
+#pragma unroll
+            for (int o = 1; o < LANES; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, off, o);
+                if (lane >= o) off += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, off, (threadIdx.x & 31) - lane + LANES - 1);
+            off -= cnt;
+            if (!act) continue;
+            int *lst = Bx.nlist + i * (long long)maxn;
+            int w = off;
+            for (int r = lane; r < nrows; r += LANES)
+                scan_row(r, [&](int j) {
+                    if (w < maxn) lst[w] = j;
+                    ++w;
+                });
+            if (lane == 0) {
+                Bx.nlist_n[i] = min(total, maxn);
+                if (total > maxn) atomicOr(Bx.status, ST_NLIST);
+            }
         }
     }
 }
@@ -473,8 +498,12 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
     }
 }
 
-void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int grid, int block, cudaStream_t s) {
-    k_build_nlist<<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int lanes, int grid, int block,
+                        cudaStream_t s) {
+    if (lanes >= 8) k_build_nlist<8><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+    else if (lanes == 4) k_build_nlist<4><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+    else if (lanes == 2) k_build_nlist<2><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+    else k_build_nlist<1><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
 }
 
 // lanes: 1, 2, 4 or 8 lanes per particle (block a multiple of 32)
