@@ -112,6 +112,10 @@ struct Batch {
     size_t pdf_elem = 8, fel = 8;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // second stream of the step: the drag reaction runs beside the DEM
+    // substeps (fork and join by events, captured into the step graph)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     dps_alloc_fn alloc = nullptr;
     dps_free_fn free = nullptr;
     void *ctx = nullptr;
@@ -130,6 +134,7 @@ struct Batch {
     int n_int = 0, n_dem = 0;
     bool any_lift = false;        // some box applies the lift force (curl launch per subcycle)
     int part_off[5] = {0, 0, 0, 0, 0};  // particle tiles grouped by DEM lanes class (1, 2, 4, 8)
+    int cpl_lanes = 1;            // most lanes per particle of the force kernels over the batch
     int n_cell_plain = 0;         // cell tiles of boxes with a constant tau (listed first);
                                   // the rest relax with a per-cell tau_e (K1 variant)
     bool layout_dirty = true;     // table/tiles must be rebuilt and uploaded
@@ -199,7 +204,7 @@ static void invalidate_graph(Batch *B) {
 }
 
 // ---- phase timing -----------------------------------------------------------
-static void tbegin(Batch *B) {
+static void tbegin(Batch *B, cudaStream_t on = nullptr) {
     if (!B->timing) return;
     if (B->ev_used * 2 + 2 > B->ev.size()) {
         cudaEvent_t a, b;
@@ -211,12 +216,12 @@ static void tbegin(Batch *B) {
         B->ev_nl.push_back(0);
     }
     // external record nodes: the events stay readable after graph replays
-    cudaEventRecordWithFlags(B->ev[2 * B->ev_used], B->stream, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(B->ev[2 * B->ev_used], on ? on : B->stream, cudaEventRecordExternal);
 }
-static void tend(Batch *B, int phase, int nl) {
+static void tend(Batch *B, int phase, int nl, cudaStream_t on = nullptr) {
     B->launch_count += nl;
     if (!B->timing) return;
-    cudaEventRecordWithFlags(B->ev[2 * B->ev_used + 1], B->stream, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(B->ev[2 * B->ev_used + 1], on ? on : B->stream, cudaEventRecordExternal);
     B->ev_phase[B->ev_used] = phase;
     B->ev_nl[B->ev_used] = nl;
     B->ev_used++;
@@ -349,6 +354,15 @@ static int dem_lanes_class(const BoxHost *h) {
     return cls;
 }
 
+// lanes per particle of the force kernels (Tile::first of the particle
+// tiles): the few-particles rule of the DEM substep alone (the 27-cell
+// support gathers do not grow with the neighbour count)
+static int force_lanes(const BoxHost *h) {
+    int lanes = 1;
+    while (lanes < 8 && h->d.np * lanes < 19456) lanes <<= 1;
+    return lanes;
+}
+
 // rebuild the device table and the tile lists from the host boxes (the
 // device step state must have been pulled first)
 static int push_layout(Batch *B) {
@@ -382,6 +396,7 @@ static int push_layout(Batch *B) {
     }
     std::vector<Tile> partc[4];  // particle tiles by DEM lanes class
     B->any_lift = false;
+    B->cpl_lanes = 1;
     for (int k = 0; k < nb; ++k) {
         BoxHost *h = B->boxes[k];
         compute_phys(h);
@@ -391,9 +406,10 @@ static int push_layout(Batch *B) {
         const long long N = h->d.g.ncell, np = h->d.np;
         for (long long c = 0; c < N; c += B->tune.cell_tile)
             ct.push_back(Tile{k, 0, c, std::min(N, c + B->tune.cell_tile)});
-        const int lc = dem_lanes_class(h);
+        const int lc = dem_lanes_class(h), fl = force_lanes(h);
+        B->cpl_lanes = std::max(B->cpl_lanes, fl);
         for (long long p = 0; p < np; p += B->tune.part_tile)
-            partc[lc].push_back(Tile{k, 0, p, std::min(np, p + B->tune.part_tile)});
+            partc[lc].push_back(Tile{k, fl, p, std::min(np, p + B->tune.part_tile)});
         int idx = 0;
         for (long long c = 0; c < N; c += ST) scan.push_back(Tile{k, idx++, c, std::min(N, c + ST)});
         brick_tiles(k, h->d.g.n, brick);
@@ -431,6 +447,14 @@ static int push_layout(Batch *B) {
 }
 
 static int grid_of(int ntiles) { return std::max(1, std::min(ntiles, 152 * 8)); }
+
+// threads per block of a particle kernel with `lanes` lanes per particle: the
+// whole tile's lane groups when that fits in 256 threads, a multiple of 32
+// (the lane-group shuffles take all 32 lanes of a warp)
+static int part_threads(const Tuning &u, int lanes) {
+    const long long want = std::max<long long>(u.part_block, (long long)u.part_tile * lanes);
+    return (int)std::min<long long>(256, (want + 31) / 32 * 32);
+}
 
 // ---- the coupled step --------------------------------------------------------------
 #define PREC_CALL(B, F64CALL, F32CALL, F16CALL) \
@@ -484,7 +508,7 @@ static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub) {
         for (int c = 0; c < 4; ++c) {  // lanes per particle as in the DEM substep
             const int nt = B->part_off[c + 1] - B->part_off[c];
             if (nt <= 0) continue;
-            const int blk = std::min(256, std::max(u.part_block, u.part_tile << c));
+            const int blk = part_threads(u, 1 << c);
             launch_build_nlist(T, B->d_part + B->part_off[c], nt, 1 << c, grid_of(nt), blk, B->stream);
             ++nlists;
         }
@@ -525,8 +549,8 @@ static void enqueue_step(Batch *B) {
             else launch_curl<float, float>(T, B->d_cell, B->n_cell, gc, u.cell_block, s);
         }
         if (pl) {
-            if (f64) launch_force_am<double>(T, B->d_part, B->n_part, gp, u.part_block, s);
-            else launch_force_am<float>(T, B->d_part, B->n_part, gp, u.part_block, s);
+            if (f64) launch_force_am<double>(T, B->d_part, B->n_part, gp, part_threads(u, B->cpl_lanes), s);
+            else launch_force_am<float>(T, B->d_part, B->n_part, gp, part_threads(u, B->cpl_lanes), s);
         }
         tend(B, PH_FAM, pl + nl);
         tbegin(B);
@@ -535,16 +559,28 @@ static void enqueue_step(Batch *B) {
         tend(B, PH_RAM, 1);
         tbegin(B);
         if (pl) {
-            if (f64) launch_force_drag<double>(T, B->d_part, B->n_part, gp, u.part_block, s);
-            else launch_force_drag<float>(T, B->d_part, B->n_part, gp, u.part_block, s);
+            if (f64) launch_force_drag<double>(T, B->d_part, B->n_part, gp, part_threads(u, B->cpl_lanes), s);
+            else launch_force_drag<float>(T, B->d_part, B->n_part, gp, part_threads(u, B->cpl_lanes), s);
         }
         tend(B, PH_FDRAG, pl);
-        tbegin(B);
+        // the drag reaction (cell fields from the frozen particle forces and
+        // weights) and the DEM substeps (particle kinematics) touch disjoint
+        // data: the reaction runs on the side stream (its phase timed there)
+        // and joins before the sort, which reorders the particles it reads
+        const bool fork = B->side != nullptr;
+        cudaStream_t rs = s;
+        if (fork) {
+            cudaEventRecord(B->ev_fork, s);
+            cudaStreamWaitEvent(B->side, B->ev_fork, 0);
+            rs = B->side;
+        }
+        tbegin(B, rs);
         if (f64)
-            launch_reaction_drag<double>(T, B->d_brick, B->n_brick, k == 0, k == B->n_int - 1, gb, 256, s);
+            launch_reaction_drag<double>(T, B->d_brick, B->n_brick, k == 0, k == B->n_int - 1, gb, 256, rs);
         else
-            launch_reaction_drag<float>(T, B->d_brick, B->n_brick, k == 0, k == B->n_int - 1, gb, 256, s);
-        tend(B, PH_RDRAG, 1);
+            launch_reaction_drag<float>(T, B->d_brick, B->n_brick, k == 0, k == B->n_int - 1, gb, 256, rs);
+        tend(B, PH_RDRAG, 1, rs);
+        if (fork) cudaEventRecord(B->ev_join, B->side);
         tbegin(B);
         int ndl = 0;
         if (pl)
@@ -553,12 +589,13 @@ static void enqueue_step(Batch *B) {
                     const int nt = B->part_off[c + 1] - B->part_off[c];
                     if (nt <= 0) continue;
                     // a block holds all lane groups of a particle tile (at most 256 threads)
-                    const int blk = std::min(256, std::max(u.part_block, u.part_tile << c));
+                    const int blk = part_threads(u, 1 << c);
                     launch_dem_substep(T, B->d_part + B->part_off[c], nt, sd & 1, B->prec != DPS_F64, 1 << c,
                                        grid_of(nt), blk, s);
                     ++ndl;
                 }
         tend(B, PH_DEM, ndl);
+        if (fork) cudaStreamWaitEvent(s, B->ev_join, 0);
         enqueue_sort_eps(B, B->n_dem & 1, 1);
     }
     tbegin(B);
@@ -703,6 +740,14 @@ static int batch_init(Batch *B, int precision, void *stream, dps_alloc_fn a, dps
 }
 
 static int ensure_stream(Batch *B) {
+    if (!B->side) {
+        if (cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            FAILB(B, DPS_ERR_CUDA, "stream or event creation failed");
+        }
+    }
     if (B->stream) return DPS_OK;
     if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -724,6 +769,14 @@ static void batch_release(Batch *B) {
     B->allocs.clear();
     for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
     B->ev.clear();
+    if (B->side) {
+        cudaStreamSynchronize(B->side);
+        cudaStreamDestroy(B->side);
+        cudaEventDestroy(B->ev_fork);
+        cudaEventDestroy(B->ev_join);
+        B->side = nullptr;
+        B->ev_fork = B->ev_join = nullptr;
+    }
     if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
     B->stream = nullptr;
 }

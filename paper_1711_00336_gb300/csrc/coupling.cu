@@ -380,14 +380,152 @@ __device__ __forceinline__ void for_brick_cells(const Geom &g, int ox, int oy, i
     }
 }
 
+// Compacted particle list of a brick and its halo: entry m is particle P[m]
+// of halo cell with x coordinate hx[m]; the entries of halo cell h are
+// [off[h], off[h+1]) in ascending h, then sorted order.  A warp gathers over
+// the rows (hz, hy) of the bounding box of its cells' supports only, so with
+// sparse particles it visits the few particles near it once, instead of each
+// lane testing all 27 neighbour cells (a warp pays for the busiest lane of
+// every neighbour cell).  The per-cell visit order is the one of
+// gather27_staged: ascending h is ascending (o_z, o_y, o_x) for a fixed cell.
+constexpr int BRICK_THREADS = 256;  // block size of every brick kernel
+constexpr int BL_MAX = 3072;        // entries; above it the block takes gather27_staged
+constexpr int BL_PER_THREAD = (HALO3 + BRICK_THREADS - 1) / BRICK_THREADS;
+
+struct BrickList {
+    BrickRanges R;
+    int off[HALO3 + 1];
+    int P[BL_MAX];
+    unsigned char hx[BL_MAX];
+    int wsum[BRICK_THREADS / 32];
+    int n;  // entries, or -1 when over BL_MAX
+};
+
+// stage the ranges and the compacted list of brick (ox,oy,oz); ends with a barrier
+__device__ __forceinline__ void stage_list(const BoxDev &B, int ox, int oy, int oz, BrickList &L) {
+    const Geom &g = B.g;
+    int s0[BL_PER_THREAD], cnt[BL_PER_THREAD], tot = 0;
+#pragma unroll
+    for (int u = 0; u < BL_PER_THREAD; ++u) {
+        const int h = BL_PER_THREAD * threadIdx.x + u;
+        int a = 0, e = 0;
+        if (h < HALO3) {
+            const int hx = h % HALO, hy = (h / HALO) % HALO, hz = h / (HALO * HALO);
+            const int x = wrap_axis(ox + hx - 1, g.n[0], g.per[0]);
+            const int y = wrap_axis(oy + hy - 1, g.n[1], g.per[1]);
+            const int z = wrap_axis(oz + hz - 1, g.n[2], g.per[2]);
+            if (x >= 0 && y >= 0 && z >= 0) {
+                const long long n = cell_index(g, x, y, z);
+                a = B.cell_start[n];
+                e = B.cell_start[n + 1];
+            }
+            L.R.s[h] = a;
+            L.R.e[h] = e;
+        }
+        s0[u] = a;
+        cnt[u] = e - a;
+        tot += e - a;
+    }
+    // block-wide exclusive prefix of the per-thread totals
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) L.wsum[wid] = incl;
+    __syncthreads();
+    int base = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < BRICK_THREADS / 32; ++q) {
+        base += q < wid ? L.wsum[q] : 0;
+        total += L.wsum[q];
+    }
+    int run = base + incl - tot;
+    const bool fits = total <= BL_MAX;
+#pragma unroll
+    for (int u = 0; u < BL_PER_THREAD; ++u) {
+        const int h = BL_PER_THREAD * threadIdx.x + u;
+        if (h < HALO3) {
+            L.off[h] = run;
+            if (fits)
+                for (int m = 0; m < cnt[u]; ++m) {
+                    L.P[run + m] = s0[u] + m;
+                    L.hx[run + m] = (unsigned char)(h % HALO);
+                }
+        }
+        run += cnt[u];
+    }
+    if (threadIdx.x == 0) {
+        L.off[HALO3] = total;
+        L.n = fits ? total : -1;
+    }
+    __syncthreads();
+}
+
+// for every cell c of the brick: St st{}; acc(st, p, W_p(c)) over the
+// particles of its support in the order of gather27_staged; fin(st, c)
+template <typename St, typename WT, typename Acc, typename Fin>
+__device__ __forceinline__ void brick_gather(const Geom &g, const BrickList &L, int ox, int oy, int oz, int ex, int ey,
+                                             int ez, const WT *__restrict__ w, long long cap, Acc &&acc, Fin &&fin) {
+    if (L.n < 0) {
+        for_brick_cells(g, ox, oy, oz, ex, ey, ez, [&](long long c, int lx, int ly, int lz) {
+            St st{};
+            gather27_staged(L.R, lx, ly, lz, w, cap, [&](int p, WT W) { acc(st, p, W); });
+            fin(st, c);
+        });
+        return;
+    }
+    const int nb = ex * ey * ez;
+    for (int k0 = 0; k0 < nb; k0 += blockDim.x) {  // trip count uniform over the block
+        const int k = k0 + threadIdx.x;
+        const bool act = k < nb;
+        int lx = 0, ly = 0, lz = 0;
+        if (act) {
+            lx = k % ex;
+            ly = (k / ex) % ey;
+            lz = k / (ex * ey);
+        }
+        if (!__any_sync(0xffffffffu, act)) continue;
+        // halo bounding box of the warp's supports: [min l, max l + 2] per axis
+        const int BIG = 1 << 20;
+        const int bx0 = __reduce_min_sync(0xffffffffu, act ? lx : BIG);
+        const int by0 = __reduce_min_sync(0xffffffffu, act ? ly : BIG);
+        const int bz0 = __reduce_min_sync(0xffffffffu, act ? lz : BIG);
+        const int bx1 = __reduce_max_sync(0xffffffffu, act ? lx : -BIG) + 2;
+        const int by1 = __reduce_max_sync(0xffffffffu, act ? ly : -BIG) + 2;
+        const int bz1 = __reduce_max_sync(0xffffffffu, act ? lz : -BIG) + 2;
+        St st{};
+        for (int hz = bz0; hz <= bz1; ++hz) {
+            const int dz = hz - (lz + 1);
+            for (int hy = by0; hy <= by1; ++hy) {
+                const int dy = hy - (ly + 1);
+                const int hrow = (hz * HALO + hy) * HALO;
+                const int m0 = L.off[hrow + bx0], m1 = L.off[hrow + bx1 + 1];
+                if (!act || dz < -1 || dz > 1 || dy < -1 || dy > 1) continue;
+                const WT *wz = w + (6 + 1 - dz) * cap, *wy = w + (3 + 1 - dy) * cap;
+                for (int m = m0; m < m1; ++m) {
+                    const int dx = (int)L.hx[m] - (lx + 1);
+                    if (dx < -1 || dx > 1) continue;
+                    const int p = L.P[m];
+                    const WT *wx = w + (1 - dx) * cap;
+                    acc(st, p, wx[p] * wy[p] * wz[p]);
+                }
+            }
+        }
+        if (act) fin(st, cell_index(g, ox + lx, oy + ly, oz + lz));
+    }
+}
+
 // ---- S2: eps_f ------------------------------------------------------------------
 // FT is the compute type of the form: FP64 for the plain method, FP32 (with
 // FP32 kernel weights) for the low-precision forms.  Also clears the sort
 // counts for the next sort (every cell is visited once).
 template <typename FT>
-__global__ void __launch_bounds__(256) k_eps_gather(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
-                                                    int ntiles) {
-    __shared__ BrickRanges R;
+__global__ void __launch_bounds__(BRICK_THREADS) k_eps_gather(const BoxDev *__restrict__ boxes,
+                                                              const Tile *__restrict__ tiles, int ntiles) {
+    __shared__ BrickList L;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &B = boxes[tl.box];
@@ -395,9 +533,8 @@ __global__ void __launch_bounds__(256) k_eps_gather(const BoxDev *__restrict__ b
         int ox, oy, oz, ex, ey, ez;
         brick_unpack(tl.begin, ox, oy, oz);
         brick_unpack(tl.end, ex, ey, ez);
-        __syncthreads();  // the previous brick is done with R
-        stage_ranges(B, ox, oy, oz, R);
-        __syncthreads();
+        __syncthreads();  // the previous brick is done with L
+        stage_list(B, ox, oy, oz, L);
         const double *pf = B.pf[B.cur];
         const long long cap = B.cap;
         const FT *w = weights_of<FT>(B, pf);
@@ -405,21 +542,25 @@ __global__ void __launch_bounds__(256) k_eps_gather(const BoxDev *__restrict__ b
         FT *eps = (FT *)B.eps;
         const FT eps_min = (FT)B.ph.eps_min;
         unsigned nclamp = 0;
-        for_brick_cells(g, ox, oy, oz, ex, ey, ez, [&](long long c, int lx, int ly, int lz) {
-            FT ep = 0;
-            gather27_staged(R, lx, ly, lz, w, cap, [&](int p, FT W) {
+        struct St {
+            FT ep;
+        };
+        brick_gather<St>(
+            g, L, ox, oy, oz, ex, ey, ez, w, cap,
+            [&](St &st, int p, FT W) {
                 const FT d = sizeof(FT) == 8 ? (FT)pf[PD * cap + p] : (FT)xf[p].w;
-                ep += W * (FT(PI_D / 6.0) * d * d * d);
+                st.ep += W * (FT(PI_D / 6.0) * d * d * d);
+            },
+            [&](St &st, long long c) {
+                FT e = FT(1) - st.ep;
+                if (e < eps_min) {
+                    if (e < FT(0)) atomicOr(B.status, ST_EPS_NEG);
+                    ++nclamp;
+                    e = eps_min;
+                }
+                eps[c] = e;
+                B.count[c] = 0;
             });
-            FT e = FT(1) - ep;
-            if (e < eps_min) {
-                if (e < FT(0)) atomicOr(B.status, ST_EPS_NEG);
-                ++nclamp;
-                e = eps_min;
-            }
-            eps[c] = e;
-            B.count[c] = 0;
-        });
         if (nclamp) atomicAdd(&B.counters[CNT_EPS_CLAMP], (unsigned long long)nclamp);
     }
 }
@@ -467,6 +608,46 @@ __device__ __forceinline__ void for_support(const Geom &g, const Support<FT> &S,
     }
 }
 
+// the cells s = lane, lane + lanes, ... (s < 27, s = 9 o_z + 3 o_y + o_x) of
+// the support; with one lane the order of for_support
+template <typename FT, typename Fn>
+__device__ __forceinline__ void for_support_lanes(const Geom &g, const Support<FT> &S, int lane, int lanes, Fn &&fn) {
+#pragma unroll 1
+    for (int s = lane; s < 27; s += lanes) {
+        const int oz = s / 9, oy = (s / 3) % 3, ox = s % 3;
+        const int z = wrap_axis(S.b[2] + oz - 1, g.n[2], g.per[2]);
+        const int y = wrap_axis(S.b[1] + oy - 1, g.n[1], g.per[1]);
+        const int x = wrap_axis(S.b[0] + ox - 1, g.n[0], g.per[0]);
+        if (x < 0 || y < 0 || z < 0) continue;
+        // selects keep the weights in registers (no indexed local array)
+        const FT wx = ox == 0 ? S.wx[0] : (ox == 1 ? S.wx[1] : S.wx[2]);
+        const FT wy = oy == 0 ? S.wy[0] : (oy == 1 ? S.wy[1] : S.wy[2]);
+        const FT wz = oz == 0 ? S.wz[0] : (oz == 1 ? S.wz[1] : S.wz[2]);
+        fn(cell_index(g, x, y, z), wx * wy * wz);
+    }
+}
+
+// sum over the lanes of a particle's lane group (xor tree: every lane of the
+// group ends with the same bits); all 32 lanes of the warp take part
+template <typename FT, int NV>
+__device__ __forceinline__ void lanes_sum(FT (&v)[NV], int lanes) {
+    for (int o = lanes >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+// Particle tiles carry the lanes per particle of the force kernels in
+// Tile::first (1, 2, 4 or 8; the support's 27 cells split over them): a box
+// with few particles spreads each over several lanes, so its latency-bound
+// gathers run on more warps.  The block size is a multiple of 32 and of the
+// lanes; the loop over a tile's particles has a trip count uniform over the block.
+#define DPS_PARTICLE_GROUPS(tl, lanes, lane, base, p, act)                                  \
+    const int lanes = (tl).first > 1 ? (tl).first : 1;                                     \
+    const int lane = (int)threadIdx.x % lanes, ngrp_ = (int)blockDim.x / lanes;            \
+    for (long long base = (tl).begin, p = (tl).begin + (int)threadIdx.x / lanes; base < (tl).end; \
+         base += ngrp_, p += ngrp_)                                                          \
+        if (const bool act = p < (tl).end; true)
+
 // K5a: added mass, F_am = C_am rho_f V (Du_f/Dt|p - du_p/dt) (Table 1);
 // du_p/dt is the change of u_p over the previous subcycle (taken in FP64).
 // With lift, the shear lift F_l = 1.61 d^2 sqrt(mu rho_f / |w|) (u_f - u_p) x w
@@ -489,24 +670,49 @@ __global__ void k_force_am(const BoxDev *__restrict__ boxes, const Tile *__restr
         const FT *rho = (const FT *)B.rho, *j = (const FT *)B.j, *eps = (const FT *)B.eps;
         const FT *curl = (const FT *)B.curl;
         const FT hb[3] = {FT(0.5) * (FT)ph.fb[0], FT(0.5) * (FT)ph.fb[1], FT(0.5) * (FT)ph.fb[2]};
-        for (long long p = tl.begin + threadIdx.x; p < tl.end; p += blockDim.x) {
-            const Support<FT> S = support_of<FT>(B, pf, p);
-            FT Du[3] = {0, 0, 0}, Fl[3] = {0, 0, 0};
+        DPS_PARTICLE_GROUPS(tl, lanes, lane, base, p, act) {
+            // v: Du_f/Dt at the particle, then (lift) u_f and the vorticity w
+            FT v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            Support<FT> S;
+            if (act) {
+                S = support_of<FT>(B, pf, p);
+                if (lift)
+                    for_support_lanes(g, S, lane, lanes, [&](long long c, FT W) {
+                        v[0] += W * DuDt[c];
+                        v[1] += W * DuDt[N + c];
+                        v[2] += W * DuDt[2 * N + c];
+                        const FT e = eps[c];
+                        const FT sc = W / (rho[c] * e);
+                        v[3] += (j[c] + e * hb[0]) * sc;
+                        v[4] += (j[N + c] + e * hb[1]) * sc;
+                        v[5] += (j[2 * N + c] + e * hb[2]) * sc;
+                        v[6] += W * curl[c];
+                        v[7] += W * curl[N + c];
+                        v[8] += W * curl[2 * N + c];
+                    });
+                else
+                    for_support_lanes(g, S, lane, lanes, [&](long long c, FT W) {
+                        v[0] += W * DuDt[c];
+                        v[1] += W * DuDt[N + c];
+                        v[2] += W * DuDt[2 * N + c];
+                    });
+            }
+            if (lanes > 1) {
+                if (lift)
+                    lanes_sum(v, lanes);
+                else {
+                    FT u3[3] = {v[0], v[1], v[2]};
+                    lanes_sum(u3, lanes);
+                    v[0] = u3[0];
+                    v[1] = u3[1];
+                    v[2] = u3[2];
+                }
+            }
+            if (!act || lane != 0) continue;
+            const FT Du[3] = {v[0], v[1], v[2]};
+            FT Fl[3] = {0, 0, 0};
             if (lift) {
-                FT uf[3] = {0, 0, 0}, w[3] = {0, 0, 0};
-                for_support(g, S, [&](long long c, FT W) {
-                    Du[0] += W * DuDt[c];
-                    Du[1] += W * DuDt[N + c];
-                    Du[2] += W * DuDt[2 * N + c];
-                    const FT e = eps[c];
-                    const FT sc = W / (rho[c] * e);
-                    uf[0] += (j[c] + e * hb[0]) * sc;
-                    uf[1] += (j[N + c] + e * hb[1]) * sc;
-                    uf[2] += (j[2 * N + c] + e * hb[2]) * sc;
-                    w[0] += W * curl[c];
-                    w[1] += W * curl[N + c];
-                    w[2] += W * curl[2 * N + c];
-                });
+                const FT uf[3] = {v[3], v[4], v[5]}, w[3] = {v[6], v[7], v[8]};
                 const FT wn = m_sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
                 if (wn > FT(0)) {
                     const double dp = pf[PD * cap + p];
@@ -517,12 +723,6 @@ __global__ void k_force_am(const BoxDev *__restrict__ boxes, const Tile *__restr
                     Fl[1] = k * (du[2] * w[0] - du[0] * w[2]);
                     Fl[2] = k * (du[0] * w[1] - du[1] * w[0]);
                 }
-            } else {
-                for_support(g, S, [&](long long c, FT W) {
-                    Du[0] += W * DuDt[c];
-                    Du[1] += W * DuDt[N + c];
-                    Du[2] += W * DuDt[2 * N + c];
-                });
             }
             const double d = pf[PD * cap + p];
             const FT cV = (FT)(ph.C_am * ph.rho_f * PI_D / 6.0 * d * d * d);
@@ -574,27 +774,33 @@ __global__ void k_force_drag(const BoxDev *__restrict__ boxes, const Tile *__res
         const FT *rho = (const FT *)Bx.rho, *j = (const FT *)Bx.j, *eps = (const FT *)Bx.eps;
         const FT *fam = (const FT *)Bx.fam, *gradP = (const FT *)Bx.gradP;
         const FT fb[3] = {(FT)ph.fb[0], (FT)ph.fb[1], (FT)ph.fb[2]};
-        for (long long p = tl.begin + threadIdx.x; p < tl.end; p += blockDim.x) {
-            const Support<FT> S = support_of<FT>(Bx, pf, p);
-            FT uf[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, ef = 0;
-            for_support(g, S, [&](long long c, FT W) {
-                const FT e = eps[c];
-                const FT s = FT(1) / (rho[c] * e);
+        DPS_PARTICLE_GROUPS(tl, lanes, lane, base, p, act) {
+            // v: u_f (3), grad P (3), eps_f at the particle
+            FT v[7] = {0, 0, 0, 0, 0, 0, 0};
+            if (act) {
+                const Support<FT> S = support_of<FT>(Bx, pf, p);
+                for_support_lanes(g, S, lane, lanes, [&](long long c, FT W) {
+                    const FT e = eps[c];
+                    const FT s = FT(1) / (rho[c] * e);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const FT F = e * fb[a] + fam[a * N + c];
-                    uf[a] += W * (j[a * N + c] + FT(0.5) * F) * s;
-                    gp[a] += W * gradP[a * N + c];
-                }
-                ef += W * e;
-            });
+                    for (int a = 0; a < 3; ++a) {
+                        const FT F = e * fb[a] + fam[a * N + c];
+                        v[a] += W * (j[a * N + c] + FT(0.5) * F) * s;
+                        v[3 + a] += W * gradP[a * N + c];
+                    }
+                    v[6] += W * e;
+                });
+            }
+            if (lanes > 1) lanes_sum(v, lanes);
+            if (!act || lane != 0) continue;
+            const FT ef = v[6];
             const double d = pf[PD * cap + p], rp = pf[PRHO * cap + p];
             const double V = PI_D / 6.0 * d * d * d;
             const FT ep = FT(1) - ef;
             FT du[3], dun = 0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                du[a] = uf[a] - (FT)pf[(PU + a) * cap + p];
+                du[a] = v[a] - (FT)pf[(PU + a) * cap + p];
                 dun += du[a] * du[a];
             }
             dun = m_sqrt(dun);
@@ -604,7 +810,7 @@ __global__ void k_force_drag(const BoxDev *__restrict__ boxes, const Tile *__res
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const FT Fd = coef * du[a];
-                const FT Fpr = ph.pressure ? -(FT)V * gp[a] : FT(0);
+                const FT Fpr = ph.pressure ? -(FT)V * v[3 + a] : FT(0);
                 const double Fg = (rp - ph.rho_f) * V * ph.g[a];  // gravity + buoyancy
                 pf[(PFD0 + a) * cap + p] = (double)Fd;
                 if (sizeof(FT) == 4) Bx.f32p[(3 + a) * cap + p] = (float)Fd;
@@ -627,9 +833,9 @@ template <> __device__ __forceinline__ const float *force_planes<float>(const Bo
 
 // K6a: f_pf,am(c) = -sum_p W F_am
 template <typename FT>
-__global__ void __launch_bounds__(256) k_reaction_am(const BoxDev *__restrict__ boxes,
-                                                     const Tile *__restrict__ tiles, int ntiles) {
-    __shared__ BrickRanges R;
+__global__ void __launch_bounds__(BRICK_THREADS) k_reaction_am(const BoxDev *__restrict__ boxes,
+                                                               const Tile *__restrict__ tiles, int ntiles) {
+    __shared__ BrickList L;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &B = boxes[tl.box];
@@ -638,32 +844,36 @@ __global__ void __launch_bounds__(256) k_reaction_am(const BoxDev *__restrict__ 
         brick_unpack(tl.begin, ox, oy, oz);
         brick_unpack(tl.end, ex, ey, ez);
         __syncthreads();
-        stage_ranges(B, ox, oy, oz, R);
-        __syncthreads();
+        stage_list(B, ox, oy, oz, L);
         const long long N = g.ncell, cap = B.cap;
         const double *pf = B.pf[B.cur];
         const FT *w = weights_of<FT>(B, pf), *Fa = force_planes<FT>(B, pf, 0);
         FT *fam = (FT *)B.fam;
-        for_brick_cells(g, ox, oy, oz, ex, ey, ez, [&](long long c, int lx, int ly, int lz) {
-            FT s0 = 0, s1 = 0, s2 = 0;
-            gather27_staged(R, lx, ly, lz, w, cap, [&](int p, FT W) {
-                s0 += W * Fa[p];
-                s1 += W * Fa[cap + p];
-                s2 += W * Fa[2 * cap + p];
+        struct St {
+            FT s0, s1, s2;
+        };
+        brick_gather<St>(
+            g, L, ox, oy, oz, ex, ey, ez, w, cap,
+            [&](St &st, int p, FT W) {
+                st.s0 += W * Fa[p];
+                st.s1 += W * Fa[cap + p];
+                st.s2 += W * Fa[2 * cap + p];
+            },
+            [&](St &st, long long c) {
+                fam[c] = -st.s0;
+                fam[N + c] = -st.s1;
+                fam[2 * N + c] = -st.s2;
             });
-            fam[c] = -s0;
-            fam[N + c] = -s1;
-            fam[2 * N + c] = -s2;
-        });
     }
 }
 
 // K6b: acc = (first ? 0 : acc) + f_pf,am - sum_p W F_d; after the last subcycle
 // the applied f_pf is the subcycle average.
 template <typename FT>
-__global__ void __launch_bounds__(256) k_reaction_drag(const BoxDev *__restrict__ boxes,
-                                                       const Tile *__restrict__ tiles, int ntiles, int first, int last) {
-    __shared__ BrickRanges R;
+__global__ void __launch_bounds__(BRICK_THREADS) k_reaction_drag(const BoxDev *__restrict__ boxes,
+                                                                 const Tile *__restrict__ tiles, int ntiles, int first,
+                                                                 int last) {
+    __shared__ BrickList L;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &B = boxes[tl.box];
@@ -672,31 +882,34 @@ __global__ void __launch_bounds__(256) k_reaction_drag(const BoxDev *__restrict_
         brick_unpack(tl.begin, ox, oy, oz);
         brick_unpack(tl.end, ex, ey, ez);
         __syncthreads();
-        stage_ranges(B, ox, oy, oz, R);
-        __syncthreads();
+        stage_list(B, ox, oy, oz, L);
         const long long N = g.ncell, cap = B.cap;
         const double *pf = B.pf[B.cur];
         const FT *w = weights_of<FT>(B, pf), *Fd = force_planes<FT>(B, pf, 1);
         const FT *fam = (const FT *)B.fam;
         FT *acc = (FT *)B.acc, *fpf = (FT *)B.fpf;
         const FT inv_nint = (FT)B.ph.dt_sub;
-        for_brick_cells(g, ox, oy, oz, ex, ey, ez, [&](long long c, int lx, int ly, int lz) {
-            FT s[3] = {0, 0, 0};
-            gather27_staged(R, lx, ly, lz, w, cap, [&](int p, FT W) {
-                s[0] += W * Fd[p];
-                s[1] += W * Fd[cap + p];
-                s[2] += W * Fd[2 * cap + p];
-            });
+        struct St {
+            FT s[3];
+        };
+        brick_gather<St>(
+            g, L, ox, oy, oz, ex, ey, ez, w, cap,
+            [&](St &st, int p, FT W) {
+                st.s[0] += W * Fd[p];
+                st.s[1] += W * Fd[cap + p];
+                st.s[2] += W * Fd[2 * cap + p];
+            },
+            [&](St &st, long long c) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const FT k = fam[a * N + c] - s[a];
-                const FT v = first ? k : acc[a * N + c] + k;
-                if (last)
-                    fpf[a * N + c] = v * inv_nint;
-                else
-                    acc[a * N + c] = v;
-            }
-        });
+                for (int a = 0; a < 3; ++a) {
+                    const FT k = fam[a * N + c] - st.s[a];
+                    const FT v = first ? k : acc[a * N + c] + k;
+                    if (last)
+                        fpf[a * N + c] = v * inv_nint;
+                    else
+                        acc[a * N + c] = v;
+                }
+            });
     }
 }
 
@@ -756,7 +969,7 @@ void launch_end_step(BoxDev *b, int nb, cudaStream_t s) { k_end_step<<<(nb + 127
 
 template <typename FT>
 void launch_eps(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
-    k_eps_gather<FT><<<grid, 256, 0, s>>>(b, t, nt);
+    k_eps_gather<FT><<<grid, BRICK_THREADS, 0, s>>>(b, t, nt);
 }
 template <typename FT>
 void launch_force_am(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
@@ -768,12 +981,12 @@ void launch_force_drag(const BoxDev *b, const Tile *t, int nt, int grid, int blo
 }
 template <typename FT>
 void launch_reaction_am(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
-    k_reaction_am<FT><<<grid, 256, 0, s>>>(b, t, nt);
+    k_reaction_am<FT><<<grid, BRICK_THREADS, 0, s>>>(b, t, nt);
 }
 template <typename FT>
 void launch_reaction_drag(const BoxDev *b, const Tile *t, int nt, int first, int last, int grid, int block,
                           cudaStream_t s) {
-    k_reaction_drag<FT><<<grid, 256, 0, s>>>(b, t, nt, first, last);
+    k_reaction_drag<FT><<<grid, BRICK_THREADS, 0, s>>>(b, t, nt, first, last);
 }
 
 #define DPS_CPL_INST(FT)                                                                                  \
