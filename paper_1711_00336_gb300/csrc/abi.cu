@@ -19,7 +19,7 @@
 namespace dps {
 // launchers (lbm.cu, coupling.cu, dem.cu, scan.cu, io.cu)
 template <typename ST, typename FT, typename CT>
-void launch_collide_stream(const BoxDev *, const Tile *, int, int, int, bool, int, int, cudaStream_t);
+void launch_collide_stream(const BoxDev *, const Tile *, int, int, int, bool, bool, int, int, cudaStream_t);
 template <typename ST, typename FT, typename CT>
 void launch_moments(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 template <typename FT, typename CT>
@@ -470,8 +470,10 @@ static int part_threads(const Tuning &u, int lanes) {
 
 // K1 over the cell tiles of the boxes with a constant tau, then the per-cell
 // tau_e variant over those of the boxes with the Eilers / Smagorinsky
-// closures (one launch when the batch holds one kind); returns the launches
-static int enqueue_collide(Batch *B, int par) {
+// closures (one launch when the batch holds one kind); returns the launches.
+// mom_in: K2a ran on these populations in this step (the coupled step), so
+// the FP64 form takes rho and j from it.
+static int enqueue_collide(Batch *B, int par, bool mom_in) {
     const BoxDev *T = B->d_table;
     const Tuning &u = B->tune;
     cudaStream_t s = B->stream;
@@ -481,9 +483,9 @@ static int enqueue_collide(Batch *B, int par) {
         if (nt <= 0) continue;
         const Tile *tl = B->d_cell + (v ? B->n_cell_plain : 0);
         const bool vi = v == 1;
-        PREC_CALL(B, (launch_collide_stream<double, double, double>(T, tl, nt, par, u.k1v, vi, grid_of(nt), u.cell_block, s)),
-                  (launch_collide_stream<float, float, float>(T, tl, nt, par, u.k1v, vi, grid_of(nt), u.cell_block, s)),
-                  (launch_collide_stream<__half, float, float>(T, tl, nt, par, u.k1v, vi, grid_of(nt), u.cell_block, s)));
+        PREC_CALL(B, (launch_collide_stream<double, double, double>(T, tl, nt, par, u.k1v, vi, mom_in, grid_of(nt), u.cell_block, s)),
+                  (launch_collide_stream<float, float, float>(T, tl, nt, par, u.k1v, vi, mom_in, grid_of(nt), u.cell_block, s)),
+                  (launch_collide_stream<__half, float, float>(T, tl, nt, par, u.k1v, vi, mom_in, grid_of(nt), u.cell_block, s)));
         ++nl;
     }
     return nl;
@@ -599,7 +601,7 @@ static void enqueue_step(Batch *B) {
         enqueue_sort_eps(B, B->n_dem & 1, 1);
     }
     tbegin(B);
-    const int nk1 = enqueue_collide(B, par);
+    const int nk1 = enqueue_collide(B, par, true);
     launch_end_step(B->d_table, (int)B->boxes.size(), s);
     tend(B, PH_COLLIDE, nk1 + 1);
     B->launches_step = B->launch_count;
@@ -1234,7 +1236,7 @@ int dps_collide_stream(dps_handle h, int64_t n) {
     if (rc) return rc;
     if ((rc = push_layout(B))) return rc;
     for (int64_t s = 0; s < n; ++s) {
-        enqueue_collide(B, B->parity);
+        enqueue_collide(B, B->parity, false);
         B->parity ^= 1;
     }
     return check_boxes(B);

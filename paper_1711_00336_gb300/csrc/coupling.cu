@@ -221,6 +221,14 @@ __global__ void k_bsort_gather(const BoxDev *__restrict__ boxes, const Tile *__r
                     dstf[(PW0 + 3 * a + 2) * cap + k] = w[2];
                 }
             }
+            {
+                // mass and the inverse factors of Eq. particle_motion (I = m d^2 / 10)
+                const double dd = srcf[PD * cap + i];
+                const double m = srcf[PRHO * cap + i] * PI_D / 6.0 * dd * dd * dd;
+                dstf[PM * cap + k] = m;
+                dstf[PIM * cap + k] = 1.0 / m;
+                dstf[PII * cap + k] = 10.0 / (m * dd * dd);
+            }
             dsti[IID * cap + k] = srci[IID * cap + i];
             dsti[ICELL * cap + k] = B.key[i];
             dsti[IKEY * cap + k] = B.key[i];

@@ -70,75 +70,88 @@ __device__ __forceinline__ PairPar<T> pair_par(const Phys &ph) {
     return q;
 }
 
+// spring-dashpot contact with Coulomb friction (Sec. 3.1.1) for overlap
+// delta > 0, in arithmetic T, accumulated in T; the torque is
+// (d_i/2) n x F_t (r x F at the contact point r = d_i/2 n).
+template <typename T>
+__device__ __forceinline__ void contact_force(const PairPar<T> &ph, const T n[3], T delta, const T ui[3],
+                                              const T wi[3], T di, const T uj[3], const T wjh[3], T m_ij, T F[3],
+                                              T Tq[3]) {
+    // k_n and xi_n of Eqs. damping_to_stiffness / collision_time, solved
+    // for the given e_n and T_c: both proportional to m_ij
+    const T k_n = m_ij * ph.kfac;
+    const T xi = m_ij * ph.xfac;
+    T ws[3], wx[3], ur[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ws[a] = T(0.5) * di * wi[a] + wjh[a];
+    cross3(ws, n, wx);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ur[a] = ui[a] - uj[a] + wx[a];
+    const T urn = ur[0] * n[0] + ur[1] * n[1] + ur[2] * n[2];
+    T ut[3], Fn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ut[a] = ur[a] - urn * n[a];
+        Fn[a] = -k_n * delta * n[a] - xi * (urn * n[a]);
+    }
+    const T Fn_abs = m_sqrt(Fn[0] * Fn[0] + Fn[1] * Fn[1] + Fn[2] * Fn[2]);
+    const T ut_abs = m_sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+    T Ft[3] = {0, 0, 0};
+    if (ut_abs > T(0)) {
+        const T mag = m_min(ph.mu_c * Fn_abs, xi * ut_abs) / ut_abs;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Ft[a] = -mag * ut[a];
+    }
+    T nF[3];
+    cross3(n, Ft, nF);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        F[a] += Fn[a] + Ft[a];
+        Tq[a] += T(0.5) * di * nF[a];
+    }
+}
+
+// lubrication correction (Sec. 3.1.3) at the floored gap hh, given <d>,
+// r = <d>/hh, ir = 1/r and the limiter cap m_ij capfac
+template <typename T>
+__device__ __forceinline__ void lub_force(const PairPar<T> &ph, const T n[3], T dmean, T r, T ir, T cap,
+                                          const T ui[3], const T uj[3], T F[3], unsigned &nlim) {
+    const T L = m_log(T(0.5) * r);  // ln(<d>/(2h))
+    T a_sq = T(1.5 * PI_D) * ph.mu * dmean * (T(0.25) * r + T(18.0 / 40.0) * L + T(9.0 / 84.0) * L * ir);
+    // a_sh (2/(h+<d>))^2 = (pi/2) mu <d> ln(<d>/(2h))
+    T a_sh = T(0.5 * PI_D) * ph.mu * dmean * L;
+    a_sq = m_max(a_sq, T(0));
+    a_sh = m_max(a_sh, T(0));
+    if (ph.lub_limiter) {
+        if (a_sq > cap) { a_sq = cap; ++nlim; }
+        if (a_sh > cap) { a_sh = cap; ++nlim; }
+    }
+    T upr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) upr[a] = ui[a] - uj[a];
+    const T upn = upr[0] * n[0] + upr[1] * n[1] + upr[2] * n[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[a] += -a_sq * upn * n[a] - a_sh * (upr[a] - upn * n[a]);
+}
+
 // force and torque on i from one partner (sphere or wall), Sec. 3.1.1 / 3.1.3,
-// in arithmetic T, accumulated in T; the torque is (d_i/2) n x F_t (r x F at
-// the contact point r = d_i/2 n).
+// given m_ij and <d>: contact while overlapping, lubrication on pairs that do
+// not overlap, 0 <= h < h_c (in contact the spring-dashpot acts alone, which
+// keeps the wet rebound of Sec. 5)
 template <typename T>
 __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T dist, T sumr, const T ui[3],
                                         const T wi[3], T di, const T uj[3], const T wjh[3], T m_ij, T dmean, T F[3],
                                         T Tq[3], unsigned &nlim) {
     const T delta = sumr - dist;
-    if (ph.contact && delta > T(0)) {
-        // k_n and xi_n of Eqs. damping_to_stiffness / collision_time, solved
-        // for the given e_n and T_c: both proportional to m_ij
-        const T k_n = m_ij * ph.kfac;
-        const T xi = m_ij * ph.xfac;
-        T ws[3], wx[3], ur[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ws[a] = T(0.5) * di * wi[a] + wjh[a];
-        cross3(ws, n, wx);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ur[a] = ui[a] - uj[a] + wx[a];
-        const T urn = ur[0] * n[0] + ur[1] * n[1] + ur[2] * n[2];
-        T ut[3], Fn[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            ut[a] = ur[a] - urn * n[a];
-            Fn[a] = -k_n * delta * n[a] - xi * (urn * n[a]);
-        }
-        const T Fn_abs = m_sqrt(Fn[0] * Fn[0] + Fn[1] * Fn[1] + Fn[2] * Fn[2]);
-        const T ut_abs = m_sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
-        T Ft[3] = {0, 0, 0};
-        if (ut_abs > T(0)) {
-            const T mag = m_min(ph.mu_c * Fn_abs, xi * ut_abs) / ut_abs;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) Ft[a] = -mag * ut[a];
-        }
-        T nF[3];
-        cross3(n, Ft, nF);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            F[a] += Fn[a] + Ft[a];
-            Tq[a] += T(0.5) * di * nF[a];
-        }
-    }
-    // lubrication on pairs that do not overlap, 0 <= h < h_c (in contact the
-    // spring-dashpot acts alone, which keeps the wet rebound of Sec. 5)
+    if (ph.contact && delta > T(0)) contact_force(ph, n, delta, ui, wi, di, uj, wjh, m_ij, F, Tq);
     const T h = dist - sumr;
     if (ph.lubrication && h >= T(0) && h < ph.h_c) {
         const T hh = m_max(h, ph.h_min);
-        const T r = dmean / hh;          // <d>/h
-        const T L = m_log(T(0.5) * r);     // ln(<d>/(2h))
-        T a_sq = T(1.5 * PI_D) * ph.mu * dmean * (T(0.25) * r + T(18.0 / 40.0) * L + T(9.0 / 84.0) * L / r);
-        // a_sh (2/(h+<d>))^2 = (pi/2) mu <d> ln(<d>/(2h))
-        T a_sh = T(0.5 * PI_D) * ph.mu * dmean * L;
-        a_sq = m_max(a_sq, T(0));
-        a_sh = m_max(a_sh, T(0));
-        if (ph.lub_limiter) {
-            const T cap = m_ij * ph.capfac;
-            if (a_sq > cap) { a_sq = cap; ++nlim; }
-            if (a_sh > cap) { a_sh = cap; ++nlim; }
-        }
-        T upr[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) upr[a] = ui[a] - uj[a];
-        const T upn = upr[0] * n[0] + upr[1] * n[1] + upr[2] * n[2];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) F[a] += -a_sq * upn * n[a] - a_sh * (upr[a] - upn * n[a]);
+        const T q = T(1) / (dmean * hh);  // r and 1/r from one division
+        lub_force(ph, n, dmean, dmean * dmean * q, hh * hh * q, m_ij * ph.capfac, ui, uj, F, nlim);
     }
 }
 
-// ---- neighbour list ----------------------------------------------------------------
 // list of particle i: partners j != i with |x_j - x_i| < (d_i+d_j)/2 + extra + skin
 // (screened in FP32 with a margin), stored row by row: nlist[i*maxn + k].
 // LANES lanes share a particle: lane l scans the cell rows l, l + LANES, ...
@@ -255,24 +268,34 @@ __device__ __forceinline__ void pair64_body(const PairPar<double> &pd, const dou
     const double dj = pf[PD * cap + j];
     const double sumr = 0.5 * (di + dj);
     if (!(dist2 > 0.0)) return;
-    // 1/|dx| and |dx| from one reciprocal square root, m_ij and <d> from one
-    // division (FP64 instructions bound this path on this GPU)
-    const double inv = rsqrt(dist2);
+    const double inv = rsqrt(dist2);  // 1/|dx| and |dx| from one reciprocal square root
     const double dist = dist2 * inv;
     if (!(dist < sumr + rng_extra)) return;
-    const double mj = pf[PRHO * cap + j] * PI_D / 6.0 * dj * dj * dj;
-    const double sm = mi + mj, sd = di + dj;
-    const double qd = 1.0 / (sm * sd);
-    const double m_ij = mi * mj * sd * qd;
-    const double dmean = 2.0 * di * dj * sm * qd;
+    const double mj = pf[PM * cap + j];
     const double n[3] = {dx[0] * inv, dx[1] * inv, dx[2] * inv};
-    double uj[3], wjh[3];
+    double uj[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        uj[a] = xin[(3 + a) * cap + j];
-        wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
+    for (int a = 0; a < 3; ++a) uj[a] = xin[(3 + a) * cap + j];
+    // m_ij = m_i m_j / (m_i + m_j) and <d> = 2 d_i d_j / (d_i + d_j): one
+    // division per pair (FP64 instructions bound this path on this GPU)
+    const double delta = sumr - dist;
+    if (pd.contact && delta > 0.0) {
+        double wjh[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
+        contact_force(pd, n, delta, ui, wi, di, uj, wjh, mi * mj / (mi + mj), F, T);
     }
-    partner<double>(pd, n, dist, sumr, ui, wi, di, uj, wjh, m_ij, dmean, F, T, nlim);
+    const double h = dist - sumr;
+    if (pd.lubrication && h >= 0.0 && h < pd.h_c) {
+        const double hh = fmax(h, pd.h_min);
+        const double sm = mi + mj, sd = di + dj, dd2 = 2.0 * di * dj;
+        const double q = 1.0 / (sm * sd * hh * dd2);
+        const double dmean = dd2 * dd2 * sm * hh * q;  // dd2 / sd
+        const double r = dd2 * dd2 * sm * q;           // <d> / hh
+        const double ir = sm * sd * sd * hh * hh * q;  // hh / <d>
+        const double cap = mi * mj * sd * hh * dd2 * q * pd.capfac;  // m_ij capfac
+        lub_force(pd, n, dmean, r, ir, cap, ui, uj, F, nlim);
+    }
 }
 // the mixed forms' near-contact pair: loads the FP64 state of particle i itself
 __device__ __noinline__ void pair64_out(const BoxDev &Bx, const double *__restrict__ xin, long long i, long long j,
@@ -287,7 +310,7 @@ __device__ __noinline__ void pair64_out(const BoxDev &Bx, const double *__restri
         wi[a] = xin[(6 + a) * cap + i];
     }
     const double di = pf[PD * cap + i];
-    const double mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
+    const double mi = pf[PM * cap + i];
     const double rng_extra = Bx.ph.lubrication ? fmax(Bx.ph.h_c, 0.0) : 0.0;
     const PairPar<double> pd = pair_par<double>(Bx.ph);
     const Geom g = Bx.g;
@@ -316,7 +339,7 @@ __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<
     }
     const float4 pi = fin[i], vi = vin[i];
     const double di = pf[PD * cap + i];
-    const double mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
+    const double mi = pf[PM * cap + i];
     // walls: the faces of every non-periodic axis (m_ij = m_i, <d> = 2 d_i)
     const double zero[3] = {0, 0, 0};
 #pragma unroll
@@ -333,7 +356,7 @@ __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<
         }
     }
     // Eq. particle_motion, semi-implicit Euler with I = m d^2 / 10
-    const double dt_m = ph.dt_dem / mi, dt_I = ph.dt_dem * 10.0 / (mi * di * di);
+    const double dt_m = ph.dt_dem * pf[PIM * cap + i], dt_I = ph.dt_dem * pf[PII * cap + i];
     double d2 = 0.0, xn3[3], un3[3], wn3[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -415,7 +438,7 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                             wi[a] = xin[(6 + a) * cap + i];
                         }
                         di = pf[PD * cap + i];
-                        mi = pf[PRHO * cap + i] * PI_D / 6.0 * di * di * di;
+                        mi = pf[PM * cap + i];
                     }
                     const float4 pi = fin[i], vi = vin[i], oi = oin[i];
                     const int nn = Bx.nlist_n[i];

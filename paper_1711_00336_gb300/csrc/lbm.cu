@@ -111,15 +111,28 @@ __device__ __forceinline__ CT tau_cell(const CT f[Q], CT s, CT rho, CT ux, CT uy
 // (Eq. LBM_Equation, same algebra as collide()) and store each opposite pair
 // as soon as it is computed, which keeps few values live.  VISC: the box may
 // relax with a per-cell tau_e (vmode bit 0 Eilers, bit 1 Smagorinsky).
-template <typename ST, typename FT, typename CT, int PAR, bool VISC>
+template <typename ST, typename FT, typename CT, int PAR, bool VISC, bool MOMIN>
 __device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], const NbDelta &D, bool in,
                                                  const Geom &g, CT e, CT fpx, CT fpy, CT fpz, long long N, long long c,
                                                  CT fbx, CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
-                                                 int *status);
+                                                 int *status, const CT *mom);
 
-template <typename ST, typename FT, typename CT, int PAR, bool VISC>
+// the moments of cell c from K2a (MOMIN), else nothing
+template <typename FT, typename CT, bool MOMIN>
+__device__ __forceinline__ void load_moments(const FT *__restrict__ rho, const FT *__restrict__ j, long long N,
+                                             long long c, CT mom[4]) {
+    if (MOMIN) {
+        mom[0] = (CT)rho[c];
+        mom[1] = (CT)j[c];
+        mom[2] = (CT)j[N + c];
+        mom[3] = (CT)j[2 * N + c];
+    }
+}
+
+template <typename ST, typename FT, typename CT, int PAR, bool VISC, bool MOMIN>
 __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const FT *__restrict__ eps,
-                                                    const FT *__restrict__ fpf, const Geom &g, long long c, CT fbx,
+                                                    const FT *__restrict__ fpf, const FT *__restrict__ rho_m,
+                                                    const FT *__restrict__ j_m, const Geom &g, long long c, CT fbx,
                                                     CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
                                                     int *status) {
     const long long N = g.ncell;
@@ -138,16 +151,19 @@ __device__ __forceinline__ void collide_stream_cell(ST *__restrict__ pdf, const 
     } else {
         load_pdfs<ST, CT, PAR>(pdf, N, c, D, f);
     }
-    relax_store_cell<ST, FT, CT, PAR, VISC>(pdf, f, D, in, g, (CT)eps[c], (CT)fpf[c], (CT)fpf[N + c],
-                                            (CT)fpf[2 * N + c], N, c, fbx, fby, fbz, omega_box, kf_box, tau, vmode,
-                                            status);
+    CT mom[4];
+    load_moments<FT, CT, MOMIN>(rho_m, j_m, N, c, mom);
+    relax_store_cell<ST, FT, CT, PAR, VISC, MOMIN>(pdf, f, D, in, g, (CT)eps[c], (CT)fpf[c], (CT)fpf[N + c],
+                                                   (CT)fpf[2 * N + c], N, c, fbx, fby, fbz, omega_box, kf_box, tau,
+                                                   vmode, status, mom);
 }
 
 // two cells per thread (c and c + stride): the loads of both are issued before
 // either is relaxed, which doubles the bytes in flight per warp
-template <typename ST, typename FT, typename CT, int PAR, bool VISC>
+template <typename ST, typename FT, typename CT, int PAR, bool VISC, bool MOMIN>
 __device__ __forceinline__ void collide_stream_cell2(ST *__restrict__ pdf, const FT *__restrict__ eps,
-                                                     const FT *__restrict__ fpf, const Geom &g, long long c,
+                                                     const FT *__restrict__ fpf, const FT *__restrict__ rho_m,
+                                                     const FT *__restrict__ j_m, const Geom &g, long long c,
                                                      long long c2, bool two, CT fbx, CT fby, CT fbz, CT omega_box,
                                                      CT kf_box, CT tau, int vmode, int *status) {
     const long long N = g.ncell;
@@ -184,11 +200,14 @@ __device__ __forceinline__ void collide_stream_cell2(ST *__restrict__ pdf, const
         b1 = (CT)fpf[N + c2];
         b2 = (CT)fpf[2 * N + c2];
     }
-    relax_store_cell<ST, FT, CT, PAR, VISC>(pdf, f, D, in, g, e, a0, a1, a2, N, c, fbx, fby, fbz, omega_box, kf_box,
-                                            tau, vmode, status);
+    CT mom[4], mom2[4];
+    load_moments<FT, CT, MOMIN>(rho_m, j_m, N, c, mom);
+    if (two) load_moments<FT, CT, MOMIN>(rho_m, j_m, N, c2, mom2);
+    relax_store_cell<ST, FT, CT, PAR, VISC, MOMIN>(pdf, f, D, in, g, e, a0, a1, a2, N, c, fbx, fby, fbz, omega_box,
+                                                   kf_box, tau, vmode, status, mom);
     if (two)
-        relax_store_cell<ST, FT, CT, PAR, VISC>(pdf, f2, D2, in2, g, e2, b0, b1, b2, N, c2, fbx, fby, fbz,
-                                                omega_box, kf_box, tau, vmode, status);
+        relax_store_cell<ST, FT, CT, PAR, VISC, MOMIN>(pdf, f2, D2, in2, g, e2, b0, b1, b2, N, c2, fbx, fby, fbz,
+                                                       omega_box, kf_box, tau, vmode, status, mom2);
 }
 
 // Correctly rounded single operations: the relaxation below spells out every
@@ -207,22 +226,32 @@ __device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a
 // relaxation (Eq. LBM_Equation) of one cell whose populations f, eps_f and
 // f_pf are loaded: f is overwritten with the post-collision populations.
 // `flag`: report a non-finite or non-positive density.
-template <typename ST, typename CT, bool VISC>
+// MOMIN: the moments s, j of these populations were computed by K2a in this
+// step with the same sums (the FP64 form): they are passed in, not re-summed.
+template <typename ST, typename CT, bool VISC, bool MOMIN = false>
 __device__ __forceinline__ void relax_cell(CT f[Q], CT e, CT fpx, CT fpy, CT fpz, CT fbx, CT fby, CT fbz,
-                                           CT omega_box, CT kf_box, CT tau, int vmode, bool flag, int *status) {
+                                           CT omega_box, CT kf_box, CT tau, int vmode, bool flag, int *status,
+                                           const CT *mom = nullptr) {
     constexpr bool DEV = Store<ST>::shifted;
     // f_ext = f_pf + eps_f f_b (Eq. Forcing)
     const CT Fx = r_fma(e, fbx, fpx);
     const CT Fy = r_fma(e, fby, fpy);
     const CT Fz = r_fma(e, fbz, fpz);
     CT s = f[0], jx = 0, jy = 0, jz = 0;
+    if (MOMIN) {
+        s = mom[0];
+        jx = mom[1];
+        jy = mom[2];
+        jz = mom[3];
+    } else {
 #pragma unroll
-    for (int k = 1; k <= 9; ++k) {
-        s = r_add(s, r_add(f[k], f[k + 9]));
-        const CT d = r_sub(f[k], f[k + 9]);
-        if (CX(k) != 0) jx = CX(k) > 0 ? r_add(jx, d) : r_sub(jx, d);
-        if (CY(k) != 0) jy = CY(k) > 0 ? r_add(jy, d) : r_sub(jy, d);
-        if (CZ(k) != 0) jz = CZ(k) > 0 ? r_add(jz, d) : r_sub(jz, d);
+        for (int k = 1; k <= 9; ++k) {
+            s = r_add(s, r_add(f[k], f[k + 9]));
+            const CT d = r_sub(f[k], f[k + 9]);
+            if (CX(k) != 0) jx = CX(k) > 0 ? r_add(jx, d) : r_sub(jx, d);
+            if (CY(k) != 0) jy = CY(k) > 0 ? r_add(jy, d) : r_sub(jy, d);
+            if (CZ(k) != 0) jz = CZ(k) > 0 ? r_add(jz, d) : r_sub(jz, d);
+        }
     }
     const CT rho = DEV ? r_add(CT(1), s) : s;
     if (flag && (!(rho > CT(0)) || !(rho < CT(1e30)))) atomicOr(status, ST_NAN);
@@ -264,12 +293,13 @@ __device__ __forceinline__ void relax_cell(CT f[Q], CT e, CT fpx, CT fpy, CT fpz
 }
 
 // relaxation and parity-aware stores of one cell
-template <typename ST, typename FT, typename CT, int PAR, bool VISC>
+template <typename ST, typename FT, typename CT, int PAR, bool VISC, bool MOMIN>
 __device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], const NbDelta &D, bool in,
                                                  const Geom &g, CT e, CT fpx, CT fpy, CT fpz, long long N, long long c,
                                                  CT fbx, CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
-                                                 int *status) {
-    relax_cell<ST, CT, VISC>(f, e, fpx, fpy, fpz, fbx, fby, fbz, omega_box, kf_box, tau, vmode, true, status);
+                                                 int *status, const CT *mom) {
+    relax_cell<ST, CT, VISC, MOMIN>(f, e, fpx, fpy, fpz, fbx, fby, fbz, omega_box, kf_box, tau, vmode, true, status,
+                                    mom);
     Store<ST>::store(pdf + (unsigned)c, f[0]);
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
@@ -284,8 +314,9 @@ template <typename CT> __device__ __forceinline__ CT pick(double d, float f);
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
-// K1: every cell tile of every box, AA parity PAR (common to the batch)
-template <typename ST, typename FT, typename CT, int PAR, int MINB, bool VISC, int CPT>
+// K1: every cell tile of every box, AA parity PAR (common to the batch).
+// MOMIN: rho and j come from K2a of the same step (FP64 coupled step)
+template <typename ST, typename FT, typename CT, int PAR, int MINB, bool VISC, int CPT, bool MOMIN = false>
 __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__restrict__ boxes,
                                                            const Tile *__restrict__ tiles, int ntiles) {
     DPS_FOR_TILES(tiles, ntiles, t) {
@@ -294,6 +325,7 @@ __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__re
         const Geom g = B.g;
         ST *pdf = (ST *)B.pdf;
         const FT *eps = (const FT *)B.eps, *fpf = (const FT *)B.fpf;
+        const FT *rho_m = (const FT *)B.rho, *j_m = (const FT *)B.j;
         const CT fbx = pick<CT>(B.ph.fb[0], B.ph.fb_f[0]), fby = pick<CT>(B.ph.fb[1], B.ph.fb_f[1]),
                  fbz = pick<CT>(B.ph.fb[2], B.ph.fb_f[2]);
         const CT omega = pick<CT>(B.ph.omega, B.ph.omega_f), kf = pick<CT>(B.ph.kf, B.ph.kf_f);
@@ -302,13 +334,13 @@ __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__re
         int *st = B.status;
         if (CPT == 1) {
             for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
-                collide_stream_cell<ST, FT, CT, PAR, VISC>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, tau, vmode,
-                                                           st);
+                collide_stream_cell<ST, FT, CT, PAR, VISC, MOMIN>(pdf, eps, fpf, rho_m, j_m, g, c, fbx, fby, fbz,
+                                                                  omega, kf, tau, vmode, st);
         } else {
             for (long long c = tl.begin + threadIdx.x; c < tl.end; c += 2 * blockDim.x) {
                 const long long c2 = c + blockDim.x;
-                collide_stream_cell2<ST, FT, CT, PAR, VISC>(pdf, eps, fpf, g, c, c2, c2 < tl.end, fbx, fby, fbz,
-                                                            omega, kf, tau, vmode, st);
+                collide_stream_cell2<ST, FT, CT, PAR, VISC, MOMIN>(pdf, eps, fpf, rho_m, j_m, g, c, c2, c2 < tl.end,
+                                                                   fbx, fby, fbz, omega, kf, tau, vmode, st);
             }
         }
     }
@@ -520,22 +552,28 @@ static int grid_for(long long n, int block) {
 // relaxes with a per-cell tau_e (one register budget for that variant).
 template <typename ST, typename FT, typename CT>
 void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, int parity, int variant, bool visc,
-                           int grid, int block, cudaStream_t s) {
+                           bool mom_in, int grid, int block, cudaStream_t s) {
     block = 128;
     if (sizeof(CT) == 8) variant = 0;  // FP64: one register-heavy variant
-#define DPS_K1V(MB, V, CPT)                                                                            \
-    do {                                                                                               \
-        if (parity)                                                                                    \
-            k_collide_stream<ST, FT, CT, 1, MB, V, CPT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
-        else                                                                                           \
-            k_collide_stream<ST, FT, CT, 0, MB, V, CPT><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
+#define DPS_K1VM(MB, V, CPT, M)                                                                           \
+    do {                                                                                                  \
+        if (parity)                                                                                       \
+            k_collide_stream<ST, FT, CT, 1, MB, V, CPT, M><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
+        else                                                                                              \
+            k_collide_stream<ST, FT, CT, 0, MB, V, CPT, M><<<grid, block, 0, s>>>(boxes, tiles, ntiles);  \
     } while (0)
+#define DPS_K1V(MB, V, CPT) DPS_K1VM(MB, V, CPT, false)
 #define DPS_K1(MB, CPT) DPS_K1V(MB, false, CPT)
     if constexpr (sizeof(CT) == 8) {
-        if (visc)
-            DPS_K1V(2, true, 1);
-        else
-            DPS_K1(2, 1);
+        // the FP64 coupled step takes rho and j from K2a (same sums, one
+        // fifth fewer FP64 instructions)
+        if (visc) {
+            if (mom_in) DPS_K1VM(2, true, 1, true);
+            else DPS_K1V(2, true, 1);
+        } else {
+            if (mom_in) DPS_K1VM(2, false, 1, true);
+            else DPS_K1(2, 1);
+        }
     } else if (visc)
         DPS_K1V(3, true, 1);
     else if (variant == 1)
@@ -552,6 +590,7 @@ void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, i
         DPS_K1(4, 1);
 #undef DPS_K1
 #undef DPS_K1V
+#undef DPS_K1VM
 }
 
 template <typename ST, typename FT, typename CT>
@@ -591,7 +630,7 @@ void launch_pdf_import(void *pdf, long long N, const double *in, cudaStream_t s)
 
 // explicit instantiations for the three precision forms
 #define DPS_LBM_INST(ST, FT, CT)                                                                             \
-    template void launch_collide_stream<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, bool, int, int, cudaStream_t); \
+    template void launch_collide_stream<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, bool, bool, int, int, cudaStream_t); \
     template void launch_moments<ST, FT, CT>(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 DPS_LBM_INST(double, double, double)
 DPS_LBM_INST(float, float, float)
