@@ -38,23 +38,26 @@ def closure_kw(wl):
                 C_am=0.5, n_int=1, n_dem=10, lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5)
 
 
-def algorithmic_bytes_collide(prec):
-    """K1 per cell: 19 PDF loads + 19 stores, eps_f and f_pf (3) loads."""
+def algorithmic_bytes_collide(prec, mom_in=False):
+    """K1 per cell: 19 PDF loads + 19 stores, eps_f and f_pf (3) loads; in the
+    FP64 coupled step (mom_in) also rho and j (4) from the moments pass."""
     s = {"f64": 8, "f32": 4, "f16s": 2}[prec]
     sf = 8 if prec == "f64" else 4
-    return 2 * 19 * s + 4 * sf
+    return 2 * 19 * s + (8 if mom_in else 4) * sf
 
 
 # FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA lanes) x 2.07 GHz maximum SM clock
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 # algorithmic FP64 flops (a division, square root or logarithm counted as one)
-K1_FLOPS_F64 = 249        # per cell: moments 42, velocity and invariants 36, 9 pairs x 16 + 13 more
-DEM_FLOPS_PARTICLE = 38   # per particle and substep: mass, semi-implicit Euler of u, w, x, skin check
+# per cell: velocity and invariants 36, 9 pairs x 16 + 13 more (rho and j, 42
+# flops, come from the moments pass of the same step)
+K1_FLOPS_F64 = 207
+DEM_FLOPS_PARTICLE = 32   # per particle and substep: semi-implicit Euler of u, w, x, skin check
 DEM_FLOPS_PAIR = 75       # per interacting partner: separation 9, masses / normal 17, Ball-Melrose force 49
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel
 # and workload (profiles/step_kernels_wall_suspension.md); None where no
 # capture of the current kernel exists
-TRAFFIC = {("dem_substep", "f64"): 1.43e6, ("collide_stream", "f64"): 48.39e6}
+TRAFFIC = {("dem_substep", "f64"): None, ("collide_stream", "f64"): None}
 
 
 def lubrication_partners(x, d, n, periodic, h_c):
@@ -323,8 +326,8 @@ def main():
                    "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": k1_flops / FP64_PEAK_GFLOPS,
                    "traffic": TRAFFIC.get(("collide_stream", "f64")), "flops_per_cell": K1_FLOPS_F64,
                    "cells_per_launch": ncell, "per_launch_us": k1_ms * 1e3,
-                   "hbm_view": {"achieved_GBps": algorithmic_bytes_collide("f64") * ncell / (k1_ms * 1e-3) / 1e9,
-                                "peak_GBps": hbm, "bytes_per_cell": algorithmic_bytes_collide("f64")},
+                   "hbm_view": {"achieved_GBps": algorithmic_bytes_collide("f64", True) * ncell / (k1_ms * 1e-3) / 1e9,
+                                "peak_GBps": hbm, "bytes_per_cell": algorithmic_bytes_collide("f64", True)},
                    "peak_source": "152 SMs x 4 FP64 flop/clk x 2.07 GHz (derived)"}
         if dom_phase == "dem_substep":
             dm = phase["dem_substep"]

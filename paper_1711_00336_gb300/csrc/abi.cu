@@ -502,7 +502,8 @@ static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub) {
     if (pl) {
         launch_bsort_scatter(T, B->d_part, B->n_part, grid_of(B->n_part), u.part_block, B->stream);
         launch_bsort_rank(T, B->d_part, B->n_part, grid_of(B->n_part), u.part_block, B->stream);
-        launch_bsort_gather(T, B->d_part, B->n_part, xsel, grid_of(B->n_part), u.part_block, B->stream);
+        launch_bsort_gather(T, B->d_part, B->n_part, xsel, grid_of(B->n_part), part_threads(u, B->cpl_lanes),
+                            B->stream);
     }
     launch_bsort_flip(B->d_table, nb, mark_usub, B->stream);
     int nlists = 0;

@@ -18,13 +18,15 @@ namespace dps {
 static constexpr double PI_D = 3.14159265358979323846;
 
 // ---- Eq. filter_def, one axis ---------------------------------------------
+// both branches take sqrt(1 - 3 s^2), s = r or 1 - r: one square root per
+// call whichever branch a lane is in (no divergent FP64 chains in a warp)
 __device__ __forceinline__ double roma_phi(double r) {
     r = fabs(r);
-    if (r < 0.5) return (1.0 + sqrt(1.0 - 3.0 * r * r)) * (1.0 / 3.0);
-    if (r < 1.5) {
-        double s = 1.0 - r;
-        return (5.0 - 3.0 * r - sqrt(1.0 - 3.0 * s * s)) * (1.0 / 6.0);
-    }
+    const bool inner = r < 0.5;
+    const double s = inner ? r : 1.0 - r;
+    const double q = sqrt(1.0 - 3.0 * s * s);
+    if (inner) return (1.0 + q) * (1.0 / 3.0);
+    if (r < 1.5) return (5.0 - 3.0 * r - q) * (1.0 / 6.0);
     return 0.0;
 }
 
@@ -132,6 +134,17 @@ __global__ void k_sort_rank(const int *__restrict__ key, const int *__restrict__
     }
 }
 
+// Particle tiles carry the lanes per particle of the particle-side coupling
+// kernels in Tile::first (1, 2, 4 or 8): a box with few particles spreads
+// each over several lanes, so its latency-bound work runs on more warps.  The block size is a multiple of 32 and of the
+// lanes; the loop over a tile's particles has a trip count uniform over the block.
+#define DPS_PARTICLE_GROUPS(tl, lanes, lane, base, p, act)                                  \
+    const int lanes = (tl).first > 1 ? (tl).first : 1;                                     \
+    const int lane = (int)threadIdx.x % lanes, ngrp_ = (int)blockDim.x / lanes;            \
+    for (long long base = (tl).begin, p = (tl).begin + (int)threadIdx.x / lanes; base < (tl).end; \
+         base += ngrp_, p += ngrp_)                                                          \
+        if (const bool act = p < (tl).end; true)
+
 // ---- S1 on the box table ----------------------------------------------------
 // x/u/w of box B: planes 0..8 of the current set, or the DEM ping-pong planes
 __device__ __forceinline__ const double *xuw_of(const BoxDev &B, int xsel) {
@@ -193,48 +206,51 @@ __global__ void k_bsort_gather(const BoxDev *__restrict__ boxes, const Tile *__r
         const int *srci = B.pi[B.cur];
         double *dstf = B.pf[1 - B.cur];
         int *dsti = B.pi[1 - B.cur];
-        for (long long k = tl.begin + threadIdx.x; k < tl.end; k += blockDim.x) {
+        // the lanes of a particle share the plane copies and the three axes
+        // of kernel weights (lane a takes axis a: one instruction stream for
+        // the warp, no divergent per-axis branches); the last share (mass,
+        // ints, float copies) goes to lane 3 mod lanes
+        DPS_PARTICLE_GROUPS(tl, lanes, lane, base, k, act) {
+            if (!act) continue;
+            const int lm = lanes - 1;
             const long long i = B.perm[k];
-            double x[3];
+            for (int f0 = 0; f0 < PXS0; f0 += 4 * lanes) {
 #pragma unroll
-            for (int f = 0; f < 9; ++f) {
-                double v = xuw[f * cap + i];
-                dstf[f * cap + k] = v;
-                if (f < 3) x[f] = v;
+                for (int u = 0; u < 4; ++u) {
+                    const int f = f0 + u * lanes + lane;
+                    if (f < PXS0) dstf[f * cap + k] = (f < 9 ? xuw : srcf)[f * cap + i];
+                }
             }
-#pragma unroll
-            for (int f = 9; f < PXS0; ++f) dstf[f * cap + k] = srcf[f * cap + i];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                dstf[(PXS0 + a) * cap + k] = x[a];
+            for (int a = lane; a < 3; a += lanes) {
+                const double xa = xuw[a * cap + i];
+                const int La = a == 0 ? g.n[0] : (a == 1 ? g.n[1] : g.n[2]);
+                const int pa = a == 0 ? g.per[0] : (a == 1 ? g.per[1] : g.per[2]);
+                dstf[(PXS0 + a) * cap + k] = xa;
                 if (B.lowp) {
                     float w[3];
-                    axis_weights_f(x[a], g.n[a], g.per[a], w);
+                    axis_weights_f(xa, La, pa, w);
                     B.pwf[(3 * a + 0) * cap + k] = w[0];
                     B.pwf[(3 * a + 1) * cap + k] = w[1];
                     B.pwf[(3 * a + 2) * cap + k] = w[2];
                 } else {
                     double w[3];
-                    axis_weights(x[a], g.n[a], g.per[a], w);
+                    axis_weights(xa, La, pa, w);
                     dstf[(PW0 + 3 * a + 0) * cap + k] = w[0];
                     dstf[(PW0 + 3 * a + 1) * cap + k] = w[1];
                     dstf[(PW0 + 3 * a + 2) * cap + k] = w[2];
                 }
             }
-            {
-                // mass and the inverse factors of Eq. particle_motion (I = m d^2 / 10)
-                const double dd = srcf[PD * cap + i];
-                const double m = srcf[PRHO * cap + i] * PI_D / 6.0 * dd * dd * dd;
-                dstf[PM * cap + k] = m;
-                dstf[PIM * cap + k] = 1.0 / m;
-                dstf[PII * cap + k] = 10.0 / (m * dd * dd);
-            }
+            if ((3 & lm) != lane) continue;
+            // mass and the inverse factors of Eq. particle_motion (I = m d^2 / 10)
+            const double dd = srcf[PD * cap + i];
+            const double m = srcf[PRHO * cap + i] * PI_D / 6.0 * dd * dd * dd;
+            dstf[PM * cap + k] = m;
+            dstf[PIM * cap + k] = 1.0 / m;
+            dstf[PII * cap + k] = 10.0 / (m * dd * dd);
             dsti[IID * cap + k] = srci[IID * cap + i];
             dsti[ICELL * cap + k] = B.key[i];
             dsti[IKEY * cap + k] = B.key[i];
-            const double dd = srcf[PD * cap + i];
-            const double m = srcf[PRHO * cap + i] * PI_D / 6.0 * dd * dd * dd;
-            B.xf[0][k] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)dd);
+            B.xf[0][k] = make_float4((float)xuw[i], (float)xuw[cap + i], (float)xuw[2 * cap + i], (float)dd);
             B.vf[0][k] = make_float4((float)xuw[3 * cap + i], (float)xuw[4 * cap + i], (float)xuw[5 * cap + i], (float)m);
             B.of[0][k] = make_float4((float)xuw[6 * cap + i], (float)xuw[7 * cap + i], (float)xuw[8 * cap + i], 0.f);
         }
@@ -644,17 +660,6 @@ __device__ __forceinline__ void lanes_sum(FT (&v)[NV], int lanes) {
         for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
 }
 
-// Particle tiles carry the lanes per particle of the force kernels in
-// Tile::first (1, 2, 4 or 8; the support's 27 cells split over them): a box
-// with few particles spreads each over several lanes, so its latency-bound
-// gathers run on more warps.  The block size is a multiple of 32 and of the
-// lanes; the loop over a tile's particles has a trip count uniform over the block.
-#define DPS_PARTICLE_GROUPS(tl, lanes, lane, base, p, act)                                  \
-    const int lanes = (tl).first > 1 ? (tl).first : 1;                                     \
-    const int lane = (int)threadIdx.x % lanes, ngrp_ = (int)blockDim.x / lanes;            \
-    for (long long base = (tl).begin, p = (tl).begin + (int)threadIdx.x / lanes; base < (tl).end; \
-         base += ngrp_, p += ngrp_)                                                          \
-        if (const bool act = p < (tl).end; true)
 
 // K5a: added mass, F_am = C_am rho_f V (Du_f/Dt|p - du_p/dt) (Table 1);
 // du_p/dt is the change of u_p over the previous subcycle (taken in FP64).
