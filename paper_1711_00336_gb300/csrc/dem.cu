@@ -252,48 +252,65 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
     }
 }
 
-// the exact FP64 pair of partner j (Sec. 3.1.1 / 3.1.3): separation from the
-// FP64 positions, then partner<double>.  Out of line in the mixed forms,
-// where it runs for the rare pairs near contact only, so that its registers
-// do not limit the occupancy of the FP32 pair loop.
-template <bool INL>
+// the exact FP64 interaction with entry j (Sec. 3.1.1 / 3.1.3): a sphere
+// (j >= 0; separation from the FP64 positions) or a wall face
+// (j = -1 - (2 axis + side), side 1 the face at n[axis]; m_ij = m_i,
+// <d> = 2 d_i, partner at rest).  Both kinds run one contact / lubrication
+// body.  Out of line in the mixed forms, where it runs for the rare pairs
+// near contact only, so that its registers do not limit the occupancy of the
+// FP32 pair loop.
 __device__ __forceinline__ void pair64_body(const PairPar<double> &pd, const double *__restrict__ xin,
                                             const double *__restrict__ pf, long long cap, const Geom &g, long long j,
                                             const double xi[3], const double ui[3], const double wi[3], double di,
                                             double mi, double rng_extra, double F[3], double T[3], unsigned &nlim) {
-    double dx[3];
+    double n[3] = {0, 0, 0}, uj[3] = {0, 0, 0}, wjh[3] = {0, 0, 0};
+    double dist, sumr, dj = 0.0, mj = 1.0;
+    const bool wall = j < 0;
+    if (!wall) {
+        double dx[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) dx[a] = min_image(xin[a * cap + j] - xi[a], g.n[a], g.per[a]);
-    const double dist2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
-    const double dj = pf[PD * cap + j];
-    const double sumr = 0.5 * (di + dj);
-    if (!(dist2 > 0.0)) return;
-    const double inv = rsqrt(dist2);  // 1/|dx| and |dx| from one reciprocal square root
-    const double dist = dist2 * inv;
-    if (!(dist < sumr + rng_extra)) return;
-    const double mj = pf[PM * cap + j];
-    const double n[3] = {dx[0] * inv, dx[1] * inv, dx[2] * inv};
-    double uj[3];
+        for (int a = 0; a < 3; ++a) dx[a] = min_image(xin[a * cap + j] - xi[a], g.n[a], g.per[a]);
+        const double dist2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+        dj = pf[PD * cap + j];
+        sumr = 0.5 * (di + dj);
+        if (!(dist2 > 0.0)) return;
+        const double inv = rsqrt(dist2);  // 1/|dx| and |dx| from one reciprocal square root
+        dist = dist2 * inv;
+        if (!(dist < sumr + rng_extra)) return;
+        mj = pf[PM * cap + j];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) uj[a] = xin[(3 + a) * cap + j];
-    // m_ij = m_i m_j / (m_i + m_j) and <d> = 2 d_i d_j / (d_i + d_j): one
-    // division per pair (FP64 instructions bound this path on this GPU)
-    const double delta = sumr - dist;
-    if (pd.contact && delta > 0.0) {
-        double wjh[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
-        contact_force(pd, n, delta, ui, wi, di, uj, wjh, mi * mj / (mi + mj), F, T);
+        for (int a = 0; a < 3; ++a) {
+            n[a] = dx[a] * inv;
+            uj[a] = xin[(3 + a) * cap + j];
+            wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
+        }
+    } else {
+        const int face = -1 - (int)j, ax = face >> 1, side = face & 1;
+        const double xa = ax == 0 ? xi[0] : (ax == 1 ? xi[1] : xi[2]);
+        const int L = ax == 0 ? g.n[0] : (ax == 1 ? g.n[1] : g.n[2]);
+        dist = side == 0 ? xa : L - xa;
+        sumr = 0.5 * di;
+        if (!(dist < sumr + rng_extra)) return;
+        const double sg = side == 0 ? -1.0 : 1.0;
+        n[0] = ax == 0 ? sg : 0.0;
+        n[1] = ax == 1 ? sg : 0.0;
+        n[2] = ax == 2 ? sg : 0.0;
     }
+    // m_ij = A / Bm and <d> = C / D: spheres m_i m_j / (m_i + m_j) and
+    // 2 d_i d_j / (d_i + d_j), walls m_i and 2 d_i; one division per pair
+    // (FP64 instructions bound this path on this GPU)
+    const double A = wall ? mi : mi * mj, Bm = wall ? 1.0 : mi + mj;
+    const double C = wall ? 2.0 * di : 2.0 * di * dj, D = wall ? 1.0 : di + dj;
+    const double delta = sumr - dist;
+    if (pd.contact && delta > 0.0) contact_force(pd, n, delta, ui, wi, di, uj, wjh, A / Bm, F, T);
     const double h = dist - sumr;
     if (pd.lubrication && h >= 0.0 && h < pd.h_c) {
         const double hh = fmax(h, pd.h_min);
-        const double sm = mi + mj, sd = di + dj, dd2 = 2.0 * di * dj;
-        const double q = 1.0 / (sm * sd * hh * dd2);
-        const double dmean = dd2 * dd2 * sm * hh * q;  // dd2 / sd
-        const double r = dd2 * dd2 * sm * q;           // <d> / hh
-        const double ir = sm * sd * sd * hh * hh * q;  // hh / <d>
-        const double cap = mi * mj * sd * hh * dd2 * q * pd.capfac;  // m_ij capfac
+        const double q = 1.0 / (Bm * D * hh * C);
+        const double dmean = wall ? C : C * C * Bm * hh * q;  // C / D
+        const double r = C * C * Bm * q;                      // <d> / hh
+        const double ir = Bm * D * D * hh * hh * q;           // hh / <d>
+        const double cap = (wall ? A : A * D * hh * C * q) * pd.capfac;  // m_ij capfac
         lub_force(pd, n, dmean, r, ir, cap, ui, uj, F, nlim);
     }
 }
@@ -314,11 +331,13 @@ __device__ __noinline__ void pair64_out(const BoxDev &Bx, const double *__restri
     const double rng_extra = Bx.ph.lubrication ? fmax(Bx.ph.h_c, 0.0) : 0.0;
     const PairPar<double> pd = pair_par<double>(Bx.ph);
     const Geom g = Bx.g;
-    pair64_body<false>(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
+    pair64_body(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
 }
 
-// one thread per particle: wall partners, then Eq. particle_motion
-// (semi-implicit Euler) and the outputs of the substep
+// one thread per particle: wall partners (WALLS; the FP64 form evaluates
+// them with the sphere pairs), then Eq. particle_motion (semi-implicit Euler)
+// and the outputs of the substep
+template <bool WALLS>
 __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<double> &pd, long long i,
                                                int src_tmp, double F[3], double T[3], unsigned nlim) {
     const double *xin = src_tmp ? Bx.xtmp : Bx.pf[Bx.cur];
@@ -344,7 +363,7 @@ __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<
     const double zero[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (g.per[a]) continue;
+        if (!WALLS || g.per[a]) continue;
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const double dist = side == 0 ? xi[a] : g.n[a] - xi[a];
@@ -390,15 +409,17 @@ __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<
 
 // ---- the substep ------------------------------------------------------------------
 // src_tmp = 0: read x/u/w (and the float positions) from the current set,
-// write the ping-pong buffers; src_tmp = 1: the other way round
-// particles per chunk of a tile: phase A (pair sums by lane groups) leaves
-// each particle's force and torque in shared memory, phase B integrates one
-// particle per thread, so the FP64 tail keeps every lane of a warp busy
+// write the ping-pong buffers; src_tmp = 1: the other way round.  A tile is
+// taken in chunks of particles: phase A sums each particle's partner forces
+// and torques into shared memory, phase B integrates one particle per thread.
 constexpr int DEM_CHUNK = 256;
 
-template <bool MIXED, int LANES>
-__global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
-                                                     int ntiles, int src_tmp) {
+// Mixed forms: lane groups of LANES lanes per particle walk its list; pairs
+// away from contact run in FP32 from the float copies, the rare pairs near
+// contact in FP64 (out of line), walls in phase B.
+template <int LANES>
+__global__ void __launch_bounds__(256) k_dem_substep_mixed(const BoxDev *__restrict__ boxes,
+                                                           const Tile *__restrict__ tiles, int ntiles, int src_tmp) {
     __shared__ double sFT[6][DEM_CHUNK];
     __shared__ unsigned sN[DEM_CHUNK];
     const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
@@ -407,12 +428,9 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
         const BoxDev &Bx = boxes[tl.box];
         const double *xin = src_tmp ? Bx.xtmp : Bx.pf[Bx.cur];
         const float4 *fin = Bx.xf[src_tmp], *vin = Bx.vf[src_tmp], *oin = Bx.of[src_tmp];
-        const double *pf = Bx.pf[Bx.cur];
-        const long long cap = Bx.cap;
         const Geom g = Bx.g;
         const Phys &ph = Bx.ph;
-        const double rng_extra = ph.lubrication ? fmax(ph.h_c, 0.0) : 0.0;
-        const float rng_extra_f = (float)rng_extra;
+        const float rng_extra_f = (float)(ph.lubrication ? fmax(ph.h_c, 0.0) : 0.0);
         const float Lf[3] = {(float)g.n[0], (float)g.n[1], (float)g.n[2]};
         const PairPar<double> pd = pair_par<double>(ph);
         const PairPar<float> pfl = pair_par<float>(ph);
@@ -424,22 +442,10 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                 const long long i = base + grp;
                 const bool act = i < ce;
                 double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-                float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};  // FP32 pairs of the mixed forms
+                float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};
                 unsigned nlim = 0;
-                bool near = false;  // this lane evaluated an FP64 pair (mixed forms)
+                bool near = false;  // this lane evaluated an FP64 pair
                 if (act) {
-                    // FP64 state of i: in registers for the FP64 form only
-                    double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, wi[3] = {0, 0, 0}, di = 0, mi = 0;
-                    if (!MIXED) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            xi[a] = xin[a * cap + i];
-                            ui[a] = xin[(3 + a) * cap + i];
-                            wi[a] = xin[(6 + a) * cap + i];
-                        }
-                        di = pf[PD * cap + i];
-                        mi = pf[PM * cap + i];
-                    }
                     const float4 pi = fin[i], vi = vin[i], oi = oin[i];
                     const int nn = Bx.nlist_n[i];
                     const int *row = Bx.nlist + i * (long long)Bx.maxn;
@@ -453,36 +459,30 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                         const float fr = sumr_f + rng_extra_f + SCREEN_MARGIN;
                         const float d2f = fx * fx + fy * fy + fz * fz;
                         if (!(d2f < fr * fr)) continue;
-                        if (MIXED) {
-                            // away from contact: the whole pair in FP32 from the float copies
-                            const float distf = sqrtf(d2f);
-                            if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
-                                if (!(distf < sumr_f + rng_extra_f)) continue;
-                                const float4 vj = vin[j], oj = oin[j];
-                                const float inv = 1.0f / distf;
-                                const float n[3] = {fx * inv, fy * inv, fz * inv};
-                                const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
-                                const float uj[3] = {vj.x, vj.y, vj.z};
-                                const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
-                                const float m_ij = vi.w * vj.w / (vi.w + vj.w);
-                                const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
-                                partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf,
-                                               nlim);
-                                continue;
-                            }
+                        // away from contact: the whole pair in FP32 from the float copies
+                        const float distf = sqrtf(d2f);
+                        if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
+                            if (!(distf < sumr_f + rng_extra_f)) continue;
+                            const float4 vj = vin[j], oj = oin[j];
+                            const float inv = 1.0f / distf;
+                            const float n[3] = {fx * inv, fy * inv, fz * inv};
+                            const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
+                            const float uj[3] = {vj.x, vj.y, vj.z};
+                            const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
+                            const float m_ij = vi.w * vj.w / (vi.w + vj.w);
+                            const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
+                            partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf,
+                                           nlim);
+                            continue;
                         }
-                        // exact separation and forces in FP64
-                        if (MIXED) {
-                            near = true;
-                            pair64_out(Bx, xin, i, j, F, T, nlim);
-                        } else
-                            pair64_body<true>(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
+                        // near contact: exact separation and forces in FP64
+                        near = true;
+                        pair64_out(Bx, xin, i, j, F, T, nlim);
                     }
                 }
                 if (LANES > 1) {
-                    // FP64 sums: always in the FP64 form; in the mixed forms only
-                    // when some lane of the warp met a pair near contact
-                    const bool red64 = !MIXED || __any_sync(0xffffffffu, near);
+                    // FP64 sums only when some lane of the warp met a pair near contact
+                    const bool red64 = __any_sync(0xffffffffu, near);
 #pragma unroll
                     for (int o = LANES / 2; o > 0; o >>= 1) {
 #pragma unroll
@@ -491,10 +491,8 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
                                 F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
                                 T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
                             }
-                            if (MIXED) {
-                                Ff[a] += __shfl_xor_sync(0xffffffffu, Ff[a], o);
-                                Tf[a] += __shfl_xor_sync(0xffffffffu, Tf[a], o);
-                            }
+                            Ff[a] += __shfl_xor_sync(0xffffffffu, Ff[a], o);
+                            Tf[a] += __shfl_xor_sync(0xffffffffu, Tf[a], o);
                         }
                         nlim += __shfl_xor_sync(0xffffffffu, nlim, o);
                     }
@@ -514,7 +512,195 @@ __global__ void __launch_bounds__(256) k_dem_substep(const BoxDev *__restrict__ 
             for (long long i = cb + threadIdx.x; i < ce; i += blockDim.x) {
                 const int s = (int)(i - cb);
                 double F[3] = {sFT[0][s], sFT[1][s], sFT[2][s]}, T[3] = {sFT[3][s], sFT[4][s], sFT[5][s]};
-                finish_particle(Bx, pd, i, src_tmp, F, T, sN[s]);
+                finish_particle<true>(Bx, pd, i, src_tmp, F, T, sN[s]);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// block-wide exclusive sum of one int per thread (blockDim a multiple of 32,
+// at most 256); total over the block; ws: 9 ints of shared memory
+__device__ __forceinline__ int block_excl_sum(int v, int *ws, int &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int w = lane < nw ? ws[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        if (lane < nw) ws[lane] = wi - w;
+        if (lane == nw - 1) ws[8] = wi;
+    }
+    __syncthreads();
+    const int r = ws[wid] + inc - v;
+    total = ws[8];
+    __syncthreads();  // ws may be reused
+    return r;
+}
+
+// FP64 form: the pairs of a block are compacted into a queue before the FP64
+// work.  Only a fraction of a particle's list entries pass the screen (at
+// low solid fractions well under one per particle), and an FP64 instruction
+// costs a warp the same whatever number of its lanes are active, so the
+// screened entries of all the block's particles are gathered and evaluated
+// one per thread.  Lane groups of LANES lanes screen a particle's list (FP32,
+// with a margin); lane 0 of the group adds the wall faces within reach.  A
+// block-wide exclusive sum over the threads places the entries (a particle's
+// entries contiguous, in the order lane 0 .. LANES-1, list order inside a
+// lane, walls after lane 0's list entries); the queue is taken in windows of
+// DQ_CAP entries, each evaluated by all threads and then added by lane 0 of
+// each group to its particle's sums, entry by entry in queue order.  A
+// particle's sum therefore depends on its own list and LANES only.
+constexpr int DQ_CAP = 384;
+
+template <int LANES>
+__global__ void __launch_bounds__(256, 1) k_dem_substep64(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
+                                                       int ntiles, int src_tmp) {
+    __shared__ double sFT[6][DEM_CHUNK];
+    __shared__ unsigned sN[DEM_CHUNK];
+    __shared__ double qR[6][DQ_CAP];
+    __shared__ unsigned qN[DQ_CAP];
+    __shared__ int qJ[DQ_CAP], qP[DQ_CAP];
+    __shared__ int ws[9];
+    const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
+    const int wl = threadIdx.x & 31;
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &Bx = boxes[tl.box];
+        const double *xin = src_tmp ? Bx.xtmp : Bx.pf[Bx.cur];
+        const float4 *fin = Bx.xf[src_tmp];
+        const double *pf = Bx.pf[Bx.cur];
+        const long long cap = Bx.cap;
+        const Geom g = Bx.g;
+        const Phys &ph = Bx.ph;
+        const double rng_extra = ph.lubrication ? fmax(ph.h_c, 0.0) : 0.0;
+        const float rng_extra_f = (float)rng_extra;
+        const float Lf[3] = {(float)g.n[0], (float)g.n[1], (float)g.n[2]};
+        const PairPar<double> pd = pair_par<double>(ph);
+        for (long long cb = tl.begin; cb < tl.end; cb += DEM_CHUNK) {
+            const long long ce = cb + DEM_CHUNK < tl.end ? cb + DEM_CHUNK : tl.end;
+            for (long long base = cb; base < ce; base += ngrp) {  // uniform trip count
+                const long long i = base + grp;
+                const bool act = i < ce;
+                float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+                int nn = 0;
+                const int *row = Bx.nlist;
+                if (act) {
+                    pi = fin[i];
+                    nn = Bx.nlist_n[i];
+                    row = Bx.nlist + i * (long long)Bx.maxn;
+                }
+                // the entries of this lane that pass the FP32 screen, in order:
+                // fn(j) for list entries k = lane, lane + LANES, ..., then (lane
+                // 0) the wall faces within reach as j = -1 - (2 axis + side)
+                auto entries = [&](auto &&fn) {
+                    for (int k = lane; k < nn; k += LANES) {
+                        const int j = row[k];
+                        const float4 pj = fin[j];
+                        const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
+                        const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
+                        const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
+                        const float fr = 0.5f * (pi.w + pj.w) + rng_extra_f + SCREEN_MARGIN;
+                        if (fx * fx + fy * fy + fz * fz < fr * fr) fn(j);
+                    }
+                    if (lane == 0) {
+                        const float pa[3] = {pi.x, pi.y, pi.z};
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            if (g.per[a]) continue;
+#pragma unroll
+                            for (int side = 0; side < 2; ++side) {
+                                const float dw = side == 0 ? pa[a] : Lf[a] - pa[a];
+                                if (dw < 0.5f * pi.w + rng_extra_f + SCREEN_MARGIN) fn(-1 - (2 * a + side));
+                            }
+                        }
+                    }
+                };
+                int cnt = 0;
+                if (act) entries([&](int) { ++cnt; });
+                int M;
+                const int off = block_excl_sum(cnt, ws, M);
+                // the particle's entries: [gs, ge) of the queue
+                const int g0 = wl - lane;
+                const int gs = __shfl_sync(0xffffffffu, off, g0);
+                const int ge = __shfl_sync(0xffffffffu, off + cnt, g0 + LANES - 1);
+                double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+                unsigned nlim = 0;
+                for (int w0 = 0; w0 < M; w0 += DQ_CAP) {
+                    const int mw = M - w0 < DQ_CAP ? M - w0 : DQ_CAP;
+                    if (act && off < w0 + mw && off + cnt > w0) {
+                        int c = off;
+                        entries([&](int j) {
+                            if (c >= w0 && c < w0 + mw) {
+                                qJ[c - w0] = j;
+                                qP[c - w0] = (int)(i - cb);
+                            }
+                            ++c;
+                        });
+                    }
+                    __syncthreads();
+                    // one entry per thread: the FP64 contact / lubrication body
+                    for (int q = threadIdx.x; q < mw; q += blockDim.x) {
+                        const long long ii = cb + qP[q];
+                        double xi[3], ui[3], wi[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            xi[a] = xin[a * cap + ii];
+                            ui[a] = xin[(3 + a) * cap + ii];
+                            wi[a] = xin[(6 + a) * cap + ii];
+                        }
+                        double Fq[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
+                        unsigned nq = 0;
+                        pair64_body(pd, xin, pf, cap, g, qJ[q], xi, ui, wi, pf[PD * cap + ii], pf[PM * cap + ii],
+                                    rng_extra, Fq, Tq, nq);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            qR[a][q] = Fq[a];
+                            qR[3 + a][q] = Tq[a];
+                        }
+                        qN[q] = nq;
+                    }
+                    __syncthreads();
+                    if (act && lane == 0) {
+                        const int a0 = gs > w0 ? gs : w0, a1 = ge < w0 + mw ? ge : w0 + mw;
+                        for (int q = a0; q < a1; ++q) {
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                F[a] += qR[a][q - w0];
+                                T[a] += qR[3 + a][q - w0];
+                            }
+                            nlim += qN[q - w0];
+                        }
+                    }
+                    __syncthreads();  // the next window overwrites the queue
+                }
+                if (act && lane == 0) {
+                    const int s = (int)(i - cb);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        sFT[a][s] = F[a];
+                        sFT[3 + a][s] = T[a];
+                    }
+                    sN[s] = nlim;
+                }
+            }
+            __syncthreads();
+            // phase B: integration, one particle per thread (walls were entries)
+            for (long long i = cb + threadIdx.x; i < ce; i += blockDim.x) {
+                const int s = (int)(i - cb);
+                double F[3] = {sFT[0][s], sFT[1][s], sFT[2][s]}, T[3] = {sFT[3][s], sFT[4][s], sFT[5][s]};
+                finish_particle<false>(Bx, pd, i, src_tmp, F, T, sN[s]);
             }
             __syncthreads();
         }
@@ -532,17 +718,17 @@ void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int 
 // lanes: 1, 2, 4 or 8 lanes per particle (block a multiple of 32)
 void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int src_tmp, int mixed, int lanes,
                         int grid, int block, cudaStream_t s) {
-#define DPS_DEM(M, L) k_dem_substep<M, L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp)
+#define DPS_DEM(K, L) K<L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp)
     if (mixed) {
-        if (lanes >= 8) DPS_DEM(true, 8);
-        else if (lanes == 4) DPS_DEM(true, 4);
-        else if (lanes == 2) DPS_DEM(true, 2);
-        else DPS_DEM(true, 1);
+        if (lanes >= 8) DPS_DEM(k_dem_substep_mixed, 8);
+        else if (lanes == 4) DPS_DEM(k_dem_substep_mixed, 4);
+        else if (lanes == 2) DPS_DEM(k_dem_substep_mixed, 2);
+        else DPS_DEM(k_dem_substep_mixed, 1);
     } else {
-        if (lanes >= 8) DPS_DEM(false, 8);
-        else if (lanes == 4) DPS_DEM(false, 4);
-        else if (lanes == 2) DPS_DEM(false, 2);
-        else DPS_DEM(false, 1);
+        if (lanes >= 8) DPS_DEM(k_dem_substep64, 8);
+        else if (lanes == 4) DPS_DEM(k_dem_substep64, 4);
+        else if (lanes == 2) DPS_DEM(k_dem_substep64, 2);
+        else DPS_DEM(k_dem_substep64, 1);
     }
 #undef DPS_DEM
 }
