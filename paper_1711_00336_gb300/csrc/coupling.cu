@@ -247,6 +247,7 @@ __global__ void k_bsort_gather(const BoxDev *__restrict__ boxes, const Tile *__r
             dstf[PM * cap + k] = m;
             dstf[PIM * cap + k] = 1.0 / m;
             dstf[PII * cap + k] = 10.0 / (m * dd * dd);
+            dstf[PVOL * cap + k] = double(PI_D / 6.0) * dd * dd * dd;
             dsti[IID * cap + k] = srci[IID * cap + i];
             dsti[ICELL * cap + k] = B.key[i];
             dsti[IKEY * cap + k] = B.key[i];
@@ -572,8 +573,12 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_eps_gather(const BoxDev *__re
         brick_gather<St>(
             g, L, ox, oy, oz, ex, ey, ez, w, cap,
             [&](St &st, int p, FT W) {
-                const FT d = sizeof(FT) == 8 ? (FT)pf[PD * cap + p] : (FT)xf[p].w;
-                st.ep += W * (FT(PI_D / 6.0) * d * d * d);
+                if (sizeof(FT) == 8) {
+                    st.ep += W * (FT)pf[PVOL * cap + p];  // the volume stored at the sort
+                } else {
+                    const FT d = (FT)xf[p].w;
+                    st.ep += W * (FT(PI_D / 6.0) * d * d * d);
+                }
             },
             [&](St &st, long long c) {
                 FT e = FT(1) - st.ep;

@@ -158,9 +158,12 @@ __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T di
 // of the (2R+1)^2 rows around it, counts its partners, takes its offset from
 // an exclusive sum over the lanes, then scans again and writes them, so the
 // list is in lane-major row order whatever the launch shape.
+constexpr int NL_CACHE = 8;  // partners per lane kept between the two passes
+
 template <int LANES>
 __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
                                                      int ntiles) {
+    __shared__ int nl_cache[256][NL_CACHE];
     const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
@@ -196,37 +199,63 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
                 }
             }
             const int ny = hi[1] - lo[1] + 1, nrows = act ? ny * (hi[2] - lo[2] + 1) : 0;
-            // partners of particle i in cell row r, in the order of the sorted particles
-            auto scan_row = [&](int r, auto &&fn) {
-                const int yy = lo[1] + r % ny, zz = lo[2] + r / ny;
-                const int z = zz < 0 ? zz + g.n[2] : (zz >= g.n[2] ? zz - g.n[2] : zz);
-                const int y = yy < 0 ? yy + g.n[1] : (yy >= g.n[1] ? yy - g.n[1] : yy);
-                const long long row = cell_index(g, 0, y, z);
-                int xs0[2], xs1[2], nseg;
-                if (lo[0] >= 0 && hi[0] <= g.n[0] - 1) {
-                    xs0[0] = lo[0]; xs1[0] = hi[0]; nseg = 1;
-                } else if (lo[0] < 0) {
-                    xs0[0] = 0; xs1[0] = hi[0];
-                    xs0[1] = lo[0] + g.n[0]; xs1[1] = g.n[0] - 1; nseg = 2;
-                } else {
-                    xs0[0] = lo[0]; xs1[0] = g.n[0] - 1;
-                    xs0[1] = 0; xs1[1] = hi[0] - g.n[0]; nseg = 2;
-                }
-                for (int sgi = 0; sgi < nseg; ++sgi) {
-                    const int s0 = Bx.cell_start[row + xs0[sgi]], e0 = Bx.cell_start[row + xs1[sgi] + 1];
-                    for (int j = s0; j < e0; ++j) {
-                        if (j == i) continue;
-                        const float4 pj = xf[j];
-                        const float dx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
-                        const float dy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
-                        const float dz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
-                        const float rr = 0.5f * (pi.w + pj.w) + extra;
-                        if (dx * dx + dy * dy + dz * dz < rr * rr) fn(j);
+            // the x segments of a cell row (two where the row wraps periodically)
+            int xs0[2] = {lo[0], 0}, xs1[2] = {hi[0], -1};
+            if (lo[0] < 0) {
+                xs0[0] = 0;
+                xs1[0] = hi[0];
+                xs0[1] = lo[0] + g.n[0];
+                xs1[1] = g.n[0] - 1;
+            } else if (hi[0] > g.n[0] - 1) {
+                xs1[0] = g.n[0] - 1;
+                xs0[1] = 0;
+                xs1[1] = hi[0] - g.n[0];
+            }
+            // partners of particle i in this lane's rows r = lane, lane +
+            // LANES, ..., in row order, then the sorted order inside a row; the
+            // particle ranges of RB rows are loaded together before any is
+            // scanned, so their loads are in flight at once
+            constexpr int RB = 8;
+            auto scan_rows = [&](auto &&fn) {
+                for (int r0 = lane; r0 < nrows; r0 += RB * LANES) {
+                    int s[2 * RB], e[2 * RB];
+#pragma unroll
+                    for (int u = 0; u < RB; ++u) {
+                        const int r = r0 + u * LANES;
+                        s[2 * u] = e[2 * u] = s[2 * u + 1] = e[2 * u + 1] = 0;
+                        if (r >= nrows) continue;
+                        const int yy = lo[1] + r % ny, zz = lo[2] + r / ny;
+                        const int z = zz < 0 ? zz + g.n[2] : (zz >= g.n[2] ? zz - g.n[2] : zz);
+                        const int y = yy < 0 ? yy + g.n[1] : (yy >= g.n[1] ? yy - g.n[1] : yy);
+                        const long long row = cell_index(g, 0, y, z);
+#pragma unroll
+                        for (int sg = 0; sg < 2; ++sg)
+                            if (xs1[sg] >= xs0[sg]) {
+                                s[2 * u + sg] = Bx.cell_start[row + xs0[sg]];
+                                e[2 * u + sg] = Bx.cell_start[row + xs1[sg] + 1];
+                            }
                     }
+#pragma unroll
+                    for (int v = 0; v < 2 * RB; ++v)
+                        for (int j = s[v]; j < e[v]; ++j) {
+                            if (j == i) continue;
+                            const float4 pj = xf[j];
+                            const float dx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
+                            const float dy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
+                            const float dz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
+                            const float rr = 0.5f * (pi.w + pj.w) + extra;
+                            if (dx * dx + dy * dy + dz * dz < rr * rr) fn(j);
+                        }
                 }
             };
+            // pass 1 counts and keeps the first NL_CACHE partners of the lane in
+            // shared memory; pass 2 writes them (scanning again only past that)
             int cnt = 0;
-            for (int r = lane; r < nrows; r += LANES) scan_row(r, [&](int) { ++cnt; });
+            int *cache = nl_cache[threadIdx.x];
+            scan_rows([&](int j) {
+                if (cnt < NL_CACHE) cache[cnt] = j;
+                ++cnt;
+            });
             // exclusive sum of the counts over the lanes of the group
             int off = cnt;
 #pragma unroll
@@ -238,12 +267,16 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
             off -= cnt;
             if (!act) continue;
             int *lst = Bx.nlist + i * (long long)maxn;
-            int w = off;
-            for (int r = lane; r < nrows; r += LANES)
-                scan_row(r, [&](int j) {
+            if (cnt <= NL_CACHE) {
+                for (int c = 0; c < cnt; ++c)
+                    if (off + c < maxn) lst[off + c] = cache[c];
+            } else {
+                int w = off;
+                scan_rows([&](int j) {
                     if (w < maxn) lst[w] = j;
                     ++w;
                 });
+            }
             if (lane == 0) {
                 Bx.nlist_n[i] = min(total, maxn);
                 if (total > maxn) atomicOr(Bx.status, ST_NLIST);

@@ -67,6 +67,7 @@ enum : int {
     POX, POY, POZ,           // angular velocity
     PD, PRHO,                // diameter, density
     PM, PIM, PII,            // mass m, 1/m and 10/(m d^2) (set at every sort)
+    PVOL,                    // volume pi d^3 / 6 (set at every sort)
     PUS0, PUS1, PUS2,        // u at the start of the previous subcycle
     PFH0, PFH1, PFH2,        // frozen F_fp + F_g of the subcycle
     PFA0, PFA1, PFA2,        // added-mass force of the subcycle
