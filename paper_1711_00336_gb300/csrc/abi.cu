@@ -48,13 +48,13 @@ void launch_eps(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
 void launch_force_am(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
-void launch_force_drag(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+void launch_force_drag(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 template <typename FT>
 void launch_reaction_am(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
 void launch_reaction_drag(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
-void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, int, int, cudaStream_t);
-void launch_build_nlist(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
+void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, int, int, int, cudaStream_t);
+void launch_build_nlist(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 long long scan_scratch_words(long long);
 void exclusive_scan(const int *, long long, int *, int *, cudaStream_t);
 template <typename ST>
@@ -74,6 +74,8 @@ void launch_fluid_sums(const void *, const void *, const void *, const Geom &, c
 void launch_particle_sums(const double *, const double *, long long, long long, double *, double *, cudaStream_t);
 void launch_particles_export(const double *, int, long long, long long, const int *, double *, cudaStream_t);
 void launch_particles_import(double *, int, long long, long long, const int *, const double *, cudaStream_t);
+void launch_particles_export4(const BoxDev *, int, const double *, const int *, long long, long long, double *,
+                              cudaStream_t);
 long long reduce_partials_doubles();
 }  // namespace dps
 
@@ -116,6 +118,12 @@ struct Batch {
     // substeps (fork and join by events, captured into the step graph)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // read-back staging: device buffer and pinned host buffer for particle
+    // exports, pinned status words (one copy and one synchronisation per call)
+    double *d_pstage = nullptr, *h_pstage = nullptr;
+    size_t cap_dpstage = 0, cap_hpstage = 0;
+    int *h_status = nullptr;
+    size_t cap_status = 0;
     dps_alloc_fn alloc = nullptr;
     dps_free_fn free = nullptr;
     void *ctx = nullptr;
@@ -448,12 +456,16 @@ static int push_layout(Batch *B) {
 
 static int grid_of(int ntiles) { return std::max(1, std::min(ntiles, 152 * 8)); }
 
-// threads per block of a particle kernel with `lanes` lanes per particle: the
-// whole tile's lane groups when that fits in 256 threads, a multiple of 32
-// (the lane-group shuffles take all 32 lanes of a warp)
+// threads per block of a particle kernel with `lanes` lanes per particle:
+// the tuned block, or all lane groups of a tile when they fit in 256 threads
+// (the small tiles of boxes with few particles); a multiple of 32, since the
+// lane-group shuffles take all 32 lanes of a warp.  Large tiles keep the tuned
+// block: these kernels hold 100-200 registers a thread, and 256-thread blocks
+// would leave one block per SM.
 static int part_threads(const Tuning &u, int lanes) {
-    const long long want = std::max<long long>(u.part_block, (long long)u.part_tile * lanes);
-    return (int)std::min<long long>(256, (want + 31) / 32 * 32);
+    const long long want = (long long)u.part_tile * lanes;
+    const long long b = lanes > 1 && want > u.part_block && want <= 256 ? want : u.part_block;
+    return (int)((b + 31) / 32 * 32);
 }
 
 // ---- the coupled step --------------------------------------------------------------
@@ -491,13 +503,15 @@ static int enqueue_collide(Batch *B, int par, bool mom_in) {
     return nl;
 }
 
-static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub) {
+// have_keys: the last DEM substep already wrote the linked cells and counts
+static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub, bool have_keys) {
     const BoxDev *T = B->d_table;
     const int nb = (int)B->boxes.size();
     const Tuning &u = B->tune;
     const int pl = B->n_part > 0;
+    const int cnt = pl && !have_keys;
     tbegin(B);
-    if (pl) launch_bsort_count(T, B->d_part, B->n_part, xsel, grid_of(B->n_part), u.part_block, B->stream);
+    if (cnt) launch_bsort_count(T, B->d_part, B->n_part, xsel, grid_of(B->n_part), u.part_block, B->stream);
     launch_bscan(T, nb, B->d_scan, B->n_scan, B->stream);
     if (pl) {
         launch_bsort_scatter(T, B->d_part, B->n_part, grid_of(B->n_part), u.part_block, B->stream);
@@ -506,16 +520,9 @@ static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub) {
                             B->stream);
     }
     launch_bsort_flip(B->d_table, nb, mark_usub, B->stream);
-    int nlists = 0;
     if (pl)
-        for (int c = 0; c < 4; ++c) {  // lanes per particle as in the DEM substep
-            const int nt = B->part_off[c + 1] - B->part_off[c];
-            if (nt <= 0) continue;
-            const int blk = part_threads(u, 1 << c);
-            launch_build_nlist(T, B->d_part + B->part_off[c], nt, 1 << c, grid_of(nt), blk, B->stream);
-            ++nlists;
-        }
-    tend(B, PH_SORT, 3 + 4 * pl + 1 + nlists);
+        launch_build_nlist(T, B->d_part, B->n_part, grid_of(B->n_part), part_threads(u, B->cpl_lanes), B->stream);
+    tend(B, PH_SORT, cnt + 3 + 3 * pl + 1 + pl);
     tbegin(B);
     if (B->fel == 8)
         launch_eps<double>(T, B->d_brick, B->n_brick, grid_of(B->n_brick), 256, B->stream);
@@ -562,8 +569,8 @@ static void enqueue_step(Batch *B) {
         tend(B, PH_RAM, 1);
         tbegin(B);
         if (pl) {
-            if (f64) launch_force_drag<double>(T, B->d_part, B->n_part, gp, part_threads(u, B->cpl_lanes), s);
-            else launch_force_drag<float>(T, B->d_part, B->n_part, gp, part_threads(u, B->cpl_lanes), s);
+            if (f64) launch_force_drag<double>(T, B->d_part, B->n_part, k == 0, gp, part_threads(u, B->cpl_lanes), s);
+            else launch_force_drag<float>(T, B->d_part, B->n_part, k == 0, gp, part_threads(u, B->cpl_lanes), s);
         }
         tend(B, PH_FDRAG, pl);
         // the drag reaction (cell fields from the frozen particle forces and
@@ -591,15 +598,22 @@ static void enqueue_step(Batch *B) {
                 for (int c = 0; c < 4; ++c) {
                     const int nt = B->part_off[c + 1] - B->part_off[c];
                     if (nt <= 0) continue;
-                    // a block holds all lane groups of a particle tile (at most 256 threads)
-                    const int blk = part_threads(u, 1 << c);
-                    launch_dem_substep(T, B->d_part + B->part_off[c], nt, sd & 1, B->prec != DPS_F64, 1 << c,
-                                       grid_of(nt), blk, s);
+                    // mixed forms: a block holds all lane groups of a particle tile,
+                    // at most 256 threads (two such blocks fit an SM); FP64 form:
+                    // the particle-kernel rule (its 200 registers a thread allow
+                    // one 256-thread block per SM)
+                    const int blk = B->prec != DPS_F64
+                                        ? (int)std::min<long long>(256, (std::max<long long>(u.part_block,
+                                                                                             (long long)u.part_tile << c) +
+                                                                         31) / 32 * 32)
+                                        : part_threads(u, 1 << c);
+                    launch_dem_substep(T, B->d_part + B->part_off[c], nt, sd & 1, sd == B->n_dem - 1,
+                                       B->prec != DPS_F64, 1 << c, grid_of(nt), blk, s);
                     ++ndl;
                 }
         tend(B, PH_DEM, ndl);
         if (fork) cudaStreamWaitEvent(s, B->ev_join, 0);
-        enqueue_sort_eps(B, B->n_dem & 1, 1);
+        enqueue_sort_eps(B, B->n_dem & 1, 1, B->n_dem > 0);
     }
     tbegin(B);
     const int nk1 = enqueue_collide(B, par, true);
@@ -609,12 +623,23 @@ static void enqueue_step(Batch *B) {
 }
 
 static int check_boxes(Batch *B) {
-    CKB(B, cudaStreamSynchronize(B->stream));
     std::string m;
     int bad = 0;
-    for (BoxHost *h : B->boxes) {
-        int st = 0;
-        CKB(B, cudaMemcpy(&st, h->d.status, sizeof(int), cudaMemcpyDeviceToHost));
+    const size_t nb = B->boxes.size();
+    if (nb > B->cap_status) {
+        if (B->h_status) cudaFreeHost(B->h_status);
+        B->h_status = nullptr;
+        B->cap_status = 0;
+        CKB(B, cudaMallocHost((void **)&B->h_status, sizeof(int) * std::max<size_t>(nb, 16)));
+        B->cap_status = std::max<size_t>(nb, 16);
+    }
+    for (size_t k = 0; k < nb; ++k)
+        CKB(B, cudaMemcpyAsync(B->h_status + k, B->boxes[k]->d.status, sizeof(int), cudaMemcpyDeviceToHost,
+                               B->stream));
+    CKB(B, cudaStreamSynchronize(B->stream));
+    for (size_t k = 0; k < nb; ++k) {
+        BoxHost *h = B->boxes[k];
+        const int st = B->h_status[k];
         if (st) {
             CKB(B, cudaMemset(h->d.status, 0, sizeof(int)));
             h->sticky |= st;
@@ -688,7 +713,7 @@ static int ready(Batch *B) {
         B->ev_used = 0;
         bool t = B->timing;
         B->timing = false;
-        enqueue_sort_eps(B, 0, 0);
+        enqueue_sort_eps(B, 0, 0, false);
         B->timing = t;
         for (BoxHost *h : B->boxes) h->prepared = true;
         int rc = check_boxes(B);
@@ -772,6 +797,13 @@ static void batch_release(Batch *B) {
     B->allocs.clear();
     for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
     B->ev.clear();
+    if (B->h_pstage) cudaFreeHost(B->h_pstage);
+    if (B->h_status) cudaFreeHost(B->h_status);
+    B->h_pstage = nullptr;
+    B->h_status = nullptr;
+    B->cap_hpstage = B->cap_status = 0;
+    B->d_pstage = nullptr;  // in B->allocs, freed above
+    B->cap_dpstage = 0;
     if (B->side) {
         cudaStreamSynchronize(B->side);
         cudaStreamDestroy(B->side);
@@ -788,7 +820,7 @@ static void batch_release(Batch *B) {
 static size_t box_bytes(int prec, long long ncell, long long cap) {
     size_t pe = prec == DPS_F64 ? 8 : (prec == DPS_F32 ? 4 : 2), fe = prec == DPS_F64 ? 8 : 4;
     size_t N = (size_t)ncell, C = (size_t)(cap > 0 ? cap : 1);
-    size_t b = 19 * N * pe + 26 * N * fe;
+    size_t b = 19 * N * pe + 27 * N * fe;
     b += 2 * (size_t)NPF * C * 8 + 2 * (size_t)NPI * C * 4 + 9 * C * 8 + 6 * C * 16 + C * 4 + 64 * C * 4 + 15 * C * 4;
     b += (3 * N + 1) * 4 + 3 * C * 4 + ((N + 8191) / 8192 + 1) * 4;
     b += 4096 + (size_t)reduce_partials_doubles() * 8;
@@ -829,6 +861,7 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
     d.pdf = A(19 * N * B->pdf_elem);
     d.eps = A(N * B->fel);
     d.rho = A(N * B->fel);
+    d.ire = A(N * B->fel);
     void **vec[] = {&d.fpf, &d.fam, &d.acc, &d.j, &d.uD, &d.uprev, &d.gradP, &d.DuDt};
     for (void **v : vec) *v = A(3 * N * B->fel);
     d.curl = d.uD;
@@ -878,6 +911,7 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
         launch_fill<float>(d.eps, ncell, 1.0, s);
     for (void *p : {d.fpf, d.fam, d.acc, d.j, d.uD, d.uprev, d.gradP, d.DuDt}) cudaMemsetAsync(p, 0, 3 * N * B->fel, s);
     cudaMemsetAsync(d.rho, 0, N * B->fel, s);
+    cudaMemsetAsync(d.ire, 0, N * B->fel, s);
     cudaMemsetAsync(d.nlist_n, 0, cap * 4, s);
     for (int k = 0; k < 2; ++k) {
         cudaMemsetAsync(d.xf[k], 0, cap * 16, s);
@@ -1016,21 +1050,42 @@ static int box_read_particles(Batch *B, BoxHost *h, double *x3, double *u3, doub
     const long long np = h->d.np;
     if (cap < np) FAILB(B, DPS_ERR_ARG, "capacity %lld < %lld particles", cap, np);
     if (np == 0) return DPS_OK;
-    int rc = pull_state(B);
-    if (rc) return rc;
-    double *buf = nullptr;
-    CKB(B, cudaMallocAsync((void **)&buf, 8 * 3 * np, B->stream));
-    double *dst[4] = {x3, u3, w3, F3};
-    const int plane[4] = {PX, PU, POX, PFH0};
-    const double *pf = h->d.pf[h->d.cur];
-    const int *ids = h->d.pi[h->d.cur] + IID * h->d.cap;
-    for (int k = 0; k < 4; ++k) {
-        if (!dst[k]) continue;
-        launch_particles_export(pf, plane[k], h->d.cap, np, ids, buf, B->stream);
-        CKB(B, cudaMemcpyAsync(dst[k], buf, 8 * 3 * np, cudaMemcpyDeviceToHost, B->stream));
+    // the box's device-table entry holds its current particle set; for a box
+    // not (yet) in the table the host copy is current once pulled
+    int k = -1;
+    for (size_t q = 0; q < B->dev_order.size(); ++q)
+        if (B->dev_order[q] == h) k = (int)q;
+    if (k < 0) {
+        int rc = pull_state(B);
+        if (rc) return rc;
     }
-    CKB(B, cudaFreeAsync(buf, B->stream));
+    const size_t n = 12 * (size_t)np;
+    if (n > B->cap_dpstage) {
+        void *p = dalloc_raw(B, n * 8);
+        if (!p) FAILB(B, DPS_ERR_OOM, "read-back buffer allocation failed");
+        if (B->d_pstage) {
+            CKB(B, cudaStreamSynchronize(B->stream));
+            dfree_raw(B, B->d_pstage);
+            B->allocs.erase(std::remove(B->allocs.begin(), B->allocs.end(), (void *)B->d_pstage), B->allocs.end());
+        }
+        B->allocs.push_back(p);
+        B->d_pstage = (double *)p;
+        B->cap_dpstage = n;
+    }
+    if (n > B->cap_hpstage) {
+        if (B->h_pstage) cudaFreeHost(B->h_pstage);
+        B->h_pstage = nullptr;
+        B->cap_hpstage = 0;
+        CKB(B, cudaMallocHost((void **)&B->h_pstage, n * 8));
+        B->cap_hpstage = n;
+    }
+    launch_particles_export4(k >= 0 ? B->d_table : nullptr, k, h->d.pf[h->d.cur], h->d.pi[h->d.cur] + IID * h->d.cap,
+                             h->d.cap, np, B->d_pstage, B->stream);
+    CKB(B, cudaMemcpyAsync(B->h_pstage, B->d_pstage, n * 8, cudaMemcpyDeviceToHost, B->stream));
     CKB(B, cudaStreamSynchronize(B->stream));
+    double *dst[4] = {x3, u3, w3, F3};
+    for (int q = 0; q < 4; ++q)
+        if (dst[q]) std::memcpy(dst[q], B->h_pstage + (size_t)q * 3 * np, 8 * 3 * (size_t)np);
     return DPS_OK;
 }
 

@@ -20,6 +20,7 @@ struct BoxDev {
     // fluid
     void *pdf;
     void *eps, *fpf, *fam, *acc, *rho, *j, *uD, *uprev, *gradP, *DuDt;
+    void *ire;         // 1/(rho eps_f) of the moments pass (eps_f of the step start)
     void *curl;        // curl of u_f for the lift force: the u_D planes, free after K2b
     // particles: two SoA sets and the DEM ping-pong planes
     double *pf[2];

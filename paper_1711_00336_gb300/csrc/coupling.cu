@@ -89,14 +89,6 @@ __device__ __forceinline__ void axis_weights_f(double x, int L, int periodic, fl
     }
 }
 
-__device__ __forceinline__ long long particle_cell(const Geom &g, double x, double y, double z, int *st) {
-    int ix = containing_cell(x, g.n[0]), iy = containing_cell(y, g.n[1]), iz = containing_cell(z, g.n[2]);
-    if (st && ((!g.per[0] && (x < 0.0 || x >= g.n[0])) || (!g.per[1] && (y < 0.0 || y >= g.n[1])) ||
-               (!g.per[2] && (z < 0.0 || z >= g.n[2]))))
-        atomicOr(st, ST_BAD_CELL);
-    return cell_index(g, ix, iy, iz);
-}
-
 // ---- S1: sort ----------------------------------------------------------------
 // key = containing cell of x (current position arrays given separately)
 __global__ void k_sort_count(const double *__restrict__ px, const double *__restrict__ py,
@@ -214,13 +206,10 @@ __global__ void k_bsort_gather(const BoxDev *__restrict__ boxes, const Tile *__r
             if (!act) continue;
             const int lm = lanes - 1;
             const long long i = B.perm[k];
-            for (int f0 = 0; f0 < PXS0; f0 += 4 * lanes) {
+            // all plane copies issued back to back (predicated per lane)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int f = f0 + u * lanes + lane;
-                    if (f < PXS0) dstf[f * cap + k] = (f < 9 ? xuw : srcf)[f * cap + i];
-                }
-            }
+            for (int f = 0; f < PXS0; ++f)
+                if ((f & lm) == lane) dstf[f * cap + k] = f < 9 ? xuw[f * cap + i] : srcf[f * cap + i];
             for (int a = lane; a < 3; a += lanes) {
                 const double xa = xuw[a * cap + i];
                 const int La = a == 0 ? g.n[0] : (a == 1 ? g.n[1] : g.n[2]);
@@ -414,7 +403,10 @@ __device__ __forceinline__ void for_brick_cells(const Geom &g, int ox, int oy, i
 // every neighbour cell).  The per-cell visit order is the one of
 // gather27_staged: ascending h is ascending (o_z, o_y, o_x) for a fixed cell.
 constexpr int BRICK_THREADS = 256;  // block size of every brick kernel
-constexpr int BL_MAX = 3072;        // entries; above it the block takes gather27_staged
+// entries; above it (about 0.13 particles per halo cell) the block takes the
+// per-cell walk of gather27_staged, faster once most probes find particles
+// (measured: the list wins at 0.02 particles per cell, the walk at 0.2)
+constexpr int BL_MAX = 128;
 constexpr int BL_PER_THREAD = (HALO3 + BRICK_THREADS - 1) / BRICK_THREADS;
 
 struct BrickList {
@@ -785,8 +777,12 @@ __device__ __forceinline__ float drag_cd(float Re, float e) {
 // K5b: pressure gradient, drag and gravity (Table 1, Sec. 3.1.2).  u_f at the
 // 27 cells is evaluated on the fly from rho, j and the force density of this
 // subcycle: u_f = (j + (eps f_b + f_pf,am)/2)/(rho eps).
+// first: the first subcycle of the step, whose eps_f is the one the moments
+// pass divided by: 1/(rho eps_f) is read from it instead of divided again
+// (the same rounded value)
 template <typename FT>
-__global__ void k_force_drag(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles) {
+__global__ void k_force_drag(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles, int ntiles,
+                             int first) {
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &Bx = boxes[tl.box];
@@ -795,7 +791,7 @@ __global__ void k_force_drag(const BoxDev *__restrict__ boxes, const Tile *__res
         const long long N = g.ncell, cap = Bx.cap;
         double *pf = Bx.pf[Bx.cur];
         const FT *rho = (const FT *)Bx.rho, *j = (const FT *)Bx.j, *eps = (const FT *)Bx.eps;
-        const FT *fam = (const FT *)Bx.fam, *gradP = (const FT *)Bx.gradP;
+        const FT *fam = (const FT *)Bx.fam, *gradP = (const FT *)Bx.gradP, *ire = (const FT *)Bx.ire;
         const FT fb[3] = {(FT)ph.fb[0], (FT)ph.fb[1], (FT)ph.fb[2]};
         DPS_PARTICLE_GROUPS(tl, lanes, lane, base, p, act) {
             // v: u_f (3), grad P (3), eps_f at the particle
@@ -804,7 +800,7 @@ __global__ void k_force_drag(const BoxDev *__restrict__ boxes, const Tile *__res
                 const Support<FT> S = support_of<FT>(Bx, pf, p);
                 for_support_lanes(g, S, lane, lanes, [&](long long c, FT W) {
                     const FT e = eps[c];
-                    const FT s = FT(1) / (rho[c] * e);
+                    const FT s = first ? ire[c] : FT(1) / (rho[c] * e);
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const FT F = e * fb[a] + fam[a * N + c];
@@ -999,8 +995,8 @@ void launch_force_am(const BoxDev *b, const Tile *t, int nt, int grid, int block
     k_force_am<FT><<<grid, block, 0, s>>>(b, t, nt);
 }
 template <typename FT>
-void launch_force_drag(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
-    k_force_drag<FT><<<grid, block, 0, s>>>(b, t, nt);
+void launch_force_drag(const BoxDev *b, const Tile *t, int nt, int first, int grid, int block, cudaStream_t s) {
+    k_force_drag<FT><<<grid, block, 0, s>>>(b, t, nt, first);
 }
 template <typename FT>
 void launch_reaction_am(const BoxDev *b, const Tile *t, int nt, int grid, int block, cudaStream_t s) {
@@ -1015,7 +1011,7 @@ void launch_reaction_drag(const BoxDev *b, const Tile *t, int nt, int first, int
 #define DPS_CPL_INST(FT)                                                                                  \
     template void launch_eps<FT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);              \
     template void launch_force_am<FT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);         \
-    template void launch_force_drag<FT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);       \
+    template void launch_force_drag<FT>(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);  \
     template void launch_reaction_am<FT>(const BoxDev *, const Tile *, int, int, int, cudaStream_t);      \
     template void launch_reaction_drag<FT>(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
 DPS_CPL_INST(double)

@@ -154,20 +154,23 @@ __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T di
 
 // list of particle i: partners j != i with |x_j - x_i| < (d_i+d_j)/2 + extra + skin
 // (screened in FP32 with a margin), stored row by row: nlist[i*maxn + k].
-// LANES lanes share a particle: lane l scans the cell rows l, l + LANES, ...
+// LANES lanes share a particle (the tile's lanes of the particle-side
+// kernels): lane l scans the cell rows l, l + LANES, ...
 // of the (2R+1)^2 rows around it, counts its partners, takes its offset from
 // an exclusive sum over the lanes, then scans again and writes them, so the
 // list is in lane-major row order whatever the launch shape.
 constexpr int NL_CACHE = 8;  // partners per lane kept between the two passes
 
-template <int LANES>
 __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
                                                      int ntiles) {
     __shared__ int nl_cache[256][NL_CACHE];
-    const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &Bx = boxes[tl.box];
+        // lanes per particle of the tile (1 for large boxes, whose lists then
+        // run in plain row order; more for boxes with few particles)
+        const int LANES = tl.first > 1 ? tl.first : 1;
+        const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
         const Geom g = Bx.g;
         const Phys &ph = Bx.ph;
         const float4 *xf = Bx.xf[0];
@@ -248,17 +251,29 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
                         }
                 }
             };
-            // pass 1 counts and keeps the first NL_CACHE partners of the lane in
+            // one lane: a single pass writes the list.  Several lanes: pass 1
+            // counts and keeps the first NL_CACHE partners of the lane in
             // shared memory; pass 2 writes them (scanning again only past that)
             int cnt = 0;
             int *cache = nl_cache[threadIdx.x];
+            int *lst = Bx.nlist + i * (long long)maxn;
+            if (LANES == 1) {
+                scan_rows([&](int j) {
+                    if (cnt < maxn) lst[cnt] = j;
+                    ++cnt;
+                });
+                if (act) {
+                    Bx.nlist_n[i] = min(cnt, maxn);
+                    if (cnt > maxn) atomicOr(Bx.status, ST_NLIST);
+                }
+                continue;
+            }
             scan_rows([&](int j) {
                 if (cnt < NL_CACHE) cache[cnt] = j;
                 ++cnt;
             });
             // exclusive sum of the counts over the lanes of the group
             int off = cnt;
-#pragma unroll
             for (int o = 1; o < LANES; o <<= 1) {
                 const int v = __shfl_up_sync(0xffffffffu, off, o);
                 if (lane >= o) off += v;
@@ -266,7 +281,6 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
             const int total = __shfl_sync(0xffffffffu, off, (threadIdx.x & 31) - lane + LANES - 1);
             off -= cnt;
             if (!act) continue;
-            int *lst = Bx.nlist + i * (long long)maxn;
             if (cnt <= NL_CACHE) {
                 for (int c = 0; c < cnt; ++c)
                     if (off + c < maxn) lst[off + c] = cache[c];
@@ -372,7 +386,7 @@ __device__ __noinline__ void pair64_out(const BoxDev &Bx, const double *__restri
 // and the outputs of the substep
 template <bool WALLS>
 __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<double> &pd, long long i,
-                                               int src_tmp, double F[3], double T[3], unsigned nlim) {
+                                               int src_tmp, double F[3], double T[3], unsigned nlim, int key_out) {
     const double *xin = src_tmp ? Bx.xtmp : Bx.pf[Bx.cur];
     double *xout = src_tmp ? Bx.pf[Bx.cur] : Bx.xtmp;
     const float4 *fin = Bx.xf[src_tmp], *vin = Bx.vf[src_tmp];
@@ -435,6 +449,13 @@ __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<
     fout[i] = make_float4((float)xn3[0], (float)xn3[1], (float)xn3[2], pi.w);
     vout[i] = make_float4((float)un3[0], (float)un3[1], (float)un3[2], vi.w);
     oout[i] = make_float4((float)wn3[0], (float)wn3[1], (float)wn3[2], 0.f);
+    if (key_out) {
+        // last substep of the subcycle: the linked cell of the new position,
+        // counted for the sort that follows (its counting pass)
+        const long long c = particle_cell(g, xn3[0], xn3[1], xn3[2], Bx.status);
+        Bx.key[i] = (int)c;
+        atomicAdd(&Bx.count[c], 1);
+    }
     if (d2 > ph.skin_half2) atomicOr(Bx.status, ST_SKIN);
     if (!(d2 < 1e30)) atomicOr(Bx.status, ST_NAN);
     if (nlim) atomicAdd(&Bx.counters[CNT_LUB_LIMITED], (unsigned long long)nlim);
@@ -450,9 +471,13 @@ constexpr int DEM_CHUNK = 256;
 // Mixed forms: lane groups of LANES lanes per particle walk its list; pairs
 // away from contact run in FP32 from the float copies, the rare pairs near
 // contact in FP64 (out of line), walls in phase B.
+// at most 128 registers a thread: two 256-thread blocks per SM (16 warps), the
+// occupancy the FP32 pair loop needs to hide its load latency (with 150
+// registers a dense settling box ran 1.3-1.7x slower)
 template <int LANES>
-__global__ void __launch_bounds__(256) k_dem_substep_mixed(const BoxDev *__restrict__ boxes,
-                                                           const Tile *__restrict__ tiles, int ntiles, int src_tmp) {
+__global__ void __launch_bounds__(256, 2) k_dem_substep_mixed(const BoxDev *__restrict__ boxes,
+                                                           const Tile *__restrict__ tiles, int ntiles, int src_tmp,
+                                                           int key_out) {
     __shared__ double sFT[6][DEM_CHUNK];
     __shared__ unsigned sN[DEM_CHUNK];
     const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
@@ -545,7 +570,7 @@ __global__ void __launch_bounds__(256) k_dem_substep_mixed(const BoxDev *__restr
             for (long long i = cb + threadIdx.x; i < ce; i += blockDim.x) {
                 const int s = (int)(i - cb);
                 double F[3] = {sFT[0][s], sFT[1][s], sFT[2][s]}, T[3] = {sFT[3][s], sFT[4][s], sFT[5][s]};
-                finish_particle<true>(Bx, pd, i, src_tmp, F, T, sN[s]);
+                finish_particle<true>(Bx, pd, i, src_tmp, F, T, sN[s], key_out);
             }
             __syncthreads();
         }
@@ -599,7 +624,7 @@ constexpr int DQ_CAP = 384;
 
 template <int LANES>
 __global__ void __launch_bounds__(256, 1) k_dem_substep64(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
-                                                       int ntiles, int src_tmp) {
+                                                       int ntiles, int src_tmp, int key_out) {
     __shared__ double sFT[6][DEM_CHUNK];
     __shared__ unsigned sN[DEM_CHUNK];
     __shared__ double qR[6][DQ_CAP];
@@ -733,25 +758,24 @@ __global__ void __launch_bounds__(256, 1) k_dem_substep64(const BoxDev *__restri
             for (long long i = cb + threadIdx.x; i < ce; i += blockDim.x) {
                 const int s = (int)(i - cb);
                 double F[3] = {sFT[0][s], sFT[1][s], sFT[2][s]}, T[3] = {sFT[3][s], sFT[4][s], sFT[5][s]};
-                finish_particle<false>(Bx, pd, i, src_tmp, F, T, sN[s]);
+                finish_particle<false>(Bx, pd, i, src_tmp, F, T, sN[s], key_out);
             }
             __syncthreads();
         }
     }
 }
 
-void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int lanes, int grid, int block,
-                        cudaStream_t s) {
-    if (lanes >= 8) k_build_nlist<8><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
-    else if (lanes == 4) k_build_nlist<4><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
-    else if (lanes == 2) k_build_nlist<2><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
-    else k_build_nlist<1><<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+// block: a multiple of 32 and of every tile's lanes (Tile::first)
+void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int grid, int block, cudaStream_t s) {
+    k_build_nlist<<<grid, block, 0, s>>>(boxes, tiles, ntiles);
 }
 
 // lanes: 1, 2, 4 or 8 lanes per particle (block a multiple of 32)
-void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int src_tmp, int mixed, int lanes,
-                        int grid, int block, cudaStream_t s) {
-#define DPS_DEM(K, L) K<L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp)
+// key_out: the last substep of a subcycle also writes the particles' linked
+// cells and their counts for the sort that follows
+void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int src_tmp, int key_out, int mixed,
+                        int lanes, int grid, int block, cudaStream_t s) {
+#define DPS_DEM(K, L) K<L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp, key_out)
     if (mixed) {
         if (lanes >= 8) DPS_DEM(k_dem_substep_mixed, 8);
         else if (lanes == 4) DPS_DEM(k_dem_substep_mixed, 4);

@@ -133,6 +133,15 @@ __host__ __device__ inline int containing_cell(double x, int L) {
     return i < 0 ? 0 : (i > L - 1 ? L - 1 : i);
 }
 
+// linked cell of a particle (flags a position outside the box on a wall axis)
+__device__ __forceinline__ long long particle_cell(const Geom &g, double x, double y, double z, int *st) {
+    int ix = containing_cell(x, g.n[0]), iy = containing_cell(y, g.n[1]), iz = containing_cell(z, g.n[2]);
+    if (st && ((!g.per[0] && (x < 0.0 || x >= g.n[0])) || (!g.per[1] && (y < 0.0 || y >= g.n[1])) ||
+               (!g.per[2] && (z < 0.0 || z >= g.n[2]))))
+        atomicOr(st, ST_BAD_CELL);
+    return cell_index(g, ix, iy, iz);
+}
+
 // closure constants, derived once on the host
 struct Phys {
     double tau, omega, kf, rho_f, mu;   // kf = 1 - 1/(2 tau) (Eq. Forcing)

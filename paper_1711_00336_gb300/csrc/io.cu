@@ -6,6 +6,7 @@
 //  - deterministic FP64 sums: a fixed grid of blocks, each summing a fixed
 //    strided subset and reducing it in a fixed tree, then one block summing
 //    the partials in index order.
+#include "box.cuh"
 #include "lbm_dev.cuh"
 
 namespace dps {
@@ -196,6 +197,25 @@ __global__ void k_particles_export(const double *__restrict__ base, int plane, l
     }
 }
 
+// x, u, omega and the frozen force of a box in insertion order, one pass:
+// out = [x(np,3) | u(np,3) | omega(np,3) | F(np,3)].  With a device table
+// the current particle set is read from its entry k (no host round trip to
+// learn it); else from pf / ids.
+__global__ void k_particles_export4(const BoxDev *__restrict__ tab, int k, const double *__restrict__ pf0,
+                                    const int *__restrict__ ids0, long long cap, long long np,
+                                    double *__restrict__ out) {
+    const double *pf = tab ? tab[k].pf[tab[k].cur] : pf0;
+    const int *ids = tab ? tab[k].pi[tab[k].cur] + IID * cap : ids0;
+    const int plane[4] = {PX, PU, POX, PFH0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np; i += (long long)gridDim.x * blockDim.x) {
+        const long long id = ids[i];
+#pragma unroll
+        for (int gq = 0; gq < 4; ++gq)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) out[gq * 3 * np + 3 * id + a] = pf[(plane[gq] + a) * cap + i];
+    }
+}
+
 __global__ void k_particles_import(double *__restrict__ base, int plane, long long cap, long long np,
                                    const int *__restrict__ ids, const double *__restrict__ in) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
@@ -255,6 +275,11 @@ void launch_particles_export(const double *base, int plane, long long cap, long 
                              cudaStream_t s) {
     if (np <= 0) return;
     k_particles_export<<<grid_for(np, 256), 256, 0, s>>>(base, plane, cap, np, ids, out);
+}
+void launch_particles_export4(const BoxDev *tab, int k, const double *pf, const int *ids, long long cap, long long np,
+                              double *out, cudaStream_t s) {
+    if (np <= 0) return;
+    k_particles_export4<<<grid_for(np, 256), 256, 0, s>>>(tab, k, pf, ids, cap, np, out);
 }
 void launch_particles_import(double *base, int plane, long long cap, long long np, const int *ids, const double *in,
                              cudaStream_t s) {

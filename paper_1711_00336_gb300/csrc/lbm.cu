@@ -351,7 +351,7 @@ template <typename ST, typename FT, typename CT, int PAR>
 __device__ __forceinline__ void moments_cell(const ST *__restrict__ pdf, const FT *__restrict__ eps,
                                              const FT *__restrict__ fpf, const Geom &g, long long c, CT fbx, CT fby,
                                              CT fbz, FT *__restrict__ rho_o, FT *__restrict__ j_o,
-                                             FT *__restrict__ uD) {
+                                             FT *__restrict__ uD, FT *__restrict__ ire) {
     const long long N = g.ncell;
     int ix, iy, iz;
     cell_coords(g, c, ix, iy, iz);
@@ -368,6 +368,7 @@ __device__ __forceinline__ void moments_cell(const ST *__restrict__ pdf, const F
     j_o[N + c] = (FT)jy;
     j_o[2 * N + c] = (FT)jz;
     const CT s = CT(1) / (rho * e);
+    ire[c] = (FT)s;  // the first subcycle's drag interpolation reuses it
     uD[c] = (FT)((jx + CT(0.5) * Fx) * s);
     uD[N + c] = (FT)((jy + CT(0.5) * Fy) * s);
     uD[2 * N + c] = (FT)((jz + CT(0.5) * Fz) * s);
@@ -382,11 +383,11 @@ __global__ void __launch_bounds__(128, sizeof(CT) == 8 ? 2 : 4) k_moments(const 
         const Geom g = B.g;
         const ST *pdf = (const ST *)B.pdf;
         const FT *eps = (const FT *)B.eps, *fpf = (const FT *)B.fpf;
-        FT *rho = (FT *)B.rho, *j = (FT *)B.j, *uD = (FT *)B.uD;
+        FT *rho = (FT *)B.rho, *j = (FT *)B.j, *uD = (FT *)B.uD, *ire = (FT *)B.ire;
         const CT fbx = pick<CT>(B.ph.fb[0], B.ph.fb_f[0]), fby = pick<CT>(B.ph.fb[1], B.ph.fb_f[1]),
                  fbz = pick<CT>(B.ph.fb[2], B.ph.fb_f[2]);
         for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
-            moments_cell<ST, FT, CT, PAR>(pdf, eps, fpf, g, c, fbx, fby, fbz, rho, j, uD);
+            moments_cell<ST, FT, CT, PAR>(pdf, eps, fpf, g, c, fbx, fby, fbz, rho, j, uD, ire);
     }
 }
 
