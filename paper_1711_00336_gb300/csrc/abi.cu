@@ -72,7 +72,6 @@ template <typename ST, typename FT>
 void launch_fluid_sums(const void *, const void *, const void *, const Geom &, const double *, int, double *, double *,
                        cudaStream_t);
 void launch_particle_sums(const double *, const double *, long long, long long, double *, double *, cudaStream_t);
-void launch_particles_export(const double *, int, long long, long long, const int *, double *, cudaStream_t);
 void launch_particles_import(double *, int, long long, long long, const int *, const double *, cudaStream_t);
 void launch_particles_export4(const BoxDev *, int, const double *, const int *, long long, long long, double *,
                               cudaStream_t);

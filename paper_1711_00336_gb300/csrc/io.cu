@@ -188,15 +188,6 @@ __global__ void k_final_sums(const double *partials, int nblocks, int nq, int mi
 
 // ---- particles in insertion order -------------------------------------------------------
 // out[3*id + a] = planes[(a)*cap + k] for the 3 planes starting at `plane`
-__global__ void k_particles_export(const double *__restrict__ base, int plane, long long cap, long long np,
-                                   const int *__restrict__ ids, double *__restrict__ out) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
-        long long id = ids[k];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) out[3 * id + a] = base[(plane + a) * cap + k];
-    }
-}
-
 // x, u, omega and the frozen force of a box in insertion order, one pass:
 // out = [x(np,3) | u(np,3) | omega(np,3) | F(np,3)].  With a device table
 // the current particle set is read from its entry k (no host round trip to
@@ -270,11 +261,6 @@ void launch_particle_sums(const double *xuw, const double *pf, long long cap, lo
                           double *out, cudaStream_t s) {
     k_particle_sums<<<RED_BLOCKS, RED_THREADS, 0, s>>>(xuw, pf, cap, np, partials);
     k_final_sums<<<1, 32, 0, s>>>(partials, RED_BLOCKS, PART_Q, -1, out);
-}
-void launch_particles_export(const double *base, int plane, long long cap, long long np, const int *ids, double *out,
-                             cudaStream_t s) {
-    if (np <= 0) return;
-    k_particles_export<<<grid_for(np, 256), 256, 0, s>>>(base, plane, cap, np, ids, out);
 }
 void launch_particles_export4(const BoxDev *tab, int k, const double *pf, const int *ids, long long cap, long long np,
                               double *out, cudaStream_t s) {

@@ -233,3 +233,34 @@ def test_serving_groups_requests_by_subcycle_counts():
     S.close()
     assert all(r["state"] == "done" and r["steps"] == 200 for r in res), res
     assert st["failed"] == 0
+
+
+def test_read_back_of_a_box_added_after_stepping():
+    """Particle read-back reads the current particle set of a stepped box from
+    the device table, and the host copy of a box added since: both give the
+    state in insertion order, and the late box then steps as it would alone."""
+    dps = _dps()
+    wls = _boxes()
+    steps = 4
+    B = dps.Batch("f64")
+    a = B.add_box(wls[0]["n"], wls[0]["periodic"], wls[0]["tau"], len(wls[0]["x"]))
+    B.add_particles(a, wls[0]["x"], wls[0]["d"], wls[0]["rho_p"])
+    B.set_closure(a, _closure(dps, wls[0]))
+    B.step(steps)
+    ra = B.read_particles(a)
+    ref_a, _ = _alone(dps, wls[0], "f64", steps)
+    assert np.array_equal(ra["x"], ref_a["x"]) and np.array_equal(ra["w"], ref_a["w"])
+    wl = wls[2]
+    b = B.add_box(wl["n"], wl["periodic"], wl["tau"], len(wl["x"]))
+    B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
+    B.set_closure(b, _closure(dps, wl))
+    rb = B.read_particles(b)  # not yet in the device table
+    assert np.array_equal(rb["x"], np.asarray(wl["x"], dtype=np.float64))
+    assert not rb["u"].any() and not rb["w"].any()
+    assert np.array_equal(B.read_particles(a)["x"], ra["x"])  # the stepped box is unchanged
+    B.step(steps)
+    ref_b, _ = _alone(dps, wl, "f64", steps)
+    got = B.read_particles(b)
+    for k in ("x", "u", "w", "F"):
+        assert np.array_equal(got[k], ref_b[k]), k
+    B.close()
