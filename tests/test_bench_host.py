@@ -1,0 +1,42 @@
+"""Host-side arithmetic of the benchmark line (no GPU): the algorithmic bytes
+per cell of the collide-stream kernel, the whole-job MLUPS of the replicas,
+and the partner count that scales the DEM flop model, each against a value
+worked out by hand."""
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_collide_stream_bytes_per_cell():
+    # 19 loads + 19 stores of the PDF type, eps_f and f_pf (4 field values);
+    # the FP64 coupled step also reads rho and j (4 more)
+    assert bench.algorithmic_bytes_collide("f64") == 2 * 19 * 8 + 4 * 8 == 336
+    assert bench.algorithmic_bytes_collide("f64", True) == 336 + 4 * 8 == 368
+    assert bench.algorithmic_bytes_collide("f32") == 2 * 19 * 4 + 4 * 4 == 168
+    assert bench.algorithmic_bytes_collide("f16s") == 2 * 19 * 2 + 4 * 4 == 92
+
+
+def test_job_mlups_counts_every_replica():
+    assert abs(bench.job_mlups(2, 262144, 100, 1000.0) - 2 * 262144 * 100 / 1.0 / 1e6) < 1e-9
+    assert bench.job_mlups(1, 1000, 10, 1.0) == 10.0
+
+
+def test_lubrication_partners_by_hand():
+    d = np.ones(5)
+    x = [(1.0, 1.0, 1.0),    # A: B at gap 0.5, bottom wall at gap 0.5
+         (2.5, 1.0, 1.0),    # B: A, bottom wall
+         (5.0, 5.0, 4.0),    # C: nothing within 1 (walls at 3.5)
+         (7.9, 6.0, 4.0),    # D: E across the periodic x face (gap -0.5)
+         (0.4, 6.0, 4.0)]    # E: D
+    n, h_c = (8, 8, 8), 1.0
+    # walls on z: A and B see the bottom wall; pairs A-B and D-E
+    assert bench.lubrication_partners(x, d, n, (1, 1, 0), h_c) == (2 + 2 + 0 + 1 + 1) / 5
+    # fully periodic: no walls
+    assert bench.lubrication_partners(x, d, n, (1, 1, 1), h_c) == (1 + 1 + 0 + 1 + 1) / 5
+    # walls on x: A (x - d/2 = 0.5) and E (-0.1) reach the x = 0 face, D the
+    # x = 8 face (-0.4); D and E are 7.5 apart, no longer partners
+    assert bench.lubrication_partners(x, d, n, (0, 1, 1), h_c) == (2 + 1 + 0 + 1 + 1) / 5
