@@ -309,3 +309,24 @@ def test_dense_box_lane_groups_match_the_oracle(eps, d):
         close(got[k], r[k], what=k, floor=fl_)
     close(dom.read_fields(("ubar",))["ubar"], ref.fields()["ubar"], what="ubar", floor=1e-3)
     dom.close()
+
+
+def test_full_size_wall_suspension_fp64():
+    """The benchmark configuration at its full size (64^3, 5000 spheres,
+    walls in z, n_int = 1, n_DEM = 10, FP64) through the same public calls the
+    benchmark makes: two coupled steps against the oracle, every particle and
+    every cell."""
+    import bench
+    wl = workloads.wall_suspension()
+    kw = {k: v for k, v in bench.closure_kw(wl).items() if k not in ("g", "fb", "fb_mode", "skin")}
+    pr = {"x": wl["x"], "d": wl["d"], "rho_p": wl["rho_p"]}
+    dom, ref = _run_pair(wl["n"], wl["periodic"], wl["tau"], pr, 2, g=wl["g"], **kw)
+    got, r = dom.read_particles(), ref.particles()
+    for k, fl_ in (("x", 0.0), ("u", 1e-3), ("w", 1e-3), ("F", 1e-6)):
+        close(got[k], r[k], what=k, floor=fl_)
+    fl, fr = dom.read_fields(("rho", "ubar", "eps_f", "f_pf")), ref.fields()
+    close(fl["rho"], fr["rho"], what="rho")
+    close(fl["ubar"], fr["ubar"], what="ubar", floor=1e-3)
+    close(fl["eps_f"], fr["eps_f"], what="eps_f")
+    close(fl["f_pf"], ref.fpf, what="f_pf", floor=1e-6)
+    dom.close()
