@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
             } else {
                 int w = off;
                 scan_rows([&](int j) {
-                    if (w < maxn) lst[w] = j;
+                    if (w < maxn && w < off + cnt) lst[w] = j;  // within the lane's counted slots
                     ++w;
                 });
             }
@@ -700,7 +700,9 @@ __global__ void __launch_bounds__(256, 1) k_dem_substep64(const BoxDev *__restri
                     if (act && off < w0 + mw && off + cnt > w0) {
                         int c = off;
                         entries([&](int j) {
-                            if (c >= w0 && c < w0 + mw) {
+                            // (c < off + cnt: the passes screen alike; the bound only
+                            // keeps a lane inside its own slots)
+                            if (c >= w0 && c < w0 + mw && c < off + cnt) {
                                 qJ[c - w0] = j;
                                 qP[c - w0] = (int)(i - cb);
                             }
