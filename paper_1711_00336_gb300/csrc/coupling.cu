@@ -750,7 +750,7 @@ __global__ void k_force_am(const BoxDev *__restrict__ boxes, const Tile *__restr
 }
 
 // Table 1 drag correlation (Tenneti et al.).  In FP64 each dependent
-// instruction costs this GPU tens of cycles, so the chain is kept short:
+// instruction costs GB300 tens of cycles, so the chain is kept short:
 // Re^0.687 as exp(0.687 ln Re) (Re > 0; relative error a few 1e-16, far below
 // the FP64 parity tolerance), and one division, 1/(1 - eps_p), for the four
 // quotients.

@@ -345,7 +345,7 @@ __device__ __forceinline__ void pair64_body(const PairPar<double> &pd, const dou
     }
     // m_ij = A / Bm and <d> = C / D: spheres m_i m_j / (m_i + m_j) and
     // 2 d_i d_j / (d_i + d_j), walls m_i and 2 d_i; one division per pair
-    // (FP64 instructions bound this path on this GPU)
+    // (FP64 instructions bound this path on GB300)
     const double A = wall ? mi : mi * mj, Bm = wall ? 1.0 : mi + mj;
     const double C = wall ? 2.0 * di : 2.0 * di * dj, D = wall ? 1.0 : di + dj;
     const double delta = sumr - dist;

@@ -164,7 +164,7 @@ struct Phys {
 // ---- precision-preserving math -----------------------------------------------
 // The kernels are templated on their arithmetic type; these overloads call the
 // single-precision functions for float, so FP32 arithmetic never widens to
-// FP64 (whose pipe is a small fraction of the FP32 rate on this GPU).
+// FP64 (whose pipe is a small fraction of the FP32 rate on GB300).
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
