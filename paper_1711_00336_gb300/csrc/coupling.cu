@@ -264,53 +264,12 @@ __global__ void k_end_step(BoxDev *boxes, int nboxes) {
 }
 
 // ---- 27-cell gather helpers ---------------------------------------------------
-struct CellNb {
-    long long c[3][3];   // neighbour linear index per axis offset (partial sums), -1 if beyond a wall
-};
-
-__device__ __forceinline__ void cell_coords_c(const Geom &g, long long c, int &ix, int &iy, int &iz) {
-    const unsigned cc = (unsigned)c, nx = (unsigned)g.n[0], nxy = nx * (unsigned)g.n[1];
-    const unsigned z = cc / nxy, r = cc - z * nxy, y = r / nx;
-    iz = (int)z;
-    iy = (int)y;
-    ix = (int)(r - y * nx);
-}
-
+// cell coordinate i on an axis of L cells: wrapped on a periodic axis, -1
+// beyond a wall
 __device__ __forceinline__ int wrap_axis(int i, int L, int per) {
     if (i >= 0 && i < L) return i;
     if (!per) return -1;
     return i < 0 ? i + L : i - L;
-}
-
-// Gather over the particles whose kernel support covers cell c: the particles
-// of the 27 cells c+o, o in {-1,0,1}^3, with weight W_p(c) =
-// w_x[1-o_x] w_y[1-o_y] w_z[1-o_z].  Visit order: o_z, o_y, o_x ascending,
-// then the sorted order inside a cell.
-template <typename WT, typename Fn>
-__device__ __forceinline__ void gather27(const Geom &g, long long c, const int *__restrict__ cell_start,
-                                         const WT *__restrict__ w, long long cap, Fn &&fn) {
-    int ix, iy, iz;
-    cell_coords_c(g, c, ix, iy, iz);
-#pragma unroll 1
-    for (int oz = -1; oz <= 1; ++oz) {
-        int z = wrap_axis(iz + oz, g.n[2], g.per[2]);
-        if (z < 0) continue;
-#pragma unroll 1
-        for (int oy = -1; oy <= 1; ++oy) {
-            int y = wrap_axis(iy + oy, g.n[1], g.per[1]);
-            if (y < 0) continue;
-            const WT *wz = w + (6 + 1 - oz) * cap, *wy = w + (3 + 1 - oy) * cap;
-#pragma unroll 1
-            for (int ox = -1; ox <= 1; ++ox) {
-                int x = wrap_axis(ix + ox, g.n[0], g.per[0]);
-                if (x < 0) continue;
-                const long long n = cell_index(g, x, y, z);
-                const int s = cell_start[n], e = cell_start[n + 1];
-                const WT *wx = w + (1 - ox) * cap;
-                for (int p = s; p < e; ++p) fn(p, wx[p] * wy[p] * wz[p]);
-            }
-        }
-    }
 }
 
 // the kernel weights of a box in the compute type FT of its form
@@ -343,24 +302,6 @@ __device__ __forceinline__ void brick_unpack(long long v, int &x, int &y, int &z
 struct BrickRanges {
     int s[HALO3], e[HALO3];
 };
-
-// stage the particle ranges of the halo cells of brick (ox,oy,oz)+[0,ex)x[0,ey)x[0,ez)
-__device__ __forceinline__ void stage_ranges(const BoxDev &B, int ox, int oy, int oz, BrickRanges &R) {
-    const Geom &g = B.g;
-    for (int h = threadIdx.x; h < HALO3; h += blockDim.x) {
-        const int hx = h % HALO, hy = (h / HALO) % HALO, hz = h / (HALO * HALO);
-        const int x = wrap_axis(ox + hx - 1, g.n[0], g.per[0]);
-        const int y = wrap_axis(oy + hy - 1, g.n[1], g.per[1]);
-        const int z = wrap_axis(oz + hz - 1, g.n[2], g.per[2]);
-        if (x < 0 || y < 0 || z < 0) {
-            R.s[h] = R.e[h] = 0;
-        } else {
-            const long long n = cell_index(g, x, y, z);
-            R.s[h] = B.cell_start[n];
-            R.e[h] = B.cell_start[n + 1];
-        }
-    }
-}
 
 // gather over the 27 halo neighbours of brick cell (lx,ly,lz) with weights w
 template <typename WT, typename Fn>
@@ -610,27 +551,8 @@ __device__ __forceinline__ Support<FT> support_of(const BoxDev &B, const double 
     return S;
 }
 
-// visit the in-domain cells of the support (Eq. interpolation), fn(cell, W)
-template <typename FT, typename Fn>
-__device__ __forceinline__ void for_support(const Geom &g, const Support<FT> &S, Fn &&fn) {
-#pragma unroll 1
-    for (int oz = 0; oz < 3; ++oz) {
-        const int z = wrap_axis(S.b[2] + oz - 1, g.n[2], g.per[2]);
-        if (z < 0) continue;
-        for (int oy = 0; oy < 3; ++oy) {
-            const int y = wrap_axis(S.b[1] + oy - 1, g.n[1], g.per[1]);
-            if (y < 0) continue;
-            for (int ox = 0; ox < 3; ++ox) {
-                const int x = wrap_axis(S.b[0] + ox - 1, g.n[0], g.per[0]);
-                if (x < 0) continue;
-                fn(cell_index(g, x, y, z), S.wx[ox] * S.wy[oy] * S.wz[oz]);
-            }
-        }
-    }
-}
-
 // the cells s = lane, lane + lanes, ... (s < 27, s = 9 o_z + 3 o_y + o_x) of
-// the support; with one lane the order of for_support
+// the support (Eq. interpolation); with one lane in (o_z, o_y, o_x) order
 template <typename FT, typename Fn>
 __device__ __forceinline__ void for_support_lanes(const Geom &g, const Support<FT> &S, int lane, int lanes, Fn &&fn) {
 #pragma unroll 1
