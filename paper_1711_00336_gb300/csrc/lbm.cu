@@ -6,66 +6,15 @@
 //    direction q goes to plane opp(q)); odd parity reads the upstream values
 //    and writes the downstream cells.  Halfway bounce-back at wall faces is
 //    folded into the odd-parity index map.  HBM traffic per cell: 19 loads and
-//    19 stores of the PDF type plus eps_f and f_pf (4 loads of the field type).
-// K2a moments: rho, j of f(x,t) and u_D = (j + f_ext/2)/(rho eps_f); one PDF read.
+//    19 stores of the PDF type plus eps_f and f_pf (4 loads of the field type);
+//    in the FP64 coupled step also rho and j from K2a (4 more).
+// K2a moments: rho, j of f(x,t), u_D = (j + f_ext/2)/(rho eps_f) and
+//    1/(rho eps_f); one PDF read.
 // K2b fields: stencil over rho and u_D giving grad(eps_f p) and Du_f/Dt.
 #include "box.cuh"
 #include "lbm_dev.cuh"
 
 namespace dps {
-
-// Eq. LBM_Equation for one cell: BGK relaxation towards the porous
-// equilibrium (Eq. LBM_EQ) plus the Guo forcing term (Eq. Forcing).  With
-// DEV the populations are deviations f_q - w_q (rho_0 = 1): rho = 1 + sum,
-// and the update of a deviation is f' - w = (1-omega)(f - w) +
-// omega(f^eq - w) + F.  The update is written per opposite pair (q, q+9): the
-// even part in c of omega*f^eq + F is E = K0 + cu (K1 cu + K2 cF), the odd part
-// O = K3 cu + K4 cF, with K0..K4 fixed per weight class.
-template <typename CT, bool DEV>
-__device__ __forceinline__ void collide(CT f[Q], CT eps, CT Fx, CT Fy, CT Fz, CT omega, CT kf, CT &rho_out) {
-    CT s = f[0], jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int k = 1; k <= 9; ++k) {
-        s += f[k] + f[k + 9];
-        const CT d = f[k] - f[k + 9];
-        if (CX(k) != 0) jx += CX(k) * d;
-        if (CY(k) != 0) jy += CY(k) * d;
-        if (CZ(k) != 0) jz += CZ(k) * d;
-    }
-    const CT rho = DEV ? CT(1) + s : s;
-    const CT ir = CT(1) / rho;
-    const CT ux = (jx + CT(0.5) * Fx) * ir;  // Eq. MacVel
-    const CT uy = (jy + CT(0.5) * Fy) * ir;
-    const CT uz = (jz + CT(0.5) * Fz) * ir;
-    const CT ie = CT(1) / eps;
-    const CT uu = ux * ux + uy * uy + uz * uz;
-    const CT uF = ux * Fx + uy * Fy + uz * Fz;
-    const CT om1 = CT(1) - omega;
-    const CT b2 = CT(-1.5) * uu * ie;                 // -u.u/(2 eps c_s^2)
-    // omega (f^eq - shift) per unit weight for cu = 0, and the force part
-    const CT e0 = DEV ? omega * (s + rho * b2) : omega * rho * (CT(1) + b2);
-    const CT f0 = CT(-3) * kf * uF * ie;
-    {
-        const CT w = (CT)WQ(0);
-        f[0] = om1 * f[0] + w * (e0 + f0);
-    }
-    const CT k1 = omega * rho * CT(4.5) * ie, k2 = CT(9) * kf * ie;
-    const CT k3 = CT(3) * omega * rho, k4 = CT(3) * kf;
-#pragma unroll
-    for (int k = 1; k <= 9; ++k) {
-        const CT w = (CT)WQ(k);
-        CT cu = 0, cF = 0;
-        if (CX(k) != 0) { cu += CX(k) * ux; cF += CX(k) * Fx; }
-        if (CY(k) != 0) { cu += CY(k) * uy; cF += CY(k) * Fy; }
-        if (CZ(k) != 0) { cu += CZ(k) * uz; cF += CZ(k) * Fz; }
-        const CT E = w * (e0 + f0 + cu * (k1 * cu + k2 * cF));
-        const CT O = w * (k3 * cu + k4 * cF);
-        const CT fp = f[k], fm = f[k + 9];
-        f[k] = om1 * fp + (E + O);
-        f[k + 9] = om1 * fm + (E - O);
-    }
-    rho_out = rho;
-}
 
 // Eq. tau_e for one cell: tau_* from the Eilers viscosity of eps_p = 1 - eps_f
 // (Eq. visc_eilers; eps_p/eps_cp capped at 0.9 where it diverges) plus the
@@ -108,8 +57,8 @@ __device__ __forceinline__ CT tau_cell(const CT f[Q], CT s, CT rho, CT ux, CT uy
 }
 
 // K1 body for one cell: load the 19 populations (AA parity PAR), relax them
-// (Eq. LBM_Equation, same algebra as collide()) and store each opposite pair
-// as soon as it is computed, which keeps few values live.  VISC: the box may
+// (Eq. LBM_Equation, relax_cell) and store each opposite pair as soon as it
+// is computed, which keeps few values live.  VISC: the box may
 // relax with a per-cell tau_e (vmode bit 0 Eilers, bit 1 Smagorinsky).
 template <typename ST, typename FT, typename CT, int PAR, bool VISC, bool MOMIN>
 __device__ __forceinline__ void relax_store_cell(ST *__restrict__ pdf, CT f[Q], const NbDelta &D, bool in,
@@ -224,7 +173,14 @@ __device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b
 __device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
 
 // relaxation (Eq. LBM_Equation) of one cell whose populations f, eps_f and
-// f_pf are loaded: f is overwritten with the post-collision populations.
+// f_pf are loaded: BGK relaxation towards the porous equilibrium (Eq.
+// LBM_EQ) plus the Guo forcing term (Eq. Forcing); f is overwritten with the
+// post-collision populations.  With deviation storage (shifted forms) the
+// populations are f_q - w_q (rho_0 = 1): rho = 1 + sum, and the update of a
+// deviation is f' - w = (1-omega)(f - w) + omega(f^eq - w) + F.  The update
+// is written per opposite pair (q, q+9): the even part in c of
+// omega f^eq + F is E = K0 + cu (K1 cu + K2 cF), the odd part
+// O = K3 cu + K4 cF, with K0..K4 fixed per weight class.
 // `flag`: report a non-finite or non-positive density.
 // MOMIN: the moments s, j of these populations were computed by K2a in this
 // step with the same sums (the FP64 form): they are passed in, not re-summed.

@@ -67,25 +67,6 @@ __device__ __forceinline__ void load_pdfs(const ST *__restrict__ pdf, long long 
     }
 }
 
-template <typename ST, typename CT, int PAR>
-__device__ __forceinline__ void store_pdfs(ST *__restrict__ pdf, long long N, long long c,
-                                           const NbDelta &D, const CT f[Q]) {
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        if (q == 0) {
-            Store<ST>::store(pdf + c, f[0]);
-        } else if (PAR == 0) {
-            Store<ST>::store(pdf + (unsigned)(OPP(q) * (unsigned)N + (unsigned)c), f[q]);
-        } else {
-            const int dp = nb_delta(D, q);
-            if (dp != INV)
-                Store<ST>::store(pdf + (unsigned)(q * (unsigned)N + (unsigned)c + (unsigned)dp), f[q]);
-            else  // bounce back: returns to this cell with velocity -c_q
-                Store<ST>::store(pdf + (unsigned)(OPP(q) * (unsigned)N + (unsigned)c), f[q]);
-        }
-    }
-}
-
 // store the post-collision pair (k, k+9) under the AA parity
 template <typename ST, typename CT, int PAR>
 __device__ __forceinline__ void store_pair(ST *__restrict__ pdf, long long N, long long c, const NbDelta &D, int k,
