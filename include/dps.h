@@ -208,11 +208,46 @@ int dps_read_particles(dps_handle h, double *x3, double *u3, double *w3, double 
                        int64_t cap);
 int dps_stats_get(dps_handle h, dps_stats *s);
 
+/* ---- checkpoint / resume ------------------------------------------------- */
+/* The state one coupled step of Algorithm 1 (Sec. 3.3) carries into the next,
+ * copied into a caller-owned host buffer between steps: the PDFs f_q(x,t) as
+ * stored (in the canonical layout, whatever the AA parity), eps_f (Eq.
+ * fluid_volume_fraction), the f_pf applied in the last step (Eq. forces_pf),
+ * the fluid velocity of the last step (for Du_f/Dt, Table 1), the particle
+ * state of Eq. particle_motion (x, u, w, d, rho_p and the per-particle history:
+ * u at the last subcycle start, the frozen forces), the step count, closure,
+ * counters and status.  Linked cells, neighbour lists and the other derived
+ * arrays are rebuilt on load by the initialisation sort, bit for bit as the
+ * uninterrupted run holds them, so N steps + save + load (into a new domain)
+ * + N steps gives the same bits as 2N steps.  The buffer format is private to
+ * this library version (a header checks it).
+ * dps_state_size: bytes of the checkpoint of h with its current particle count.
+ * dps_save_state: waits for h's stream, writes the checkpoint into buf
+ *   (cap bytes).  Errors: DPS_ERR_ARG (buf NULL or too small), DPS_ERR_CUDA.
+ * dps_load_state: restores a checkpoint into h, which must have been created
+ *   with the same n, periodic, tau, rho_f and precision and with
+ *   max_particles >= the saved particle count; h's own particles and fluid are
+ *   replaced.  Errors: DPS_ERR_ARG (not a checkpoint, truncated, or of another
+ *   geometry / form), DPS_ERR_OOM, DPS_ERR_CUDA. */
+int dps_state_size(dps_handle h, size_t *bytes);
+int dps_save_state(dps_handle h, void *buf, size_t cap);
+int dps_load_state(dps_handle h, const void *buf, size_t size);
+
 /* The current linked-cell sort (the neighbour search of the DEM and the
  * gather of the coupling): cell_start[ncell+1] over cell keys, order[np] the
  * insertion indices in sorted order.  See dps_op_cell_sort for the key. */
 int dps_read_cell_list(dps_handle h, int32_t *cell_start, int32_t *order, int64_t cap_cells,
                        int64_t cap_particles);
+/* The neighbour (Verlet) list of the DEM substeps (Sec. 3.1, pairs that
+ * the contact and lubrication laws may reach) as built at the last linked-
+ * cell sort: for particle i (insertion order) every partner j != i whose
+ * centre lay within (d_i + d_j)/2 + h_c + skin of x_i at that sort (minimum
+ * image on periodic axes; the search compares in FP32 with a margin of 1e-3
+ * dx, so pairs within that margin of the range may be listed), as CSR:
+ * offsets[np + 1] (int64) and partners[offsets[np]] (insertion indices, each
+ * row ascending).  partners may be NULL to learn offsets only; cap = capacity
+ * of partners.  Errors: DPS_ERR_ARG (capacity), DPS_ERR_CUDA. */
+int dps_read_neighbor_list(dps_handle h, int64_t *offsets, int32_t *partners, int64_t cap);
 /* bin edge B (cells) chosen for the current closure */
 int dps_bin_edge(dps_handle h, int *B);
 
@@ -269,6 +304,13 @@ int dps_batch_stats(dps_batch b, int box, dps_stats *s);
 /* mean particle velocity of a box (FP64, fixed summation order) */
 int dps_batch_particle_mean(dps_batch b, int box, double u[3]);
 int dps_batch_num_boxes(dps_batch b, int *n);
+/* checkpoint / resume of one box of a batch: the format and rules of
+ * dps_save_state / dps_load_state.  A box restored into a batch at the other
+ * AA parity has its PDFs moved to that parity's layout (a permutation of the
+ * stored values, no arithmetic). */
+int dps_batch_state_size(dps_batch b, int box, size_t *bytes);
+int dps_batch_save_box(dps_batch b, int box, void *buf, size_t cap);
+int dps_batch_load_box(dps_batch b, int box, const void *buf, size_t size);
 /* launch shape: cfg = {cell threads/block, cells/tile, particle threads/block,
  * particles/tile, collide-stream variant 0 ... 5 (register budget and cells
  * per thread of the low-precision forms; ignored in FP64)} */
@@ -352,10 +394,16 @@ int dps_serve_destroy(dps_server s);
  * cells per axis (the last bin of an axis takes the remainder); the key of a
  * cell orders cells bin-major (bz,by,bx), then (z,y,x) inside the bin, so
  * that every bin and every cell is one contiguous key range.  Particles are
- * sorted by (key of the cell containing them, ids).  Outputs (device):
- * cell_start[ncell+1] (exclusive prefix of the counts per key) and
- * order[np] (input index of each sorted slot).  Scratch is allocated on the
- * stream (stream-ordered).  Errors: DPS_ERR_ARG, DPS_ERR_OOM, DPS_ERR_CUDA. */
+ * sorted by (key of the cell containing them, ids, input index): ids are the
+ * tie-break of the method (the particle numbering) and should be distinct;
+ * equal ids keep their input order.  Outputs (device): cell_start[ncell+1]
+ * (exclusive prefix of the counts per key) and order[np] (input index of
+ * each sorted slot).  Every coordinate must lie in [0, n) on its axis
+ * (periodic axes already wrapped); the call waits for its stream to read a
+ * status word back and returns DPS_ERR_ARG if some coordinate lies outside or
+ * is not finite (the outputs then count such a particle in the clamped edge
+ * cell).  Scratch is allocated on the stream (stream-ordered).
+ * Errors: DPS_ERR_ARG, DPS_ERR_OOM, DPS_ERR_CUDA. */
 int dps_op_cell_sort(const int n[3], const int periodic[3], int B, int64_t np,
                      const double *x3, const int32_t *ids, int32_t *cell_start, int32_t *order,
                      void *stream);
@@ -375,9 +423,12 @@ int dps_op_cell_sort(const int n[3], const int periodic[3], int B, int64_t np,
  * larger sizes return DPS_ERR_ARG.  It calls no cudaMalloc/cudaFree or other
  * allocating routine.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call uses the one array and
- * leaves its contents behind: calls that overlap on the GPU (other streams or
- * threads) race, so the caller must serialise them. */
+ * first call before any stream capture.  The address is kept for the life of
+ * the process: the library must not be used on a device after a
+ * cudaDeviceReset of it.  Every call uses the one array and leaves its
+ * contents behind: calls that overlap on the GPU (other streams or threads)
+ * race, so the caller must serialise them.  Like dps_op_cell_sort it waits
+ * for its stream to read the status word back. */
 #define DPS_NOALLOC_MAX_CELLS 262144
 #define DPS_NOALLOC_MAX_PARTICLES 262144
 int dps_op_cell_sort_noalloc(const int n[3], const int periodic[3], int B, int64_t np, const double *x3,

@@ -76,6 +76,7 @@ void launch_particles_import(double *, int, long long, long long, const int *, c
 void launch_particles_export4(const BoxDev *, int, const double *, const int *, long long, long long, double *,
                               cudaStream_t);
 long long reduce_partials_doubles();
+void launch_pdf_relayout(const void *, const Geom &, int, int, void *, cudaStream_t);
 }  // namespace dps
 
 using namespace dps;
@@ -1150,6 +1151,184 @@ static int box_stats(Batch *B, BoxHost *h, dps_stats *s) {
     return DPS_OK;
 }
 
+// ---- checkpoint / resume ------------------------------------------------------------------
+// A checkpoint holds the state that one coupled step carries into the next:
+// the PDFs as stored (canonical layout, plane q of cell x holding f_q(x),
+// whatever the AA parity), eps_f, the f_pf applied in the last step, the
+// fluid velocity of the last step (Du_f/Dt), the current particle set (all
+// planes in cell-sorted order, u at the last subcycle start included), the
+// counters and status, and the host-side box state (step count, closure,
+// subcycle history flags, parity).  Everything else is re-derived on load by
+// the linked-cell sort of Algorithm 1's initialisation, which on an already
+// sorted set reproduces the neighbour lists, float copies and kernel
+// weights bit for bit.
+struct CkptHeader {
+    char magic[8];
+    int version, precision;
+    int n[3], per[3];
+    double tau, rho_f;
+    long long np, steps;
+    int parity, have_uprev, have_usub, sticky;
+    int have_closure, prepared;
+    double sumV, sumWb, dmax, dmin;
+    dps_closure cl;
+};
+static const char CKPT_MAGIC[8] = {'D', 'P', 'S', 'C', 'K', 'P', 'T', '1'};
+
+static size_t box_state_bytes(const Batch *B, const BoxHost *h) {
+    const size_t N = (size_t)h->d.g.ncell, np = (size_t)h->d.np;
+    return sizeof(CkptHeader) + 19 * N * B->pdf_elem + 7 * N * B->fel + np * ((size_t)NPF * 8 + (size_t)NPI * 4) +
+           8 * CNT_N + 8;
+}
+
+static int box_save_state(Batch *B, BoxHost *h, void *buf, size_t cap) {
+    if (!buf) FAILB(B, DPS_ERR_ARG, "null buffer");
+    const size_t need = box_state_bytes(B, h);
+    if (cap < need) FAILB(B, DPS_ERR_ARG, "buffer of %zu bytes, the state needs %zu", cap, need);
+    int rc = pull_state(B);
+    if (rc) return rc;
+    const BoxDev &d = h->d;
+    const size_t N = (size_t)d.g.ncell, np = (size_t)d.np, cp = (size_t)d.cap;
+    CkptHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, CKPT_MAGIC, 8);
+    hd.version = 1;
+    hd.precision = B->prec;
+    for (int a = 0; a < 3; ++a) {
+        hd.n[a] = d.g.n[a];
+        hd.per[a] = d.g.per[a];
+    }
+    hd.tau = h->tau;
+    hd.rho_f = h->rho_f;
+    hd.np = d.np;
+    hd.steps = h->steps;
+    hd.parity = B->parity;
+    hd.have_uprev = d.have_uprev;
+    hd.have_usub = d.have_usub;
+    hd.sticky = h->sticky;
+    hd.have_closure = h->have_closure;
+    hd.prepared = h->prepared;
+    hd.sumV = h->sumV;
+    hd.sumWb = h->sumWb;
+    hd.dmax = h->dmax;
+    hd.dmin = h->dmin;
+    hd.cl = h->cl;
+    char *o = (char *)buf;
+    std::memcpy(o, &hd, sizeof(hd));
+    o += sizeof(hd);
+    const size_t pdf_bytes = 19 * N * B->pdf_elem;
+    cudaStream_t s = B->stream;
+    if (B->parity) {
+        void *tmp = nullptr;
+        CKB(B, cudaMallocAsync(&tmp, pdf_bytes, s));
+        launch_pdf_relayout(d.pdf, d.g, (int)B->pdf_elem, 1, tmp, s);
+        CKB(B, cudaMemcpyAsync(o, tmp, pdf_bytes, cudaMemcpyDeviceToHost, s));
+        CKB(B, cudaFreeAsync(tmp, s));
+    } else {
+        CKB(B, cudaMemcpyAsync(o, d.pdf, pdf_bytes, cudaMemcpyDeviceToHost, s));
+    }
+    o += pdf_bytes;
+    CKB(B, cudaMemcpyAsync(o, d.eps, N * B->fel, cudaMemcpyDeviceToHost, s));
+    o += N * B->fel;
+    CKB(B, cudaMemcpyAsync(o, d.fpf, 3 * N * B->fel, cudaMemcpyDeviceToHost, s));
+    o += 3 * N * B->fel;
+    CKB(B, cudaMemcpyAsync(o, d.uprev, 3 * N * B->fel, cudaMemcpyDeviceToHost, s));
+    o += 3 * N * B->fel;
+    if (np) {
+        CKB(B, cudaMemcpy2DAsync(o, np * 8, d.pf[d.cur], cp * 8, np * 8, NPF, cudaMemcpyDeviceToHost, s));
+        o += (size_t)NPF * np * 8;
+        CKB(B, cudaMemcpy2DAsync(o, np * 4, d.pi[d.cur], cp * 4, np * 4, NPI, cudaMemcpyDeviceToHost, s));
+        o += (size_t)NPI * np * 4;
+    }
+    CKB(B, cudaMemcpyAsync(o, d.counters, 8 * CNT_N, cudaMemcpyDeviceToHost, s));
+    o += 8 * CNT_N;
+    std::memset(o, 0, 8);
+    CKB(B, cudaMemcpyAsync(o, d.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKB(B, cudaStreamSynchronize(s));
+    return DPS_OK;
+}
+
+// restore a checkpoint into box h, which has the geometry, fluid and form of
+// the saved box and room for its particles
+static int box_load_state(Batch *B, BoxHost *h, const void *buf, size_t size) {
+    if (!buf || size < sizeof(CkptHeader)) FAILB(B, DPS_ERR_ARG, "not a checkpoint (too short)");
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, CKPT_MAGIC, 8) != 0 || hd.version != 1) FAILB(B, DPS_ERR_ARG, "not a checkpoint");
+    BoxDev &d = h->d;
+    if (hd.precision != B->prec) FAILB(B, DPS_ERR_ARG, "checkpoint precision form %d, box %d", hd.precision, B->prec);
+    for (int a = 0; a < 3; ++a)
+        if (hd.n[a] != d.g.n[a] || (hd.per[a] != 0) != (d.g.per[a] != 0))
+            FAILB(B, DPS_ERR_ARG, "checkpoint lattice or boundaries differ from the box");
+    if (hd.tau != h->tau || hd.rho_f != h->rho_f) FAILB(B, DPS_ERR_ARG, "checkpoint tau or rho_f differ from the box");
+    if (hd.np < 0 || hd.np > h->max_particles)
+        FAILB(B, DPS_ERR_ARG, "checkpoint holds %lld particles, the box has room for %lld", hd.np, h->max_particles);
+    if (hd.have_closure) {
+        int rc = check_closure(B, &hd.cl);
+        if (rc) return rc;
+    }
+    int rc = pull_state(B);
+    if (rc) return rc;
+    const size_t N = (size_t)d.g.ncell, np = (size_t)hd.np, cp = (size_t)d.cap;
+    h->d.np = hd.np;
+    if (box_state_bytes(B, h) > size) {
+        h->d.np = 0;
+        FAILB(B, DPS_ERR_ARG, "checkpoint truncated (%zu bytes)", size);
+    }
+    h->sumV = hd.sumV;
+    h->sumWb = hd.sumWb;
+    h->dmax = hd.dmax;
+    h->dmin = hd.dmin;
+    h->cl = hd.cl;
+    h->have_closure = hd.have_closure != 0;
+    h->steps = hd.steps;
+    h->sticky = hd.sticky;
+    const char *in = (const char *)buf + sizeof(hd);
+    const size_t pdf_bytes = 19 * N * B->pdf_elem;
+    const char *in_pdf = in;
+    const char *in_fields = in + pdf_bytes;
+    const char *in_part = in_fields + 7 * N * B->fel;
+    const char *in_tail = in_part + np * ((size_t)NPF * 8 + (size_t)NPI * 4);
+    cudaStream_t s = B->stream;
+    // the particle set first: the initialisation sort below re-derives the
+    // linked cells, lists, float copies and weights from it
+    if (np) {
+        CKB(B, cudaMemcpy2DAsync(d.pf[d.cur], cp * 8, in_part, np * 8, np * 8, NPF, cudaMemcpyHostToDevice, s));
+        CKB(B, cudaMemcpy2DAsync(d.pi[d.cur], cp * 4, in_part + (size_t)NPF * np * 8, np * 4, np * 4, NPI,
+                                 cudaMemcpyHostToDevice, s));
+    }
+    CKB(B, cudaStreamSynchronize(s));
+    h->prepared = false;
+    B->layout_dirty = true;
+    if (h->have_closure && hd.prepared) {
+        if ((rc = ready(B))) return rc;
+    }
+    // subcycle history flags and the AA parity of the saved step
+    if ((rc = pull_state(B))) return rc;
+    d.have_uprev = hd.have_uprev;
+    d.have_usub = hd.have_usub;
+    if (B->boxes.size() == 1) B->parity = hd.parity;
+    if ((rc = push_layout(B))) return rc;
+    if (B->parity) {
+        void *tmp = nullptr;
+        CKB(B, cudaMallocAsync(&tmp, pdf_bytes, s));
+        CKB(B, cudaMemcpyAsync(tmp, in_pdf, pdf_bytes, cudaMemcpyHostToDevice, s));
+        launch_pdf_relayout(tmp, d.g, (int)B->pdf_elem, 0, d.pdf, s);
+        CKB(B, cudaFreeAsync(tmp, s));
+    } else {
+        CKB(B, cudaMemcpyAsync(d.pdf, in_pdf, pdf_bytes, cudaMemcpyHostToDevice, s));
+    }
+    CKB(B, cudaMemcpyAsync(d.eps, in_fields, N * B->fel, cudaMemcpyHostToDevice, s));
+    CKB(B, cudaMemcpyAsync(d.fpf, in_fields + N * B->fel, 3 * N * B->fel, cudaMemcpyHostToDevice, s));
+    CKB(B, cudaMemcpyAsync(d.uprev, in_fields + 4 * N * B->fel, 3 * N * B->fel, cudaMemcpyHostToDevice, s));
+    CKB(B, cudaMemcpyAsync(d.counters, in_tail, 8 * CNT_N, cudaMemcpyHostToDevice, s));
+    CKB(B, cudaMemcpyAsync(d.status, in_tail + 8 * CNT_N, sizeof(int), cudaMemcpyHostToDevice, s));
+    CKB(B, cudaStreamSynchronize(s));
+    h->prepared = hd.prepared != 0 && h->have_closure;
+    invalidate_graph(B);
+    return DPS_OK;
+}
+
 // ===============================================================================================
 // domain = batch of one box
 // ===============================================================================================
@@ -1387,6 +1566,22 @@ int dps_stats_get(dps_handle h, dps_stats *s) {
     return box_stats(&h->B, h->box, s);
 }
 
+int dps_state_size(dps_handle h, size_t *bytes) {
+    if (!h || !bytes) return DPS_ERR_ARG;
+    *bytes = box_state_bytes(&h->B, h->box);
+    return DPS_OK;
+}
+
+int dps_save_state(dps_handle h, void *buf, size_t cap) {
+    if (!h) return DPS_ERR_ARG;
+    return box_save_state(&h->B, h->box, buf, cap);
+}
+
+int dps_load_state(dps_handle h, const void *buf, size_t size) {
+    if (!h) return DPS_ERR_ARG;
+    return box_load_state(&h->B, h->box, buf, size);
+}
+
 int dps_read_cell_list(dps_handle h, int32_t *cell_start, int32_t *order, int64_t cap_cells, int64_t cap_particles) {
     if (!h || !cell_start || !order) return DPS_ERR_ARG;
     Batch *B = &h->B;
@@ -1397,6 +1592,36 @@ int dps_read_cell_list(dps_handle h, int32_t *cell_start, int32_t *order, int64_
     const BoxDev &d = h->box->d;
     CKB(B, cudaMemcpy(cell_start, d.cell_start, 4 * (d.g.ncell + 1), cudaMemcpyDeviceToHost));
     if (d.np) CKB(B, cudaMemcpy(order, d.pi[d.cur] + IID * d.cap, 4 * d.np, cudaMemcpyDeviceToHost));
+    return DPS_OK;
+}
+
+int dps_read_neighbor_list(dps_handle h, int64_t *offsets, int32_t *partners, int64_t cap) {
+    if (!h || !offsets) return DPS_ERR_ARG;
+    Batch *B = &h->B;
+    int rc = h->box->have_closure && !h->box->prepared ? ready(B) : pull_state(B);
+    if (rc) return rc;
+    const BoxDev &d = h->box->d;
+    const long long np = d.np;
+    if (np == 0 || !d.nlist) {
+        for (long long i = 0; i <= np; ++i) offsets[i] = 0;
+        return DPS_OK;
+    }
+    std::vector<int> cnt((size_t)np), ids((size_t)np), rows((size_t)np * d.maxn);
+    CKB(B, cudaMemcpy(cnt.data(), d.nlist_n, 4 * np, cudaMemcpyDeviceToHost));
+    CKB(B, cudaMemcpy(ids.data(), d.pi[d.cur] + IID * d.cap, 4 * np, cudaMemcpyDeviceToHost));
+    CKB(B, cudaMemcpy(rows.data(), d.nlist, 4 * (size_t)np * d.maxn, cudaMemcpyDeviceToHost));
+    // rows by insertion id, partners as insertion ids in ascending order
+    std::vector<long long> len((size_t)np, 0);
+    for (long long s = 0; s < np; ++s) len[ids[s]] = cnt[s];
+    offsets[0] = 0;
+    for (long long i = 0; i < np; ++i) offsets[i + 1] = offsets[i] + len[i];
+    if (!partners) return DPS_OK;
+    if (cap < offsets[np]) FAILB(B, DPS_ERR_ARG, "capacity %lld < %lld list entries", (long long)cap, (long long)offsets[np]);
+    for (long long s = 0; s < np; ++s) {
+        int32_t *o = partners + offsets[ids[s]];
+        for (int k = 0; k < cnt[s]; ++k) o[k] = ids[rows[(size_t)s * d.maxn + k]];
+        std::sort(o, o + cnt[s]);
+    }
     return DPS_OK;
 }
 
@@ -1593,6 +1818,22 @@ int dps_batch_particle_mean(dps_batch b, int id, double u[3]) {
     for (int a = 0; a < 3; ++a) u[a] = d.np ? pt[3 + a] / d.np : 0.0;
     return DPS_OK;
 }
+int dps_batch_state_size(dps_batch b, int id, size_t *bytes) {
+    if (!b || !bytes) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    *bytes = box_state_bytes(&b->B, h);
+    return DPS_OK;
+}
+int dps_batch_save_box(dps_batch b, int id, void *buf, size_t cap) {
+    if (!b) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    return box_save_state(&b->B, h, buf, cap);
+}
+int dps_batch_load_box(dps_batch b, int id, const void *buf, size_t size) {
+    if (!b) return DPS_ERR_ARG;
+    BOX_OR_FAIL(b, id, h);
+    return box_load_state(&b->B, h, buf, size);
+}
 int dps_batch_num_boxes(dps_batch b, int *n) {
     if (!b || !n) return DPS_ERR_ARG;
     *n = (int)b->B.boxes.size();
@@ -1740,8 +1981,14 @@ int dps_op_cell_sort(const int n[3], const int periodic[3], int B, int64_t np, c
     cudaMemsetAsync(fill, 0, sizeof(int) * N, s);
     launch_sort_scatter(key, np, cell_start, fill, tmp, s);
     launch_sort_rank(key, ids, np, cell_start, tmp, np > 0 ? order : perm, s);
+    int st = 0;
+    const cudaError_t ec = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(scr, s);
-    return cudaGetLastError() == cudaSuccess ? DPS_OK : DPS_ERR_CUDA;
+    if (ec != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return DPS_ERR_CUDA;
+    }
+    return (st & ST_BAD_CELL) ? DPS_ERR_ARG : DPS_OK;
 }
 
 }  // extern "C"

@@ -90,13 +90,18 @@ __device__ __forceinline__ void axis_weights_f(double x, int L, int periodic, fl
 }
 
 // ---- S1: sort ----------------------------------------------------------------
-// key = containing cell of x (current position arrays given separately)
+// key = containing cell of x (current position arrays given separately).  The
+// op entry points take positions from the caller: any coordinate outside
+// [0, n) (or not finite) on any axis is flagged ST_BAD_CELL; it is counted in
+// the clamped edge cell, and the op reports the flag as an argument error.
 __global__ void k_sort_count(const double *__restrict__ px, const double *__restrict__ py,
                              const double *__restrict__ pz, long long stride, long long np, Geom g,
                              int *__restrict__ count, int *__restrict__ key, int *status) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
          i += (long long)gridDim.x * blockDim.x) {
-        long long c = particle_cell(g, px[i * stride], py[i * stride], pz[i * stride], status);
+        const double x = px[i * stride], y = py[i * stride], z = pz[i * stride];
+        if (!(x >= 0.0 && x < g.n[0] && y >= 0.0 && y < g.n[1] && z >= 0.0 && z < g.n[2])) atomicOr(status, ST_BAD_CELL);
+        long long c = particle_cell(g, x, y, z, nullptr);
         key[i] = (int)c;
         atomicAdd(&count[c], 1);
     }
@@ -112,7 +117,9 @@ __global__ void k_sort_scatter(const int *__restrict__ key, long long np, const 
     }
 }
 
-// rank each particle inside its cell by id: final slot = segment start + rank
+// rank each particle inside its cell by (id, input index): final slot =
+// segment start + rank; equal ids keep their input order, so every slot of
+// the segment is written exactly once
 __global__ void k_sort_rank(const int *__restrict__ key, const int *__restrict__ ids, long long np,
                             const int *__restrict__ cell_start, const int *__restrict__ tmp,
                             int *__restrict__ perm) {
@@ -121,7 +128,10 @@ __global__ void k_sort_rank(const int *__restrict__ key, const int *__restrict__
         int k = key[i];
         int s = cell_start[k], e = cell_start[k + 1];
         int my = ids[i], r = 0;
-        for (int t = s; t < e; ++t) r += ids[tmp[t]] < my;
+        for (int t = s; t < e; ++t) {
+            const int o = tmp[t], io = ids[o];
+            r += io < my || (io == my && o < i);
+        }
         perm[s + r] = (int)i;
     }
 }

@@ -216,7 +216,53 @@ __global__ void k_particles_import(double *__restrict__ base, int plane, long lo
     }
 }
 
+// ---- checkpoint layout of the PDFs -------------------------------------------------------
+// Raw re-layout between the odd AA parity and the canonical layout (plane q
+// of cell x holds f_q(x)), copying the stored bits (E: an unsigned type of
+// the storage size, so no value is converted).  At odd parity f_q(x) sits in
+// plane opp(q) of x - c_q, or in plane q of x itself when x - c_q lies beyond
+// a wall (its bounced value).  TO_CANON = 1: odd -> canonical, 0: back.
+template <typename E, int TO_CANON>
+__global__ void k_pdf_relayout(const E *__restrict__ in, Geom g, E *__restrict__ out) {
+    const long long N = g.ncell;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        cell_coords(g, c, ix, iy, iz);
+        const NbDelta D = neighbour_deltas(g, ix, iy, iz);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            long long odd = (long long)q * N + c;
+            if (q != 0) {
+                const int dx = D.d[0][-CX(q) + 1], dy = D.d[1][-CY(q) + 1], dz = D.d[2][-CZ(q) + 1];
+                if (dx != INV && dy != INV && dz != INV) odd = (long long)OPP(q) * N + c + dx + dy + dz;
+            }
+            const long long canon = (long long)q * N + c;
+            if (TO_CANON)
+                out[canon] = in[odd];
+            else
+                out[odd] = in[canon];
+        }
+    }
+}
+
 // ---- launchers ---------------------------------------------------------------------------
+// elem: bytes per stored PDF value (8, 4 or 2); out of place
+void launch_pdf_relayout(const void *in, const Geom &g, int elem, int to_canon, void *out, cudaStream_t s) {
+    const int grid = grid_for(g.ncell, 256);
+#define DPS_RELAYOUT(E)                                                                              \
+    if (to_canon) k_pdf_relayout<E, 1><<<grid, 256, 0, s>>>((const E *)in, g, (E *)out);           \
+    else k_pdf_relayout<E, 0><<<grid, 256, 0, s>>>((const E *)in, g, (E *)out);
+    if (elem == 8) {
+        DPS_RELAYOUT(unsigned long long)
+    } else if (elem == 4) {
+        DPS_RELAYOUT(unsigned int)
+    } else {
+        DPS_RELAYOUT(unsigned short)
+    }
+#undef DPS_RELAYOUT
+}
+
 template <typename ST>
 void launch_pdf_rest(void *pdf, long long N, cudaStream_t s) {
     k_pdf_rest<ST><<<grid_for(N, 256), 256, 0, s>>>((ST *)pdf, N);

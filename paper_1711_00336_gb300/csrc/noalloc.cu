@@ -92,5 +92,13 @@ extern "C" int dps_op_cell_sort_noalloc(const int n[3], const int periodic[3], i
     cudaMemsetAsync(fill, 0, sizeof(int) * N, s);
     launch_sort_scatter(key, np, cell_start, fill, tmp, s);
     launch_sort_rank(key, ids, np, cell_start, tmp, np > 0 ? order : perm, s);
-    return cudaGetLastError() == cudaSuccess ? DPS_OK : DPS_ERR_CUDA;
+    // a host int is pageable memory: the copy allocates nothing and the
+    // synchronisation that follows makes the status readable
+    int st = 0;
+    if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return DPS_ERR_CUDA;
+    }
+    return (st & ST_BAD_CELL) ? DPS_ERR_ARG : DPS_OK;
 }

@@ -99,6 +99,10 @@ def lib():
         L.dps_collect_timing.argtypes = [ctypes.c_void_p]
         L.dps_get_timing.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         L.dps_launches_per_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+        L.dps_read_neighbor_list.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), _I32P, ctypes.c_int64]
+        L.dps_state_size.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+        L.dps_save_state.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+        L.dps_load_state.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
         L.dps_op_cell_sort.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]
@@ -315,6 +319,30 @@ class Domain:
             out[name] = np.array(list(v)) if hasattr(v, "__len__") else v
         return out
 
+    def read_neighbor_list(self):
+        """DEM neighbour list (dps_read_neighbor_list): CSR (offsets[np+1], partners)."""
+        off = np.zeros(self.np + 1, np.int64)
+        op = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        self._ck(lib().dps_read_neighbor_list(self.h, op, None, 0))
+        part = np.zeros(max(int(off[-1]), 1), np.int32)
+        self._ck(lib().dps_read_neighbor_list(self.h, op, part.ctypes.data_as(_I32P), part.size))
+        return off, part[:int(off[-1])]
+
+    def save_state(self):
+        """Checkpoint of the domain (dps_save_state) as a uint8 numpy array."""
+        n = ctypes.c_size_t()
+        self._ck(lib().dps_state_size(self.h, ctypes.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        self._ck(lib().dps_save_state(self.h, ctypes.c_void_p(buf.ctypes.data), buf.size))
+        return buf
+
+    def load_state(self, buf):
+        """Restore a checkpoint written by save_state (dps_load_state)."""
+        buf = np.ascontiguousarray(np.asarray(buf, np.uint8))
+        self._ck(lib().dps_load_state(self.h, ctypes.c_void_p(buf.ctypes.data), buf.size))
+        st = self.stats()
+        self.np = int(st["n_particles"])
+
     def read_cell_list(self):
         cs = np.zeros(self.ncell + 1, np.int32)
         order = np.zeros(max(self.np, 1), np.int32)
@@ -378,6 +406,9 @@ def _declare_batch(L):
     L.dps_batch_collect_timing.argtypes = [vp]
     L.dps_batch_get_timing.argtypes = [vp, vp, vp, ctypes.c_int]
     L.dps_batch_launches_per_step.argtypes = [vp, ctypes.POINTER(i64)]
+    L.dps_batch_state_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.dps_batch_save_box.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t]
+    L.dps_batch_load_box.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t]
     L.dps_box_bytes.argtypes = [ctypes.c_int, ip3, i64, ctypes.POINTER(ctypes.c_size_t)]
     L.dps_serve_create.argtypes = [ctypes.POINTER(ServeDesc), ctypes.POINTER(vp)]
     L.dps_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(i64)]
@@ -434,6 +465,20 @@ class Batch:
                                          int(max_particles), ctypes.byref(b)))
         self.boxes[b.value] = dict(n=tuple(n), np=0)
         return b.value
+
+    def save_box(self, box):
+        """Checkpoint of one box (dps_batch_save_box) as a uint8 numpy array."""
+        n = ctypes.c_size_t()
+        self._ck(lib().dps_batch_state_size(self.h, int(box), ctypes.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        self._ck(lib().dps_batch_save_box(self.h, int(box), ctypes.c_void_p(buf.ctypes.data), buf.size))
+        return buf
+
+    def load_box(self, box, buf):
+        """Restore a checkpoint into an existing box of the same geometry (dps_batch_load_box)."""
+        buf = np.ascontiguousarray(np.asarray(buf, np.uint8))
+        self._ck(lib().dps_batch_load_box(self.h, int(box), ctypes.c_void_p(buf.ctypes.data), buf.size))
+        self.boxes[box]["np"] = int(self.stats(box)["n_particles"])
 
     def remove_box(self, box):
         self._ck(lib().dps_batch_remove_box(self.h, int(box)))
