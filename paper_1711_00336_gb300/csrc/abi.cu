@@ -54,7 +54,7 @@ void launch_reaction_am(const BoxDev *, const Tile *, int, int, int, cudaStream_
 template <typename FT>
 void launch_reaction_drag(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
 void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, int, int, int, cudaStream_t);
-void launch_build_nlist(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
+void launch_build_nlist(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 long long scan_scratch_words(long long);
 void exclusive_scan(const int *, long long, int *, int *, cudaStream_t);
 template <typename ST>
@@ -520,9 +520,11 @@ static void enqueue_sort_eps(Batch *B, int xsel, int mark_usub, bool have_keys) 
                             B->stream);
     }
     launch_bsort_flip(B->d_table, nb, mark_usub, B->stream);
+    const int pairs = B->prec == DPS_F64;  // the FP64 form evaluates each pair once
     if (pl)
-        launch_build_nlist(T, B->d_part, B->n_part, grid_of(B->n_part), part_threads(u, B->cpl_lanes), B->stream);
-    tend(B, PH_SORT, cnt + 3 + 3 * pl + 1 + pl);
+        launch_build_nlist(T, B->d_part, B->n_part, grid_of(B->n_part), part_threads(u, B->cpl_lanes), pairs,
+                           B->stream);
+    tend(B, PH_SORT, cnt + 3 + 3 * pl + 1 + pl * (1 + 2 * pairs));
     tbegin(B);
     if (B->fel == 8)
         launch_eps<double>(T, B->d_brick, B->n_brick, grid_of(B->n_brick), 256, B->stream);
@@ -609,7 +611,7 @@ static void enqueue_step(Batch *B) {
                                         : part_threads(u, 1 << c);
                     launch_dem_substep(T, B->d_part + B->part_off[c], nt, sd & 1, sd == B->n_dem - 1,
                                        B->prec != DPS_F64, 1 << c, grid_of(nt), blk, s);
-                    ++ndl;
+                    ndl += B->prec == DPS_F64 ? 2 : 1;  // FP64: pair kernel + gather kernel
                 }
         tend(B, PH_DEM, ndl);
         if (fork) cudaStreamWaitEvent(s, B->ev_join, 0);
@@ -669,17 +671,42 @@ static int list_capacity(const BoxHost *h) {
     return (int)std::fmax(1.0, std::fmin(n, 1024.0));
 }
 
+static void box_release(Batch *B, BoxHost *h, void *p) {
+    if (!p) return;
+    dfree_raw(B, p);
+    h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
+}
+
+// the pair slots of the FP64 form: every unordered pair of the list once;
+// the list holds at most maxn partners per particle, so at most cap*maxn/2
+// pairs
+static long long pair_capacity(const BoxHost *h, int maxn) { return (long long)h->d.cap * maxn / 2 + 1; }
+
 static int ensure_lists(Batch *B) {
     for (BoxHost *h : B->boxes) {
         const int need = list_capacity(h);
         if (need <= h->d.maxn && h->d.nlist) continue;
-        void *p = box_alloc(B, h, (size_t)need * (size_t)h->d.cap * 4);
+        const size_t C = (size_t)h->d.cap;
+        void *p = box_alloc(B, h, (size_t)need * C * 4);
         if (!p) FAILB(B, DPS_ERR_OOM, "neighbour list allocation failed");
-        if (h->d.nlist) {
-            dfree_raw(B, h->d.nlist);
-            h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void *)h->d.nlist), h->allocs.end());
-        }
+        box_release(B, h, h->d.nlist);
         h->d.nlist = (int *)p;
+        if (B->prec == DPS_F64) {
+            const long long pc = pair_capacity(h, need);
+            if (pc >= (1LL << 31)) FAILB(B, DPS_ERR_ARG, "too many neighbour pairs for one box (%lld)", pc);
+            void *hj = box_alloc(B, h, (size_t)pc * 4), *rr = box_alloc(B, h, (size_t)need * C * 4);
+            void *pr = box_alloc(B, h, (size_t)pc * 48), *pg = box_alloc(B, h, (size_t)pc);
+            if (!hj || !rr || !pr || !pg) FAILB(B, DPS_ERR_OOM, "pair list allocation failed");
+            box_release(B, h, h->d.hj);
+            box_release(B, h, h->d.rrow);
+            box_release(B, h, h->d.pres);
+            box_release(B, h, h->d.pflag);
+            h->d.hj = (int *)hj;
+            h->d.rrow = (int *)rr;
+            h->d.pres = (double *)pr;
+            h->d.pflag = (unsigned char *)pg;
+            h->d.pcap = pc;
+        }
         h->d.maxn = need;
         B->layout_dirty = true;
     }
@@ -821,7 +848,8 @@ static size_t box_bytes(int prec, long long ncell, long long cap) {
     size_t pe = prec == DPS_F64 ? 8 : (prec == DPS_F32 ? 4 : 2), fe = prec == DPS_F64 ? 8 : 4;
     size_t N = (size_t)ncell, C = (size_t)(cap > 0 ? cap : 1);
     size_t b = 19 * N * pe + 27 * N * fe;
-    b += 2 * (size_t)NPF * C * 8 + 2 * (size_t)NPI * C * 4 + 9 * C * 8 + 6 * C * 16 + C * 4 + 64 * C * 4 + 15 * C * 4;
+    b += 2 * (size_t)NPF * C * 8 + 2 * (size_t)NPI * C * 4 + 9 * C * 8 + 6 * C * 16 + C * 4 + 64 * C * 4 + 18 * C * 4;
+    if (prec == DPS_F64) b += 64 * C * 4 + 32 * C * (4 + 48 + 1);  // pair lists and results (64 partners)
     b += (3 * N + 1) * 4 + 3 * C * 4 + ((N + 8191) / 8192 + 1) * 4;
     b += 4096 + (size_t)reduce_partials_doubles() * 8;
     return b;
@@ -881,6 +909,14 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
     d.f32p = d.lowp ? (float *)A(6 * cap * 4) : nullptr;
     d.nlist = nullptr;  // sized at preparation (depends on the closure)
     d.maxn = 0;
+    d.hj = d.rrow = nullptr;
+    d.pres = nullptr;
+    d.pflag = nullptr;
+    d.pcap = 0;
+    d.hoff = (int *)A(cap * 4);
+    d.hn = (int *)A(cap * 4);
+    d.rn = (int *)A(cap * 4);
+    d.ptop = (unsigned long long *)A(16);
     d.cell_start = (int *)A((N + 1) * 4);
     d.count = (int *)A(N * 4);
     d.fill = (int *)A(N * 4);
@@ -913,6 +949,8 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
     cudaMemsetAsync(d.rho, 0, N * B->fel, s);
     cudaMemsetAsync(d.ire, 0, N * B->fel, s);
     cudaMemsetAsync(d.nlist_n, 0, cap * 4, s);
+    for (int *z : {d.hoff, d.hn, d.rn}) cudaMemsetAsync(z, 0, cap * 4, s);
+    cudaMemsetAsync(d.ptop, 0, 16, s);
     for (int k = 0; k < 2; ++k) {
         cudaMemsetAsync(d.xf[k], 0, cap * 16, s);
         cudaMemsetAsync(d.vf[k], 0, cap * 16, s);
@@ -1669,7 +1707,8 @@ static long long b_launches_per_step(Batch *B) {
     const int pl = np > 0;
     const int n_int = B->boxes.empty() ? 1 : B->boxes[0]->cl.n_int;
     const int n_dem = B->boxes.empty() ? 1 : B->boxes[0]->cl.n_dem;
-    return 2 + 2 + (long long)n_int * (2 * pl + 2 + pl * n_dem + 3 + 5 * pl + 1 + 1);
+    const int f64 = B->prec == DPS_F64;
+    return 2 + 2 + (long long)n_int * (2 * pl + 2 + pl * n_dem * (1 + f64) + 3 + (5 + 2 * f64) * pl + 1 + 1);
 }
 
 int dps_set_timing(dps_handle h, int enable) { return h ? b_set_timing(&h->B, enable) : DPS_ERR_ARG; }

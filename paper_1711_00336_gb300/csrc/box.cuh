@@ -29,9 +29,21 @@ struct BoxDev {
     float4 *xf[2];     // float (x, y, z, d) of the current set / of the ping-pong planes
     float4 *vf[2];     // float (u, m) likewise
     float4 *of[2];     // float (omega, 0) likewise
-    int *nlist;        // Verlet list, k-major: nlist[k*cap + i]
+    int *nlist;        // Verlet list, row by row: nlist[i*maxn + k]
     int *nlist_n;      // list length per particle
     int maxn;          // list capacity per particle
+    // FP64 form: the list as unordered pairs, each evaluated once per
+    // substep (Newton's third law).  Particle i owns the pairs with its
+    // partners j > i: hn[i] of them, in ascending j, at slots hoff[i] ...
+    // (hj: the partner of a slot; slots are allocated per block from *ptop).
+    // rn[i] / rrow[i*maxn + r]: the slots of the pairs (k, i), k < i, in
+    // ascending k.  pres[6 s ...]: force on the owner and n x F_t of slot s;
+    // pflag[s]: the pair passed the screen of this substep.
+    int *hj, *hoff, *hn, *rrow, *rn;
+    double *pres;
+    unsigned char *pflag;
+    unsigned long long *ptop;
+    long long pcap;    // slots
     int lowp;          // 1: low-precision form (FP32 coupling arithmetic)
     float *pwf;        // FP32 kernel weights [9][cap] (low-precision forms)
     float *f32p;       // FP32 copies of F_am (3 planes) and F_d (3 planes) [6][cap]

@@ -264,6 +264,7 @@ __global__ void k_bsort_flip(BoxDev *boxes, int nboxes, int mark_usub) {
     if (b < nboxes) {
         boxes[b].cur ^= 1;
         if (mark_usub) boxes[b].have_usub = 1;
+        *boxes[b].ptop = 0;  // pair slots of the list built next
     }
 }
 

@@ -73,10 +73,12 @@ __device__ __forceinline__ PairPar<T> pair_par(const Phys &ph) {
 // spring-dashpot contact with Coulomb friction (Sec. 3.1.1) for overlap
 // delta > 0, in arithmetic T, accumulated in T; the torque is
 // (d_i/2) n x F_t (r x F at the contact point r = d_i/2 n).
+// lev: the lever of the torque, d_i/2 (or 1, which leaves n x F_t in Tq for
+// the pair kernel of the FP64 form: both partners take it times their d/2)
 template <typename T>
 __device__ __forceinline__ void contact_force(const PairPar<T> &ph, const T n[3], T delta, const T ui[3],
-                                              const T wi[3], T di, const T uj[3], const T wjh[3], T m_ij, T F[3],
-                                              T Tq[3]) {
+                                              const T wi[3], T di, const T uj[3], const T wjh[3], T m_ij, T lev,
+                                              T F[3], T Tq[3]) {
     // k_n and xi_n of Eqs. damping_to_stiffness / collision_time, solved
     // for the given e_n and T_c: both proportional to m_ij
     const T k_n = m_ij * ph.kfac;
@@ -107,7 +109,7 @@ __device__ __forceinline__ void contact_force(const PairPar<T> &ph, const T n[3]
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         F[a] += Fn[a] + Ft[a];
-        Tq[a] += T(0.5) * di * nF[a];
+        Tq[a] += lev * nF[a];
     }
 }
 
@@ -143,7 +145,7 @@ __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T di
                                         const T wi[3], T di, const T uj[3], const T wjh[3], T m_ij, T dmean, T F[3],
                                         T Tq[3], unsigned &nlim) {
     const T delta = sumr - dist;
-    if (ph.contact && delta > T(0)) contact_force(ph, n, delta, ui, wi, di, uj, wjh, m_ij, F, Tq);
+    if (ph.contact && delta > T(0)) contact_force(ph, n, delta, ui, wi, di, uj, wjh, m_ij, T(0.5) * di, F, Tq);
     const T h = dist - sumr;
     if (ph.lubrication && h >= T(0) && h < ph.h_c) {
         const T hh = m_max(h, ph.h_min);
@@ -309,7 +311,8 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
 __device__ __forceinline__ void pair64_body(const PairPar<double> &pd, const double *__restrict__ xin,
                                             const double *__restrict__ pf, long long cap, const Geom &g, long long j,
                                             const double xi[3], const double ui[3], const double wi[3], double di,
-                                            double mi, double rng_extra, double F[3], double T[3], unsigned &nlim) {
+                                            double mi, double rng_extra, double lev, double F[3], double T[3],
+                                            unsigned &nlim) {
     double n[3] = {0, 0, 0}, uj[3] = {0, 0, 0}, wjh[3] = {0, 0, 0};
     double dist, sumr, dj = 0.0, mj = 1.0;
     const bool wall = j < 0;
@@ -349,7 +352,7 @@ __device__ __forceinline__ void pair64_body(const PairPar<double> &pd, const dou
     const double A = wall ? mi : mi * mj, Bm = wall ? 1.0 : mi + mj;
     const double C = wall ? 2.0 * di : 2.0 * di * dj, D = wall ? 1.0 : di + dj;
     const double delta = sumr - dist;
-    if (pd.contact && delta > 0.0) contact_force(pd, n, delta, ui, wi, di, uj, wjh, A / Bm, F, T);
+    if (pd.contact && delta > 0.0) contact_force(pd, n, delta, ui, wi, di, uj, wjh, A / Bm, lev, F, T);
     const double h = dist - sumr;
     if (pd.lubrication && h >= 0.0 && h < pd.h_c) {
         const double hh = fmax(h, pd.h_min);
@@ -378,7 +381,7 @@ __device__ __noinline__ void pair64_out(const BoxDev &Bx, const double *__restri
     const double rng_extra = Bx.ph.lubrication ? fmax(Bx.ph.h_c, 0.0) : 0.0;
     const PairPar<double> pd = pair_par<double>(Bx.ph);
     const Geom g = Bx.g;
-    pair64_body(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, F, T, nlim);
+    pair64_body(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, 0.5 * di, F, T, nlim);
 }
 
 // one thread per particle: wall partners (WALLS; the FP64 form evaluates
@@ -607,32 +610,118 @@ __device__ __forceinline__ int block_excl_sum(int v, int *ws, int &total) {
     return r;
 }
 
-// FP64 form: the pairs of a block are compacted into a queue before the FP64
-// work.  Only a fraction of a particle's list entries pass the screen (at
-// low solid fractions well under one per particle), and an FP64 instruction
-// costs a warp the same whatever number of its lanes are active, so the
-// screened entries of all the block's particles are gathered and evaluated
-// one per thread.  Lane groups of LANES lanes screen a particle's list (FP32,
-// with a margin); lane 0 of the group adds the wall faces within reach.  A
-// block-wide exclusive sum over the threads places the entries (a particle's
-// entries contiguous, in the order lane 0 .. LANES-1, list order inside a
-// lane, walls after lane 0's list entries); the queue is taken in windows of
-// DQ_CAP entries, each evaluated by all threads and then added by lane 0 of
-// each group to its particle's sums, entry by entry in queue order.  A
-// particle's sum therefore depends on its own list and LANES only.
-constexpr int DQ_CAP = 384;
+// ---- FP64 form: every pair once (Newton's third law) ------------------------------
+// The FP64 pair chain is what bounds this form on GB300 (a dense settling box
+// keeps the FP64 pipe ~70 % busy), and the contact and lubrication laws of
+// Sec. 3.1.1 / 3.1.3 are antisymmetric: F_ji = -F_ij, and with n_ji = -n_ij,
+// F_t,ji = -F_t,ij the torques (d/2) n x F_t of both partners share n x F_t.
+// So each substep evaluates each pair of the neighbour list once and a second
+// kernel gathers, per particle and in a fixed order (its own pairs by
+// ascending partner, then the pairs owned by its lower partners by ascending
+// owner, then the walls), before the explicit update of Eq. particle_motion.
+
+// After the list build: the pairs particle i owns (partners j > i, ascending
+// j) get consecutive slots from a per-block allocation; its partners k < i
+// go to rrow (ascending k) until k_reverse_slots replaces them by the slots
+// of the pairs (k, i).  Ranks by counting keep the rows free of any sort.
+__global__ void __launch_bounds__(256) k_half_rows(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
+                                                   int ntiles) {
+    __shared__ int ws[9];
+    __shared__ unsigned long long sbase;
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &Bx = boxes[tl.box];
+        const int maxn = Bx.maxn;
+        for (long long base = tl.begin; base < tl.end; base += blockDim.x) {  // uniform trip count
+            const long long i = base + threadIdx.x;
+            const bool act = i < tl.end;
+            int nn = 0, nh = 0;
+            const int *row = Bx.nlist;
+            if (act) {
+                nn = min(Bx.nlist_n[i], maxn);
+                row = Bx.nlist + i * (long long)maxn;
+                for (int k = 0; k < nn; ++k) nh += row[k] > i;
+            }
+            int total;
+            const int off = block_excl_sum(nh, ws, total);
+            if (threadIdx.x == 0) sbase = atomicAdd(Bx.ptop, (unsigned long long)total);
+            __syncthreads();
+            const long long h0 = (long long)sbase + off;
+            __syncthreads();  // sbase is written again in the next round
+            if (!act) continue;
+            if (h0 + nh > Bx.pcap) {  // not reached: pcap bounds the pairs of any list
+                atomicOr(Bx.status, ST_NLIST);
+                Bx.hn[i] = Bx.rn[i] = 0;
+                continue;
+            }
+            Bx.hoff[i] = (int)h0;
+            Bx.hn[i] = nh;
+            Bx.rn[i] = nn - nh;
+            int *rr = Bx.rrow + i * (long long)maxn;
+            for (int k = 0; k < nn; ++k) {
+                const int j = row[k];
+                const bool up = j > i;
+                int r = 0;  // rank of j among the partners on its side of i
+                for (int m = 0; m < nn; ++m) {
+                    const int o = row[m];
+                    r += o < j && (up ? o > i : o < i);
+                }
+                if (up)
+                    Bx.hj[h0 + r] = j;
+                else
+                    rr[r] = j;
+            }
+        }
+    }
+}
+
+// rrow: lower partner k -> the slot of the pair (k, i) (binary search of i in
+// the ascending row of k)
+__global__ void __launch_bounds__(256) k_reverse_slots(const BoxDev *__restrict__ boxes,
+                                                       const Tile *__restrict__ tiles, int ntiles) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &Bx = boxes[tl.box];
+        for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            const int nr = Bx.rn[i];
+            int *rr = Bx.rrow + i * (long long)Bx.maxn;
+            for (int r = 0; r < nr; ++r) {
+                const int k = rr[r];
+                const int hk = Bx.hn[k], ok = Bx.hoff[k];
+                const int *h = Bx.hj + ok;
+                int lo = 0, hi = hk;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (h[mid] < i)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                if (lo < hk && h[lo] == i) {
+                    rr[r] = ok + lo;
+                } else {  // not reached: the list search is symmetric
+                    rr[r] = -1;
+                    atomicOr(Bx.status, ST_NLIST);
+                }
+            }
+        }
+    }
+}
+
+// The pairs of a substep.  Lane groups of LANES lanes screen the owned pairs
+// of a particle in FP32 (with a margin); a block-wide exclusive sum places the
+// entries that pass in a queue, evaluated one per thread by the exact FP64
+// contact / lubrication body (an FP64 instruction costs a warp the same
+// whatever number of its lanes are active), which writes the force on the
+// owner and n x F_t to the pair's slot.  Every owned slot gets its flag.
+constexpr int DQ_CAP = 512;
 
 template <int LANES>
-__global__ void __launch_bounds__(256, 1) k_dem_substep64(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
-                                                       int ntiles, int src_tmp, int key_out) {
-    __shared__ double sFT[6][DEM_CHUNK];
-    __shared__ unsigned sN[DEM_CHUNK];
-    __shared__ double qR[6][DQ_CAP];
-    __shared__ unsigned qN[DQ_CAP];
-    __shared__ int qJ[DQ_CAP], qP[DQ_CAP];
+__global__ void __launch_bounds__(256, 1) k_dem_pairs64(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
+                                                     int ntiles, int src_tmp) {
+    __shared__ int qS[DQ_CAP], qJ[DQ_CAP], qP[DQ_CAP];
     __shared__ int ws[9];
     const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
-    const int wl = threadIdx.x & 31;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &Bx = boxes[tl.box];
@@ -646,133 +735,136 @@ __global__ void __launch_bounds__(256, 1) k_dem_substep64(const BoxDev *__restri
         const float rng_extra_f = (float)rng_extra;
         const float Lf[3] = {(float)g.n[0], (float)g.n[1], (float)g.n[2]};
         const PairPar<double> pd = pair_par<double>(ph);
-        for (long long cb = tl.begin; cb < tl.end; cb += DEM_CHUNK) {
-            const long long ce = cb + DEM_CHUNK < tl.end ? cb + DEM_CHUNK : tl.end;
-            for (long long base = cb; base < ce; base += ngrp) {  // uniform trip count
-                const long long i = base + grp;
-                const bool act = i < ce;
-                float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-                int nn = 0;
-                const int *row = Bx.nlist;
-                if (act) {
-                    pi = fin[i];
-                    nn = Bx.nlist_n[i];
-                    row = Bx.nlist + i * (long long)Bx.maxn;
+        unsigned nlim = 0;
+        for (long long base = tl.begin; base < tl.end; base += ngrp) {  // uniform trip count
+            const long long i = base + grp;
+            const bool act = i < tl.end;
+            float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+            int nh = 0, h0 = 0;
+            if (act) {
+                pi = fin[i];
+                nh = Bx.hn[i];
+                h0 = Bx.hoff[i];
+            }
+            // the owned pairs of this lane (c = lane, lane + LANES, ...) that
+            // pass the FP32 screen, in order: fn(slot, j)
+            auto entries = [&](bool flag, auto &&fn) {
+                for (int c = lane; c < nh; c += LANES) {
+                    const int sl = h0 + c, j = Bx.hj[sl];
+                    const float4 pj = fin[j];
+                    const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
+                    const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
+                    const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
+                    const float fr = 0.5f * (pi.w + pj.w) + rng_extra_f + SCREEN_MARGIN;
+                    const bool pass = fx * fx + fy * fy + fz * fz < fr * fr;
+                    if (flag) Bx.pflag[sl] = pass;
+                    if (pass) fn(sl, j);
                 }
-                // the entries of this lane that pass the FP32 screen, in order:
-                // fn(j) for list entries k = lane, lane + LANES, ..., then (lane
-                // 0) the wall faces within reach as j = -1 - (2 axis + side)
-                auto entries = [&](auto &&fn) {
-                    for (int k = lane; k < nn; k += LANES) {
-                        const int j = row[k];
-                        const float4 pj = fin[j];
-                        const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
-                        const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
-                        const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
-                        const float fr = 0.5f * (pi.w + pj.w) + rng_extra_f + SCREEN_MARGIN;
-                        if (fx * fx + fy * fy + fz * fz < fr * fr) fn(j);
-                    }
-                    if (lane == 0) {
-                        const float pa[3] = {pi.x, pi.y, pi.z};
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            if (g.per[a]) continue;
-#pragma unroll
-                            for (int side = 0; side < 2; ++side) {
-                                const float dw = side == 0 ? pa[a] : Lf[a] - pa[a];
-                                if (dw < 0.5f * pi.w + rng_extra_f + SCREEN_MARGIN) fn(-1 - (2 * a + side));
-                            }
+            };
+            int cnt = 0;
+            if (act) entries(true, [&](int, int) { ++cnt; });
+            int M;
+            const int off = block_excl_sum(cnt, ws, M);
+            for (int w0 = 0; w0 < M; w0 += DQ_CAP) {
+                const int mw = M - w0 < DQ_CAP ? M - w0 : DQ_CAP;
+                if (act && off < w0 + mw && off + cnt > w0) {
+                    int c = off;
+                    entries(false, [&](int sl, int j) {
+                        // (c < off + cnt: both passes screen alike; the bound only
+                        // keeps a lane inside its own slots)
+                        if (c >= w0 && c < w0 + mw && c < off + cnt) {
+                            qS[c - w0] = sl;
+                            qJ[c - w0] = j;
+                            qP[c - w0] = (int)(i - tl.begin);
                         }
-                    }
-                };
-                int cnt = 0;
-                if (act) entries([&](int) { ++cnt; });
-                int M;
-                const int off = block_excl_sum(cnt, ws, M);
-                // the particle's entries: [gs, ge) of the queue
-                const int g0 = wl - lane;
-                const int gs = __shfl_sync(0xffffffffu, off, g0);
-                const int ge = __shfl_sync(0xffffffffu, off + cnt, g0 + LANES - 1);
-                double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-                unsigned nlim = 0;
-                for (int w0 = 0; w0 < M; w0 += DQ_CAP) {
-                    const int mw = M - w0 < DQ_CAP ? M - w0 : DQ_CAP;
-                    if (act && off < w0 + mw && off + cnt > w0) {
-                        int c = off;
-                        entries([&](int j) {
-                            // (c < off + cnt: the passes screen alike; the bound only
-                            // keeps a lane inside its own slots)
-                            if (c >= w0 && c < w0 + mw && c < off + cnt) {
-                                qJ[c - w0] = j;
-                                qP[c - w0] = (int)(i - cb);
-                            }
-                            ++c;
-                        });
-                    }
-                    __syncthreads();
-                    // one entry per thread: the FP64 contact / lubrication body
-                    for (int q = threadIdx.x; q < mw; q += blockDim.x) {
-                        const long long ii = cb + qP[q];
-                        double xi[3], ui[3], wi[3];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            xi[a] = xin[a * cap + ii];
-                            ui[a] = xin[(3 + a) * cap + ii];
-                            wi[a] = xin[(6 + a) * cap + ii];
-                        }
-                        double Fq[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
-                        unsigned nq = 0;
-                        pair64_body(pd, xin, pf, cap, g, qJ[q], xi, ui, wi, pf[PD * cap + ii], pf[PM * cap + ii],
-                                    rng_extra, Fq, Tq, nq);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            qR[a][q] = Fq[a];
-                            qR[3 + a][q] = Tq[a];
-                        }
-                        qN[q] = nq;
-                    }
-                    __syncthreads();
-                    if (act && lane == 0) {
-                        const int a0 = gs > w0 ? gs : w0, a1 = ge < w0 + mw ? ge : w0 + mw;
-                        for (int q = a0; q < a1; ++q) {
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                F[a] += qR[a][q - w0];
-                                T[a] += qR[3 + a][q - w0];
-                            }
-                            nlim += qN[q - w0];
-                        }
-                    }
-                    __syncthreads();  // the next window overwrites the queue
+                        ++c;
+                    });
                 }
-                if (act && lane == 0) {
-                    const int s = (int)(i - cb);
+                __syncthreads();
+                for (int q = threadIdx.x; q < mw; q += blockDim.x) {
+                    const long long ii = tl.begin + qP[q];
+                    double xi[3], ui[3], wi[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        sFT[a][s] = F[a];
-                        sFT[3 + a][s] = T[a];
+                        xi[a] = xin[a * cap + ii];
+                        ui[a] = xin[(3 + a) * cap + ii];
+                        wi[a] = xin[(6 + a) * cap + ii];
                     }
-                    sN[s] = nlim;
+                    double Fq[3] = {0, 0, 0}, Cq[3] = {0, 0, 0};
+                    pair64_body(pd, xin, pf, cap, g, qJ[q], xi, ui, wi, pf[PD * cap + ii], pf[PM * cap + ii],
+                                rng_extra, 1.0, Fq, Cq, nlim);
+                    double *r = Bx.pres + 6 * (long long)qS[q];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        r[a] = Fq[a];
+                        r[3 + a] = Cq[a];
+                    }
+                }
+                __syncthreads();  // the next window overwrites the queue
+            }
+        }
+        // each capped coefficient acts on both partners (the count of the
+        // per-particle evaluation of Sec. 3.1.3)
+        if (nlim) atomicAdd(&Bx.counters[CNT_LUB_LIMITED], 2ull * nlim);
+    }
+}
+
+// The sums of a substep and the update: one thread per particle adds the
+// forces of its owned pairs (ascending partner), minus those of the pairs its
+// lower partners own (ascending owner), each pair's n x F_t times d_i/2, then
+// the walls and Eq. particle_motion.  The order depends on the list alone.
+__global__ void __launch_bounds__(128) k_dem_gather64(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
+                                                     int ntiles, int src_tmp, int key_out) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &Bx = boxes[tl.box];
+        const double *pf = Bx.pf[Bx.cur];
+        const long long cap = Bx.cap;
+        const PairPar<double> pd = pair_par<double>(Bx.ph);
+        for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            const double lev = 0.5 * pf[PD * cap + i];
+            double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+            const int h0 = Bx.hoff[i], nh = Bx.hn[i];
+            for (int c = 0; c < nh; ++c) {
+                const long long sl = h0 + c;
+                if (!Bx.pflag[sl]) continue;
+                const double *r = Bx.pres + 6 * sl;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    F[a] += r[a];
+                    T[a] += lev * r[3 + a];
                 }
             }
-            __syncthreads();
-            // phase B: integration, one particle per thread (walls were entries)
-            for (long long i = cb + threadIdx.x; i < ce; i += blockDim.x) {
-                const int s = (int)(i - cb);
-                double F[3] = {sFT[0][s], sFT[1][s], sFT[2][s]}, T[3] = {sFT[3][s], sFT[4][s], sFT[5][s]};
-                finish_particle<false>(Bx, pd, i, src_tmp, F, T, sN[s], key_out);
+            const int nr = Bx.rn[i];
+            const int *rr = Bx.rrow + i * (long long)Bx.maxn;
+            for (int c = 0; c < nr; ++c) {
+                const int sl = rr[c];
+                if (sl < 0 || !Bx.pflag[sl]) continue;
+                const double *r = Bx.pres + 6 * (long long)sl;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    F[a] -= r[a];
+                    T[a] += lev * r[3 + a];
+                }
             }
-            __syncthreads();
+            finish_particle<true>(Bx, pd, i, src_tmp, F, T, 0u, key_out);
         }
     }
 }
 
-// block: a multiple of 32 and of every tile's lanes (Tile::first)
-void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int grid, int block, cudaStream_t s) {
+// block: a multiple of 32 and of every tile's lanes (Tile::first).
+// pairs: also the pair rows of the FP64 form (two more launches)
+void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int grid, int block, int pairs,
+                        cudaStream_t s) {
     k_build_nlist<<<grid, block, 0, s>>>(boxes, tiles, ntiles);
+    if (pairs) {
+        k_half_rows<<<grid, 128, 0, s>>>(boxes, tiles, ntiles);
+        k_reverse_slots<<<grid, 128, 0, s>>>(boxes, tiles, ntiles);
+    }
 }
 
-// lanes: 1, 2, 4 or 8 lanes per particle (block a multiple of 32)
+// lanes: 1, 2, 4 or 8 lanes per particle (block a multiple of 32); the FP64
+// form launches its pair kernel and then its gather kernel
 // key_out: the last substep of a subcycle also writes the particles' linked
 // cells and their counts for the sort that follows
 void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int src_tmp, int key_out, int mixed,
@@ -784,10 +876,13 @@ void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int 
         else if (lanes == 2) DPS_DEM(k_dem_substep_mixed, 2);
         else DPS_DEM(k_dem_substep_mixed, 1);
     } else {
-        if (lanes >= 8) DPS_DEM(k_dem_substep64, 8);
-        else if (lanes == 4) DPS_DEM(k_dem_substep64, 4);
-        else if (lanes == 2) DPS_DEM(k_dem_substep64, 2);
-        else DPS_DEM(k_dem_substep64, 1);
+#define DPS_PAIRS(L) k_dem_pairs64<L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp)
+        if (lanes >= 8) DPS_PAIRS(8);
+        else if (lanes == 4) DPS_PAIRS(4);
+        else if (lanes == 2) DPS_PAIRS(2);
+        else DPS_PAIRS(1);
+#undef DPS_PAIRS
+        k_dem_gather64<<<grid, 128, 0, s>>>(boxes, tiles, ntiles, src_tmp, key_out);
     }
 #undef DPS_DEM
 }
