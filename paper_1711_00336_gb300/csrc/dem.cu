@@ -203,8 +203,11 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
                     }
                 }
             }
-            const int ny = hi[1] - lo[1] + 1, nrows = act ? ny * (hi[2] - lo[2] + 1) : 0;
-            // the x segments of a cell row (two where the row wraps periodically)
+            const int ny = hi[1] - lo[1] + 1, nz = hi[2] - lo[2] + 1, nrows = act ? ny * nz : 0;
+            // the x segments of a cell row (two where the row wraps
+            // periodically), and the rows, are visited in ascending cell index
+            // of the wrapped cells, so that one lane's partners come out in
+            // ascending sorted index (the cells are the sort's keys)
             int xs0[2] = {lo[0], 0}, xs1[2] = {hi[0], -1};
             if (lo[0] < 0) {
                 xs0[0] = 0;
@@ -212,10 +215,13 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
                 xs0[1] = lo[0] + g.n[0];
                 xs1[1] = g.n[0] - 1;
             } else if (hi[0] > g.n[0] - 1) {
-                xs1[0] = g.n[0] - 1;
-                xs0[1] = 0;
-                xs1[1] = hi[0] - g.n[0];
+                xs0[0] = 0;
+                xs1[0] = hi[0] - g.n[0];
+                xs0[1] = lo[0];
+                xs1[1] = g.n[0] - 1;
             }
+            const int roty = lo[1] < 0 ? -lo[1] : (hi[1] > g.n[1] - 1 ? g.n[1] - lo[1] : 0);
+            const int rotz = lo[2] < 0 ? -lo[2] : (hi[2] > g.n[2] - 1 ? g.n[2] - lo[2] : 0);
             // partners of particle i in this lane's rows r = lane, lane +
             // LANES, ..., in row order, then the sorted order inside a row; the
             // particle ranges of RB rows are loaded together before any is
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ 
                         const int r = r0 + u * LANES;
                         s[2 * u] = e[2 * u] = s[2 * u + 1] = e[2 * u + 1] = 0;
                         if (r >= nrows) continue;
-                        const int yy = lo[1] + r % ny, zz = lo[2] + r / ny;
+                        const int yy = lo[1] + (r % ny + roty) % ny, zz = lo[2] + (r / ny + rotz) % nz;
                         const int z = zz < 0 ? zz + g.n[2] : (zz >= g.n[2] ? zz - g.n[2] : zz);
                         const int y = yy < 0 ? yy + g.n[1] : (yy >= g.n[1] ? yy - g.n[1] : yy);
                         const long long row = cell_index(g, 0, y, z);
@@ -658,6 +664,14 @@ __global__ void __launch_bounds__(256) k_half_rows(const BoxDev *__restrict__ bo
             Bx.hn[i] = nh;
             Bx.rn[i] = nn - nh;
             int *rr = Bx.rrow + i * (long long)maxn;
+            bool asc = true;  // rows of one lane come out ascending
+            for (int k = 1; k < nn; ++k) asc = asc && row[k] > row[k - 1];
+            if (asc) {
+                const int lo = nn - nh;
+                for (int k = 0; k < lo; ++k) rr[k] = row[k];
+                for (int k = lo; k < nn; ++k) Bx.hj[h0 + k - lo] = row[k];
+                continue;
+            }
             for (int k = 0; k < nn; ++k) {
                 const int j = row[k];
                 const bool up = j > i;
