@@ -1,12 +1,20 @@
 """Benchmark of the coupled LBM-DEM step (one step = one pass of Algorithm 1:
-sort, volume fraction, moments and fields, particle forces, reaction gathers,
-DEM substeps with lubrication, collide-stream) on a synthetic suspension.
+moments and fields, particle forces, reaction gathers, DEM substeps with
+contact and lubrication, linked-cell sort, volume fraction, collide-stream)
+on a synthetic suspension.
 
-Default workload: 64^3 box with walls at z, 5000 spheres of d = 1 (random
-sequential insertion, seed 12345), density ratio 2.5, tau 0.65, 1 interaction
-subcycle with 10 DEM substeps, contact (e_n 0.9, T_c = 1), lubrication
-(h_c = d), FP64.  Prints one JSON line (see the contract in the README of this
-repository's design notes): value = coupled MLUPS over all ranks.
+Default workload (the largest single-GPU configuration): a triply periodic
+256^3 box of spheres of d = 1.5 at solid volume fraction 0.2 (1,898,792
+spheres on a jittered cubic lattice, seed 20), density ratio 2.5, tau 0.55,
+gravity for a Stokes Reynolds number of 0.1, body force balancing the
+buoyant weight, 2 interaction subcycles of 10 DEM substeps, contact (e_n 0.88,
+T_c = dt/2, mu_c 0.25), lubrication (h_c = d), FP64 plain method.  The PDFs
+(2.55 GB) exceed the 129 MB L2, and a 256 MB buffer is also written between
+timed steps.  Secondary lines: the FP32 and FP16-shifted forms on the same
+workload, and the 64^3 wall-bounded suspension (5000 spheres, FP64).
+
+Prints one JSON line: value = coupled MLUPS over all ranks (replicas, one
+box per GPU).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -30,12 +38,35 @@ from paper_1711_00336_gb300 import workloads  # noqa: E402
 PHASES = ["moments+fields", "force_am", "reaction_am", "force_drag", "reaction_drag", "dem_substep", "cell_sort",
           "eps_gather", "collide_stream"]
 
+# the headline workload: 256^3, d 1.5, eps 0.2 (seed 20, as in the precision suite)
+HEADLINE = dict(L=256, eps=0.2, d=1.5, seed=20)
+N_INT, N_DEM = 2, 10
+
+
+def headline_workload(L=None):
+    """The 256^3 settling workload (or its L^3 sample with the same eps, d)."""
+    h = dict(HEADLINE)
+    if L is not None:
+        h["L"] = L
+    return workloads.settling_box(L=h["L"], eps=h["eps"], d=h["d"], seed=h["seed"])
+
+
+def settling_closure_kw(wl):
+    """Closure of the settling workloads: n_int = 2, n_DEM = 10, T_c = dt/2,
+    e_n 0.88, mu_c 0.25, h_c = d, body force balancing the buoyant weight."""
+    return dict(g=wl["g"], fb_mode=1, e_n=0.88, mu_c=0.25, T_c=0.5, h_c=float(wl["d"][0]), h_min=1e-5, C_am=0.5,
+                n_int=N_INT, n_dem=N_DEM, lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5)
+
 
 def closure_kw(wl):
-    # reading of the wall-suspension configuration: n_int = 1, n_DEM = 10,
-    # T_c = (d/dx) dt, h_c = d, e_n = 0.9, mu_c = 0.25
+    """Closure of the 64^3 wall suspension: n_int = 1, n_DEM = 10, T_c = (d/dx)
+    dt, h_c = d, e_n = 0.9, mu_c = 0.25, no body force on the fluid."""
     return dict(g=wl["g"], fb_mode=0, fb=(0, 0, 0), e_n=0.9, mu_c=0.25, T_c=1.0, h_c=1.0, h_min=1e-5,
                 C_am=0.5, n_int=1, n_dem=10, lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5)
+
+
+def closure_of(wl):
+    return closure_kw(wl) if wl["name"].startswith("wall_suspension") else settling_closure_kw(wl)
 
 
 def algorithmic_bytes_collide(prec, mom_in=False):
@@ -46,42 +77,37 @@ def algorithmic_bytes_collide(prec, mom_in=False):
     return 2 * 19 * s + (8 if mom_in else 4) * sf
 
 
-# FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA lanes) x 2.07 GHz maximum SM clock
-FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 # algorithmic FP64 flops (a division, square root or logarithm counted as one)
-# per cell: velocity and invariants 36, 9 pairs x 16 + 13 more (rho and j, 42
-# flops, come from the moments pass of the same step)
+# per cell of the collide-stream: velocity and invariants 36, 9 pairs x 16 +
+# 13 more (rho and j, 42 flops, come from the moments pass of the same step)
 K1_FLOPS_F64 = 207
 DEM_FLOPS_PARTICLE = 32   # per particle and substep: semi-implicit Euler of u, w, x, skin check
-DEM_FLOPS_PAIR = 75       # per interacting partner: separation 9, masses / normal 17, Ball-Melrose force 49
-# DRAM bytes (read + write) per launch from one ncu capture of the same kernel
-# and workload (the step-kernel capture of the wall suspension); None where no
-# capture of the current kernel exists
-TRAFFIC = {("dem_substep", "f64"): 1.47e6, ("collide_stream", "f64"): 56.8e6}
+DEM_FLOPS_PAIR = 75       # per interacting pair (once: F_ji = -F_ij): separation 9, masses / normal 17,
+                          # contact or Ball-Melrose force 49
+# DRAM bytes (read + write) per particle-substep of the FP64 DEM pair and
+# gather kernels, from the ncu capture of profiles/dem_pairs_fp64_settling_64.md
+# (a 64^3 box of the headline eps and d; traffic grows with the particle count)
+DEM_TRAFFIC_PER_PARTICLE = 971.0  # (4.53 + 24.28) MB / 29,669 spheres, cold-cache capture
 
 
-def lubrication_partners(x, d, n, periodic, h_c):
-    """Mean number of partners (spheres, and walls on the non-periodic axes)
-    within the lubrication range of a particle: the pairs a DEM substep
-    evaluates beyond the neighbour-list screening."""
+def interacting_pairs(x, d, n, periodic, h_c, sample=20000, seed=0):
+    """Unordered pairs within the interaction range (gap < h_c: lubrication or
+    contact), estimated from the partners of a random sample of particles
+    (N * mean partners / 2), plus the sphere-wall pairs of the wall axes."""
+    from scipy.spatial import cKDTree
     x = np.asarray(x, float)
-    N = len(x)
     L = np.asarray(n, float)
-    cnt = 0
-    for a0 in range(0, N, 512):
-        dx = x[a0:a0 + 512, None, :] - x[None, :, :]
-        for a in range(3):
-            if periodic[a]:
-                dx[..., a] -= L[a] * np.round(dx[..., a] / L[a])
-        dist = np.sqrt((dx * dx).sum(-1))
-        gap = dist - 0.5 * (d[a0:a0 + 512, None] + d[None, :])
-        ok = gap < h_c
-        ok[np.arange(ok.shape[0]), np.arange(a0, a0 + ok.shape[0])] = False
-        cnt += int(ok.sum())
+    box = np.where(np.asarray(periodic) > 0, L, 1e9)  # a wall axis: no wrap
+    tree = cKDTree(np.where(np.asarray(periodic) > 0, np.mod(x, L), x), boxsize=box)
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(x), min(sample, len(x)), replace=False)
+    r = float(np.max(d)) + h_c
+    cnt = tree.query_ball_point(tree.data[idx], r, return_length=True) - 1
+    pairs = len(x) * float(np.mean(cnt)) / 2.0
     for a in range(3):
         if not periodic[a]:
-            cnt += int((x[:, a] - 0.5 * d < h_c).sum() + (L[a] - x[:, a] - 0.5 * d < h_c).sum())
-    return cnt / max(N, 1)
+            pairs += float((x[:, a] - 0.5 * d < h_c).sum() + (L[a] - x[:, a] - 0.5 * d < h_c).sum())
+    return pairs
 
 
 def measured_peaks():
@@ -136,16 +162,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+
+
 def make_domain(dps, wl, prec, stream=None):
     dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], prec, max_particles=len(wl["x"]), stream=stream)
     dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
-    dom.set_closure(**closure_kw(wl))
+    dom.set_closure(**closure_of(wl))
     return dom
 
 
 def time_device(dps, wl, prec, steps, warmup, flush, timing=True):
     """Device-timed steps: CUDA events on the domain's stream around every
-    step, L2 flushed (256 MB write) between steps outside the events."""
+    step, a 256 MB buffer written between steps outside the events."""
     import torch
     dom = make_domain(dps, wl, prec)
     s = dom.stream
@@ -198,45 +226,60 @@ def e2e_run(dps, wl, prec, steps):
     return dt, h2d, d2h
 
 
-def oracle_sample(wl, seconds=12.0, max_steps=200):
-    """Time the FP64 CPU oracle (as it stands, one host thread) on the same
-    workload: as many whole steps as fit in `seconds`."""
+# ---- the FP64 CPU oracle on the host cores (CPU baseline, reference arm) ----------------
+def _oracle_domain(wl):
     import oracle as O
-    kw = closure_kw(wl)
-    P = O.make_params(wl["n"], wl["periodic"], wl["tau"], g=kw["g"], f_b=kw["fb"], e_n=kw["e_n"], mu_c=kw["mu_c"],
+    kw = closure_of(wl)
+    fb = kw.get("fb", (0.0, 0.0, 0.0))
+    if kw["fb_mode"] == 1:  # balance the buoyant weight (the library's fb_mode 1)
+        V = math.pi / 6 * np.asarray(wl["d"]) ** 3
+        wb = float(((np.asarray(wl["rho_p"]) - 1.0) * V).sum())
+        fb = tuple(-wb * np.asarray(kw["g"]) / (float(np.prod(wl["n"])) - float(V.sum())))
+    P = O.make_params(wl["n"], wl["periodic"], wl["tau"], g=kw["g"], f_b=fb, e_n=kw["e_n"], mu_c=kw["mu_c"],
                       T_c=kw["T_c"], h_c=kw["h_c"], h_min=kw["h_min"], C_am=kw["C_am"], n_int=kw["n_int"],
                       n_dem=kw["n_dem"], lub_limiter=1, lub_cap=kw["lub_cap"], eps_min=kw["eps_min"])
-    dom = O.Domain(P, x=wl["x"], d=wl["d"], rho_p=wl["rho_p"])
-    dom.step(1)
+    return O.Domain(P, x=wl["x"], d=wl["d"], rho_p=wl["rho_p"])
+
+
+def _oracle_worker(job):
+    """one host process: the oracle on an L^3 sample of the headline workload
+    (seed offset per process); (warmup) untimed steps, then `steps` timed ones
+    (or as many as fit in `seconds` when steps is 0)"""
+    L, seed_off, warmup, steps, seconds = job
+    h = dict(HEADLINE)
+    wl = workloads.settling_box(L=L, eps=h["eps"], d=h["d"], seed=h["seed"] + seed_off)
+    dom = _oracle_domain(wl)
+    dom.step(warmup)
     t0 = time.perf_counter()
     k = 0
-    while k < max_steps:
+    while (steps and k < steps) or (not steps and (k == 0 or time.perf_counter() - t0 < seconds)):
         dom.step(1)
         k += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    dt = time.perf_counter() - t0
-    ncell = int(np.prod(wl["n"]))
-    return ncell * k / dt / 1e6, k, dt
+    return k, time.perf_counter() - t0, int(np.prod(wl["n"])), len(wl["x"])
 
 
-def run_reference(args, wl, ncell):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    import oracle as O
-    O.build.build()
-    mlups, k, dt = oracle_sample(wl, seconds=max(3.0, min(60.0, 1.5 * (args.steps + args.warmup))),
-                                 max_steps=args.steps + args.warmup)
-    ms = dt / k * 1e3
-    line = {"metric": "coupled MLUPS (FP64 plain method)", "value": mlups, "unit": "MLUPS", "impl": "reference",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(wl, ncell, "f64"),
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{k} coupled steps of the same workload on one host thread"},
-            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def oracle_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_throughput(procs, L, warmup, steps, seconds=0.0):
+    """The oracle as it stands on `procs` host processes at once, each on its
+    own L^3 sample (spawned processes: safe beside a CUDA context).  Returns
+    (MLUPS over all processes, particle-steps/s, steps per process, seconds)."""
+    import multiprocessing as mp
+    jobs = [(L, k, warmup, steps, seconds) for k in range(procs)]
+    if procs == 1:
+        res = [_oracle_worker(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    t = max(r[1] for r in res)
+    cells = sum(r[0] * r[2] for r in res)
+    parts = sum(r[0] * r[3] for r in res)
+    return cells / t / 1e6, parts / t, min(r[0] for r in res), t
 
 
 def max_over_ranks(x, world, device):
@@ -257,30 +300,93 @@ def job_mlups(world, ncell, steps, t_ms):
 
 
 def config_of(wl, ncell, prec):
+    kw = closure_of(wl)
+    per = "triply periodic" if all(wl["periodic"]) else "periodic x,y; walls z"
     return {"workload": wl["name"], "cells": ncell, "particles": int(len(wl["x"])), "precision": prec,
-            "n_int": 1, "n_dem": 10, "boundaries": "periodic x,y; walls z",
-            "l2": "flushed between timed steps (256 MB write outside the step events)",
+            "n_int": kw["n_int"], "n_dem": kw["n_dem"], "boundaries": per,
+            "l2": "inputs larger than L2 (PDFs 2.55 GB at 256^3 FP64); also a 256 MB write between timed steps",
             "parallelism": "replicas (one independent box per GPU)"}
+
+
+METRIC = "coupled MLUPS (FP64 plain method)"
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on all host cores
+    (one process per core, each on a 64^3 sample of the headline workload:
+    same eps, d and closure), warmup + steps whole coupled steps each."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build.build()
+    wl = headline_workload()
+    ncell = int(np.prod(wl["n"]))
+    cores = oracle_cores()
+    mlups, psteps, k, t = oracle_throughput(cores, 64, args.warmup, args.steps)
+    sample = (f"{cores} host processes at once, each {k} timed coupled steps (after {args.warmup} untimed) of a "
+              f"64^3 sample of the workload (same eps, d, closure; its own seed)")
+    line = {"metric": METRIC, "value": mlups, "unit": "MLUPS", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / k * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, ncell, "f64"), "particle_steps_per_s": psteps,
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def dem_roofline(phase, wl, st, steps, fp64_peak, hbm):
+    """FP64 DEM substeps (pair kernel + gather kernel, timed together by the
+    phase events): algorithmic flops per substep = 32 per particle + 75 per
+    interacting pair (each pair once) over the mean substep time."""
+    kw = closure_of(wl)
+    dm = phase["dem_substep"]
+    nsub = steps * kw["n_int"] * kw["n_dem"]
+    per_ms = dm["ms"] / nsub
+    npart = len(wl["x"])
+    pairs = interacting_pairs(st["x_final"], np.asarray(wl["d"]), wl["n"], wl["periodic"], kw["h_c"])
+    flops = npart * DEM_FLOPS_PARTICLE + pairs * DEM_FLOPS_PAIR
+    ach = flops / (per_ms * 1e-3) / 1e9
+    traffic = DEM_TRAFFIC_PER_PARTICLE * npart if DEM_TRAFFIC_PER_PARTICLE else None
+    return {"kernel": "DEM substep, FP64 form: k_dem_pairs64 + k_dem_gather64", "bound": "alu", "achieved": ach,
+            "peak": fp64_peak, "unit": "GFLOP/s", "frac": ach / fp64_peak, "traffic": traffic,
+            "per_launch_us": per_ms * 1e3, "launch": "one substep (its two kernels)", "units_per_launch": npart,
+            "unit_of_work": "particle-substep", "flops_per_unit": flops / npart, "pairs_in_range": pairs,
+            "peak_source": "dps_probe_fp64_peak: FP64 FMA throughput of this GPU in this run (of measured)",
+            "hbm_view": {"achieved_GBps": npart * 184 / (per_ms * 1e-3) / 1e9, "peak_GBps": hbm,
+                         "bytes_per_particle": 184}}
+
+
+def collide_roofline(phase, ncell, steps, fp64_peak, hbm):
+    cs = phase["collide_stream"]
+    k1_ms = cs["ms"] / steps  # the phase: K1 and the end-of-step update
+    k1_flops = K1_FLOPS_F64 * ncell / (k1_ms * 1e-3) / 1e9
+    b = algorithmic_bytes_collide("f64", True)
+    return {"kernel": "k_collide_stream (K1, FP64)", "bound": "alu", "achieved": k1_flops, "peak": fp64_peak,
+            "unit": "GFLOP/s", "frac": k1_flops / fp64_peak, "traffic": None, "flops_per_cell": K1_FLOPS_F64,
+            "cells_per_launch": ncell, "per_launch_us": k1_ms * 1e3,
+            "hbm_view": {"achieved_GBps": b * ncell / (k1_ms * 1e-3) / 1e9, "peak_GBps": hbm, "bytes_per_cell": b},
+            "peak_source": "dps_probe_fp64_peak (of measured)"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="settling256", choices=["settling256", "wall_suspension"])
     ap.add_argument("--forms", default="f32,f16s", help="extra precision forms to time (comma list, '' for none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 64^3 wall-suspension line")
     ap.add_argument("--suite", default="", help="precision,accuracy,batch,serve,rebound,hindered: measure the "
                     "forms, the sphere-wall rebound or hindered settling instead")
     args = ap.parse_args()
     if args.suite:
         run_suite(args)
         return
-    wl = workloads.wall_suspension()
-    ncell = int(np.prod(wl["n"]))
     if args.impl == "reference":
-        run_reference(args, wl, ncell)
+        run_reference(args)
         return
 
     import torch
@@ -293,7 +399,12 @@ def main():
         dist.init_process_group("nccl")
     from paper_1711_00336_gb300 import build, dps
     build.build()
+    import oracle as O
+    O.build.build()  # before any host process is spawned
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    wl = headline_workload() if args.workload == "settling256" else workloads.wall_suspension()
+    ncell = int(np.prod(wl["n"]))
+    fp64_peak = dps.probe_fp64_peak()
 
     if world > 1:
         dist.barrier()
@@ -308,81 +419,64 @@ def main():
     value = job_mlups(world, ncell, args.steps, t_all)
     ms_step = t_all / args.steps
 
-    # roofline of the dominant kernel, measured live over the timed region
-    # (per-phase CUDA events on the domain's stream)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6800 (of fallback)"
-    roof, roof_k1 = None, None
-    if phase:
-        single = ("dem_substep", "collide_stream", "force_drag", "force_am", "eps_gather", "reaction_am",
-                  "reaction_drag")
-        dom_phase = max((k for k in single if k in phase), key=lambda k: phase[k]["ms"])
-        cs = phase["collide_stream"]
-        k1_launches = max(cs["launches"] // 2, 1)  # the phase holds K1 and the end-of-step update
-        k1_ms = cs["ms"] / k1_launches
-        k1_flops = K1_FLOPS_F64 * ncell / (k1_ms * 1e-3) / 1e9
-        roof_k1 = {"kernel": "k_collide_stream (K1, FP64)", "bound": "alu", "achieved": k1_flops,
-                   "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": k1_flops / FP64_PEAK_GFLOPS,
-                   "traffic": TRAFFIC.get(("collide_stream", "f64")), "flops_per_cell": K1_FLOPS_F64,
-                   "cells_per_launch": ncell, "per_launch_us": k1_ms * 1e3,
-                   "hbm_view": {"achieved_GBps": algorithmic_bytes_collide("f64", True) * ncell / (k1_ms * 1e-3) / 1e9,
-                                "peak_GBps": hbm, "bytes_per_cell": algorithmic_bytes_collide("f64", True)},
-                   "peak_source": "152 SMs x 4 FP64 flop/clk x 2.07 GHz (derived)"}
-        if dom_phase == "dem_substep":
-            dm = phase["dem_substep"]
-            per_ms = dm["ms"] / max(dm["launches"], 1)
-            npart = len(wl["x"])
-            partners = lubrication_partners(st["x_final"], wl["d"], wl["n"], wl["periodic"], 1.0)
-            flops_launch = npart * (DEM_FLOPS_PARTICLE + DEM_FLOPS_PAIR * partners)
-            ach = flops_launch / (per_ms * 1e-3) / 1e9
-            roof = {"kernel": "k_dem_substep (FP64 form)", "bound": "alu", "achieved": ach,
-                    "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
-                    "traffic": TRAFFIC.get(("dem_substep", "f64")), "per_launch_us": per_ms * 1e3,
-                    "units_per_launch": npart, "unit_of_work": "particle-substep",
-                    "flops_per_unit": DEM_FLOPS_PARTICLE + DEM_FLOPS_PAIR * partners,
-                    "lubrication_partners_per_particle": partners,
-                    "peak_source": "152 SMs x 4 FP64 flop/clk x 2.07 GHz (derived)", "dominant_phase": dom_phase}
-        elif dom_phase == "collide_stream":
-            roof = dict(roof_k1, dominant_phase=dom_phase)
-        else:
-            roof = {"kernel": dom_phase, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
-                    "frac": None, "traffic": None, "dominant_phase": dom_phase}
+    dom_phase = max((k for k in phase if k != "moments+fields"), key=lambda k: phase[k]["ms"])
+    roof_dem = dem_roofline(phase, wl, st, args.steps, fp64_peak, hbm)
+    roof_k1 = collide_roofline(phase, ncell, args.steps, fp64_peak, hbm)
+    roof = dict(roof_dem if dom_phase != "collide_stream" else roof_k1, dominant_phase=dom_phase)
 
     forms = {}
     for prec in [f for f in args.forms.split(",") if f]:
-        tot, _, ph, _, st2 = time_device(dps, wl, prec, max(args.steps // 2, 10), args.warmup, flush)
-        k = max(args.steps // 2, 10)
-        cs = ph["collide_stream"]
-        per = cs["ms"] / max(cs["launches"] // 2, 1)  # K1 and the end-of-step update per step
-        gbs = algorithmic_bytes_collide(prec) * ncell / (per * 1e-3) / 1e9
+        k = args.steps  # the FP64 run's history: the settling velocities compare
+        tot, _, ph, _, st2 = time_device(dps, wl, prec, k, args.warmup, flush)
+        cs_ms = ph["collide_stream"]["ms"] / k
+        gbs = algorithmic_bytes_collide(prec) * ncell / (cs_ms * 1e-3) / 1e9
         forms[prec] = {"value": ncell * k / (tot * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": tot / k,
+                       "speedup_vs_f64": ms_step / (tot / k), "dem_ms_per_step": ph["dem_substep"]["ms"] / k,
                        "collide_stream_GBps": gbs, "collide_stream_frac_of_hbm": gbs / hbm,
-                       "u_pS_z": float(st2["u_pS"][2])}
+                       "u_pS_z": float(st2["u_pS"][2]), "u_pS_z_f64": float(st["u_pS"][2])}
 
-    e2e_steps = min(args.steps, 50)
+    secondary = None
+    if args.workload == "settling256" and not args.no_secondary:
+        ws = workloads.wall_suspension()
+        k = max(args.steps, 20)
+        tot, tms, _, _, _ = time_device(dps, ws, "f64", k, args.warmup, flush, timing=False)
+        nc = int(np.prod(ws["n"]))
+        secondary = {"workload": ws["name"], "value": nc * k / (tot * 1e-3) / 1e6, "unit": "MLUPS",
+                     "ms_per_step": tot / k, "step_ms_p99": float(np.percentile(tms, 99)), "precision": "f64"}
+
+    e2e_steps = min(args.steps, 10)
     dt, h2d, d2h = e2e_run(dps, wl, "f64", e2e_steps)
-    e2e = {"value": ncell * e2e_steps / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+    e2e = {"value": world * ncell * e2e_steps / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "steps": e2e_steps,
            "what": "create + upload particles + per step (step, read x/u/w/F) + destroy, wall clock"}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        mlups_cpu, k, dt = oracle_sample(wl)
-        cpu = {"value": mlups_cpu, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{k} coupled steps of the same 64^3 / 5000-sphere workload, one host thread"}
+        cores = oracle_cores()
+        m1, p1, k1, _ = oracle_throughput(1, 64, 1, 0, seconds=12.0)
+        mc, pc, kc, _ = oracle_throughput(cores, 64, 1, 0, seconds=12.0)
+        cpu = {"value": mc, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": (f"a 64^3 sample of the workload (same eps, d, closure), whole coupled steps for ~12 s: "
+                          f"{cores} processes at once (>= {kc} steps each; the oracle is single-threaded, so the "
+                          f"host cores run independent samples)"),
+               "particle_steps_per_s": pc,
+               "single_thread": {"value": m1, "unit": "MLUPS", "cores": 1, "steps": k1, "particle_steps_per_s": p1}}
 
     if rank == 0:
+        kw = closure_of(wl)
         psteps = len(wl["x"]) * args.steps / (t_all * 1e-3)
-        line = {"metric": "coupled MLUPS (FP64 plain method)", "value": value, "unit": "MLUPS", "n_gpus": world,
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_of(wl, ncell, "f64"),
                 "particle_steps_per_s": world * psteps,
-                "particle_substeps_per_s": world * psteps * 10,
+                "particle_substeps_per_s": world * psteps * kw["n_int"] * kw["n_dem"],
                 "step_ms_p50": float(np.percentile(times, 50)), "step_ms_p99": float(np.percentile(times, 99)),
-                "roofline": roof, "roofline_collide_stream": roof_k1, "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in phase.items()} if phase else None,
-                "forms": forms, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+                "roofline": roof, "roofline_collide_stream": roof_k1, "fp64_peak_gflops": fp64_peak,
+                "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in phase.items()},
+                "forms": forms, "secondary": secondary, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(lps * args.steps),
                 "u_pS_z": float(st["u_pS"][2]), "status": int(st["status"])}
         print(json.dumps(line), flush=True)

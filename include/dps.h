@@ -408,6 +408,15 @@ int dps_op_cell_sort(const int n[3], const int periodic[3], int B, int64_t np,
                      const double *x3, const int32_t *ids, int32_t *cell_start, int32_t *order,
                      void *stream);
 
+/* ---- measurement ----------------------------------------------------------- */
+/* The paper has no counterpart: a property of the GPU, not of the method.
+ * Measured FP64 throughput of the current device in GFLOP/s (independent
+ * fused multiply-add chains on every SM, best of 5 timed launches, 2 flops
+ * per FMA), the peak against which the FP64-bound kernels of this library
+ * are reported.  Allocates 8 bytes of device memory for its run.
+ * Errors: DPS_ERR_ARG (NULL), DPS_ERR_OOM, DPS_ERR_CUDA. */
+int dps_probe_fp64_peak(double *gflops);
+
 /* ---- allocation-free variant of the cell sort ---------------------------- */
 /* The paper has no counterpart: this entry point is a property of the
  * library, not of the method.  dps_op_cell_sort takes its scratch memory

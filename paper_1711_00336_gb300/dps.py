@@ -351,6 +351,17 @@ class Domain:
         return cs, order[:self.np]
 
 
+def probe_fp64_peak():
+    """Measured FP64 FMA throughput of the current GPU in GFLOP/s."""
+    L = lib()
+    L.dps_probe_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    v = ctypes.c_double()
+    rc = L.dps_probe_fp64_peak(ctypes.byref(v))
+    if rc != DPS_OK:
+        raise DPSError(rc, "dps_probe_fp64_peak failed")
+    return v.value
+
+
 def op_cell_sort(n, periodic, x_dev, ids_dev, stream=None):
     """Linked-cell sort of device positions (torch float64 [np,3]) and ids
     (torch int32 [np]); returns device (cell_start[ncell+1], order[np])."""

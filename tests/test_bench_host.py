@@ -25,18 +25,19 @@ def test_job_mlups_counts_every_replica():
     assert bench.job_mlups(1, 1000, 10, 1.0) == 10.0
 
 
-def test_lubrication_partners_by_hand():
+def test_interacting_pairs_by_hand():
+    """unordered pairs within gap h_c (each pair once) plus sphere-wall pairs"""
     d = np.ones(5)
-    x = [(1.0, 1.0, 1.0),    # A: B at gap 0.5, bottom wall at gap 0.5
-         (2.5, 1.0, 1.0),    # B: A, bottom wall
-         (5.0, 5.0, 4.0),    # C: nothing within 1 (walls at 3.5)
-         (7.9, 6.0, 4.0),    # D: E across the periodic x face (gap -0.5)
-         (0.4, 6.0, 4.0)]    # E: D
+    x = np.array([(1.0, 1.0, 1.0),    # A: B at gap 0.5, bottom wall at gap 0.5
+                  (2.5, 1.0, 1.0),    # B: A, bottom wall
+                  (5.0, 5.0, 4.0),    # C: nothing within 1 (walls at 3.5)
+                  (7.9, 6.0, 4.0),    # D: E across the periodic x face (gap -0.5)
+                  (0.4, 6.0, 4.0)])   # E: D
     n, h_c = (8, 8, 8), 1.0
-    # walls on z: A and B see the bottom wall; pairs A-B and D-E
-    assert bench.lubrication_partners(x, d, n, (1, 1, 0), h_c) == (2 + 2 + 0 + 1 + 1) / 5
-    # fully periodic: no walls
-    assert bench.lubrication_partners(x, d, n, (1, 1, 1), h_c) == (1 + 1 + 0 + 1 + 1) / 5
-    # walls on x: A (x - d/2 = 0.5) and E (-0.1) reach the x = 0 face, D the
-    # x = 8 face (-0.4); D and E are 7.5 apart, no longer partners
-    assert bench.lubrication_partners(x, d, n, (0, 1, 1), h_c) == (2 + 1 + 0 + 1 + 1) / 5
+    # walls on z: pairs A-B, D-E and the bottom wall of A and B
+    assert bench.interacting_pairs(x, d, n, (1, 1, 0), h_c) == 2 + 2
+    # fully periodic: the two sphere pairs
+    assert bench.interacting_pairs(x, d, n, (1, 1, 1), h_c) == 2
+    # walls on x: D and E are 7.5 apart; A (x - d/2 = 0.5) and E (-0.1)
+    # reach the x = 0 face, D the x = 8 face (-0.4)
+    assert bench.interacting_pairs(x, d, n, (0, 1, 1), h_c) == 1 + 3
