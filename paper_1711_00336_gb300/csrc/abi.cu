@@ -53,7 +53,7 @@ template <typename FT>
 void launch_reaction_am(const BoxDev *, const Tile *, int, int, int, cudaStream_t);
 template <typename FT>
 void launch_reaction_drag(const BoxDev *, const Tile *, int, int, int, int, int, cudaStream_t);
-void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, int, int, int, cudaStream_t);
+void launch_dem_substep(const BoxDev *, const Tile *, int, int, int, int, int, int, int, int, cudaStream_t);
 void launch_build_nlist(const BoxDev *, const Tile *, int, int, int, int, cudaStream_t);
 long long scan_scratch_words(long long);
 void exclusive_scan(const int *, long long, int *, int *, cudaStream_t);
@@ -141,6 +141,7 @@ struct Batch {
     bool shape_fixed = false;     // launch shapes set by the caller or the autotuner
     int n_int = 0, n_dem = 0;
     bool any_lift = false;        // some box applies the lift force (curl launch per subcycle)
+    bool any_walls = true;        // some box with particles has a wall axis (DEM wall code)
     int part_off[5] = {0, 0, 0, 0, 0};  // particle tiles grouped by DEM lanes class (1, 2, 4, 8)
     int cpl_lanes = 1;            // most lanes per particle of the force kernels over the batch
     int n_cell_plain = 0;         // cell tiles of boxes with a constant tau (listed first);
@@ -404,11 +405,13 @@ static int push_layout(Batch *B) {
     }
     std::vector<Tile> partc[4];  // particle tiles by DEM lanes class
     B->any_lift = false;
+    B->any_walls = false;
     B->cpl_lanes = 1;
     for (int k = 0; k < nb; ++k) {
         BoxHost *h = B->boxes[k];
         compute_phys(h);
         B->any_lift |= h->d.ph.lift && h->d.np > 0;
+        B->any_walls |= h->d.np > 0 && !(h->d.g.per[0] && h->d.g.per[1] && h->d.g.per[2]);
         std::vector<Tile> &ct = (h->d.ph.eilers || h->d.ph.smag) ? cellv : cell;
         tab[k] = h->d;
         const long long N = h->d.g.ncell, np = h->d.np;
@@ -610,7 +613,7 @@ static void enqueue_step(Batch *B) {
                                                                          31) / 32 * 32)
                                         : part_threads(u, 1 << c);
                     launch_dem_substep(T, B->d_part + B->part_off[c], nt, sd & 1, sd == B->n_dem - 1,
-                                       B->prec != DPS_F64, 1 << c, grid_of(nt), blk, s);
+                                       B->prec != DPS_F64, 1 << c, B->any_walls, grid_of(nt), blk, s);
                     ndl += B->prec == DPS_F64 ? 2 : 1;  // FP64: pair kernel + gather kernel
                 }
         tend(B, PH_DEM, ndl);

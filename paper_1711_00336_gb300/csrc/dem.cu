@@ -827,8 +827,13 @@ __global__ void __launch_bounds__(256, 1) k_dem_pairs64(const BoxDev *__restrict
 // forces of its owned pairs (ascending partner), minus those of the pairs its
 // lower partners own (ascending owner), each pair's n x F_t times d_i/2, then
 // the walls and Eq. particle_motion.  The order depends on the list alone.
-__global__ void __launch_bounds__(128) k_dem_gather64(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
-                                                     int ntiles, int src_tmp, int key_out) {
+// WALLS: some box of the batch has a wall axis (else the wall code is left
+// out: 128 registers instead of 168, more warps for a kernel that waits on
+// the scattered loads of the pair results)
+template <bool WALLS>
+__global__ void __launch_bounds__(128, 4) k_dem_gather64(const BoxDev *__restrict__ boxes,
+                                                        const Tile *__restrict__ tiles, int ntiles, int src_tmp,
+                                                        int key_out) {
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
         const BoxDev &Bx = boxes[tl.box];
@@ -861,7 +866,7 @@ __global__ void __launch_bounds__(128) k_dem_gather64(const BoxDev *__restrict__
                     T[a] += lev * r[3 + a];
                 }
             }
-            finish_particle<true>(Bx, pd, i, src_tmp, F, T, 0u, key_out);
+            finish_particle<WALLS>(Bx, pd, i, src_tmp, F, T, 0u, key_out);
         }
     }
 }
@@ -878,11 +883,12 @@ void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int 
 }
 
 // lanes: 1, 2, 4 or 8 lanes per particle (block a multiple of 32); the FP64
-// form launches its pair kernel and then its gather kernel
+// form launches its pair kernel and then its gather kernel; walls: some box
+// has a wall axis
 // key_out: the last substep of a subcycle also writes the particles' linked
 // cells and their counts for the sort that follows
 void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int src_tmp, int key_out, int mixed,
-                        int lanes, int grid, int block, cudaStream_t s) {
+                        int lanes, int walls, int grid, int block, cudaStream_t s) {
 #define DPS_DEM(K, L) K<L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp, key_out)
     if (mixed) {
         if (lanes >= 8) DPS_DEM(k_dem_substep_mixed, 8);
@@ -896,7 +902,10 @@ void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int 
         else if (lanes == 2) DPS_PAIRS(2);
         else DPS_PAIRS(1);
 #undef DPS_PAIRS
-        k_dem_gather64<<<grid, 128, 0, s>>>(boxes, tiles, ntiles, src_tmp, key_out);
+        if (walls)
+            k_dem_gather64<true><<<grid, 128, 0, s>>>(boxes, tiles, ntiles, src_tmp, key_out);
+        else
+            k_dem_gather64<false><<<grid, 128, 0, s>>>(boxes, tiles, ntiles, src_tmp, key_out);
     }
 #undef DPS_DEM
 }
