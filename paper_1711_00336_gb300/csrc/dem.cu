@@ -831,7 +831,7 @@ __global__ void __launch_bounds__(256, 1) k_dem_pairs64(const BoxDev *__restrict
 // out: 128 registers instead of 168, more warps for a kernel that waits on
 // the scattered loads of the pair results)
 template <bool WALLS>
-__global__ void __launch_bounds__(128, 4) k_dem_gather64(const BoxDev *__restrict__ boxes,
+__global__ void __launch_bounds__(128, WALLS ? 1 : 4) k_dem_gather64(const BoxDev *__restrict__ boxes,
                                                         const Tile *__restrict__ tiles, int ntiles, int src_tmp,
                                                         int key_out) {
     DPS_FOR_TILES(tiles, ntiles, t) {
