@@ -8,12 +8,15 @@
 // Neighbour list: after every sort a Verlet list is built per particle from
 // the linked cells of the +-R cells around it, keeping every partner within
 // the interaction range plus the skin; the n_DEM substeps then loop over the
-// list only.  A substep gives each particle a group of LANES consecutive
-// lanes of a warp: lane l takes the list entries l, l + LANES, ... and the
-// group's force and torque sums are combined by warp shuffles (a fixed xor
-// tree, so the result does not depend on the launch shape); lane 0 then adds
-// the walls and integrates.  A particle that moves more than skin/2 before the next sort
-// raises DPS_ERR_UNSTABLE.  Candidate distances are screened in FP32 (a float
+// list only.  FP64 form: each pair of the list is evaluated once per substep
+// (k_dem_pairs64) and a gather kernel adds it to both partners in an order
+// fixed by the list (k_dem_gather64).  Mixed forms: a substep gives each
+// particle a group of LANES consecutive lanes of a warp: lane l takes the list
+// entries l, l + LANES, ... and the group's force and torque sums are combined
+// by warp shuffles (a fixed xor tree, so the result does not depend on the
+// launch shape); one thread per particle then adds the walls and integrates.
+// A particle that moves more than skin/2 before the next sort raises
+// DPS_ERR_UNSTABLE.  Candidate distances are screened in FP32 (a float
 // copy of the positions, refreshed every substep, with a margin far above its
 // rounding) and every pair that passes is evaluated exactly: in FP64 for the
 // FP64 form, and for the low-precision forms in FP32 except close to contact
@@ -480,11 +483,16 @@ constexpr int DEM_CHUNK = 256;
 // Mixed forms: lane groups of LANES lanes per particle walk its list; pairs
 // away from contact run in FP32 from the float copies, the rare pairs near
 // contact in FP64 (out of line), walls in phase B.
-// at most 128 registers a thread: two 256-thread blocks per SM (16 warps), the
-// occupancy the FP32 pair loop needs to hide its load latency (with 150
-// registers a dense settling box ran 1.3-1.7x slower)
+// The FP32 pair loop waits on the partners' loads, so warps count more than
+// registers: sized for eight 256-thread blocks per SM (32 registers a thread,
+// every warp slot; the rest spills to L1-resident local memory).  Measured
+// at 256^3, eps 0.2 / 0.4: DEM 35.2 / 102.6 ms per step with 128 registers,
+// 26.1 / 71.4 with 64, 23.4 / 64.4 with 32.
+#ifndef DPS_MIXED_MINB
+#define DPS_MIXED_MINB 8  // 256-thread blocks per SM the register budget is sized for
+#endif
 template <int LANES>
-__global__ void __launch_bounds__(256, 2) k_dem_substep_mixed(const BoxDev *__restrict__ boxes,
+__global__ void __launch_bounds__(256, DPS_MIXED_MINB) k_dem_substep_mixed(const BoxDev *__restrict__ boxes,
                                                            const Tile *__restrict__ tiles, int ntiles, int src_tmp,
                                                            int key_out) {
     __shared__ double sFT[6][DEM_CHUNK];
@@ -730,8 +738,11 @@ __global__ void __launch_bounds__(256) k_reverse_slots(const BoxDev *__restrict_
 // owner and n x F_t to the pair's slot.  Every owned slot gets its flag.
 constexpr int DQ_CAP = 512;
 
+#ifndef DPS_PAIRS_MINB
+#define DPS_PAIRS_MINB 2  // 256-thread blocks per SM the register budget is sized for
+#endif
 template <int LANES>
-__global__ void __launch_bounds__(256, 1) k_dem_pairs64(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
+__global__ void __launch_bounds__(256, DPS_PAIRS_MINB) k_dem_pairs64(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
                                                      int ntiles, int src_tmp) {
     __shared__ int qS[DQ_CAP], qJ[DQ_CAP], qP[DQ_CAP];
     __shared__ int ws[9];
@@ -830,8 +841,11 @@ __global__ void __launch_bounds__(256, 1) k_dem_pairs64(const BoxDev *__restrict
 // WALLS: some box of the batch has a wall axis (else the wall code is left
 // out: 128 registers instead of 168, more warps for a kernel that waits on
 // the scattered loads of the pair results)
+#ifndef DPS_GATHER_MINB
+#define DPS_GATHER_MINB 4  // 128-thread blocks per SM the register budget is sized for
+#endif
 template <bool WALLS>
-__global__ void __launch_bounds__(128, WALLS ? 1 : 4) k_dem_gather64(const BoxDev *__restrict__ boxes,
+__global__ void __launch_bounds__(128, WALLS ? 1 : DPS_GATHER_MINB) k_dem_gather64(const BoxDev *__restrict__ boxes,
                                                         const Tile *__restrict__ tiles, int ntiles, int src_tmp,
                                                         int key_out) {
     DPS_FOR_TILES(tiles, ntiles, t) {
