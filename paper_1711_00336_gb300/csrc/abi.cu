@@ -614,7 +614,7 @@ static void enqueue_step(Batch *B) {
                                         : part_threads(u, 1 << c);
                     launch_dem_substep(T, B->d_part + B->part_off[c], nt, sd & 1, sd == B->n_dem - 1,
                                        B->prec != DPS_F64, 1 << c, B->any_walls, grid_of(nt), blk, s);
-                    ndl += B->prec == DPS_F64 ? 2 : 1;  // FP64: pair kernel + gather kernel
+                    ndl += 2;  // pair kernel + gather / integration kernel
                 }
         tend(B, PH_DEM, ndl);
         if (fork) cudaStreamWaitEvent(s, B->ev_join, 0);
@@ -852,6 +852,7 @@ static size_t box_bytes(int prec, long long ncell, long long cap) {
     size_t N = (size_t)ncell, C = (size_t)(cap > 0 ? cap : 1);
     size_t b = 19 * N * pe + 27 * N * fe;
     b += 2 * (size_t)NPF * C * 8 + 2 * (size_t)NPI * C * 4 + 9 * C * 8 + 6 * C * 16 + C * 4 + 64 * C * 4 + 18 * C * 4;
+    if (prec != DPS_F64) b += 6 * C * 8;  // mixed-form pair sums
     if (prec == DPS_F64) b += 64 * C * 4 + 32 * C * (4 + 48 + 1);  // pair lists and results (64 partners)
     b += (3 * N + 1) * 4 + 3 * C * 4 + ((N + 8191) / 8192 + 1) * 4;
     b += 4096 + (size_t)reduce_partials_doubles() * 8;
@@ -910,6 +911,7 @@ static int box_create(Batch *B, const int n[3], const int per[3], double tau, do
     d.lowp = B->prec != DPS_F64;
     d.pwf = d.lowp ? (float *)A(9 * cap * 4) : nullptr;
     d.f32p = d.lowp ? (float *)A(6 * cap * 4) : nullptr;
+    d.psum = d.lowp ? (double *)A(6 * cap * 8) : nullptr;
     d.nlist = nullptr;  // sized at preparation (depends on the closure)
     d.maxn = 0;
     d.hj = d.rrow = nullptr;
@@ -1711,7 +1713,7 @@ static long long b_launches_per_step(Batch *B) {
     const int n_int = B->boxes.empty() ? 1 : B->boxes[0]->cl.n_int;
     const int n_dem = B->boxes.empty() ? 1 : B->boxes[0]->cl.n_dem;
     const int f64 = B->prec == DPS_F64;
-    return 2 + 2 + (long long)n_int * (2 * pl + 2 + pl * n_dem * (1 + f64) + 3 + (5 + 2 * f64) * pl + 1 + 1);
+    return 2 + 2 + (long long)n_int * (2 * pl + 2 + pl * n_dem * 2 + 3 + (5 + 2 * f64) * pl + 1 + 1);
 }
 
 int dps_set_timing(dps_handle h, int enable) { return h ? b_set_timing(&h->B, enable) : DPS_ERR_ARG; }

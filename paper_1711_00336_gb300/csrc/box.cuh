@@ -47,6 +47,7 @@ struct BoxDev {
     int lowp;          // 1: low-precision form (FP32 coupling arithmetic)
     float *pwf;        // FP32 kernel weights [9][cap] (low-precision forms)
     float *f32p;       // FP32 copies of F_am (3 planes) and F_d (3 planes) [6][cap]
+    double *psum;      // mixed-form DEM: pair sums of a substep, force and torque [6][cap]
     // linked cells
     int *cell_start, *count, *fill, *key, *tmp, *perm;
     int *scan_part;    // per scan tile partial sums of this box

@@ -473,30 +473,24 @@ __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<
     if (nlim) atomicAdd(&Bx.counters[CNT_LUB_LIMITED], (unsigned long long)nlim);
 }
 
-// ---- the substep ------------------------------------------------------------------
+// ---- the substep of the mixed forms ----------------------------------------------------
 // src_tmp = 0: read x/u/w (and the float positions) from the current set,
-// write the ping-pong buffers; src_tmp = 1: the other way round.  A tile is
-// taken in chunks of particles: phase A sums each particle's partner forces
-// and torques into shared memory, phase B integrates one particle per thread.
-constexpr int DEM_CHUNK = 256;
-
-// Mixed forms: lane groups of LANES lanes per particle walk its list; pairs
-// away from contact run in FP32 from the float copies, the rare pairs near
-// contact in FP64 (out of line), walls in phase B.
-// The FP32 pair loop waits on the partners' loads, so warps count more than
-// registers: sized for eight 256-thread blocks per SM (32 registers a thread,
-// every warp slot; the rest spills to L1-resident local memory).  Measured
-// at 256^3, eps 0.2 / 0.4: DEM 35.2 / 102.6 ms per step with 128 registers,
-// 26.1 / 71.4 with 64, 23.4 / 64.4 with 32.
+// write the ping-pong buffers; src_tmp = 1: the other way round.
+// k_dem_pairsum_mixed: lane groups of LANES lanes per particle walk its list;
+// pairs away from contact run in FP32 from the float copies, the rare pairs
+// near contact in FP64 (out of line); the group's sums (a fixed xor tree) go
+// to psum[6][cap] (force, torque) and the lubrication-cap count to the
+// counters.  k_dem_integrate then adds the walls and integrates, one thread
+// per particle.  Two kernels so that each has its own register budget: the
+// pair loop waits on the partners' loads and needs every warp slot of the SM,
+// the FP64 update needs registers.
 #ifndef DPS_MIXED_MINB
-#define DPS_MIXED_MINB 8  // 256-thread blocks per SM the register budget is sized for
+#define DPS_MIXED_MINB 8  // 256-thread blocks per SM the register budget of the pair loop is sized for
 #endif
 template <int LANES>
-__global__ void __launch_bounds__(256, DPS_MIXED_MINB) k_dem_substep_mixed(const BoxDev *__restrict__ boxes,
-                                                           const Tile *__restrict__ tiles, int ntiles, int src_tmp,
-                                                           int key_out) {
-    __shared__ double sFT[6][DEM_CHUNK];
-    __shared__ unsigned sN[DEM_CHUNK];
+__global__ void __launch_bounds__(256, DPS_MIXED_MINB) k_dem_pairsum_mixed(const BoxDev *__restrict__ boxes,
+                                                                       const Tile *__restrict__ tiles, int ntiles,
+                                                                       int src_tmp) {
     const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
     DPS_FOR_TILES(tiles, ntiles, t) {
         const Tile tl = tiles[t];
@@ -507,89 +501,97 @@ __global__ void __launch_bounds__(256, DPS_MIXED_MINB) k_dem_substep_mixed(const
         const Phys &ph = Bx.ph;
         const float rng_extra_f = (float)(ph.lubrication ? fmax(ph.h_c, 0.0) : 0.0);
         const float Lf[3] = {(float)g.n[0], (float)g.n[1], (float)g.n[2]};
-        const PairPar<double> pd = pair_par<double>(ph);
         const PairPar<float> pfl = pair_par<float>(ph);
-        for (long long cb = tl.begin; cb < tl.end; cb += DEM_CHUNK) {
-            const long long ce = cb + DEM_CHUNK < tl.end ? cb + DEM_CHUNK : tl.end;
-            // phase A: the trip count is uniform over the block, so every lane
-            // reaches the shuffles
-            for (long long base = cb; base < ce; base += ngrp) {
-                const long long i = base + grp;
-                const bool act = i < ce;
-                double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-                float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};
-                unsigned nlim = 0;
-                bool near = false;  // this lane evaluated an FP64 pair
-                if (act) {
-                    const float4 pi = fin[i], vi = vin[i], oi = oin[i];
-                    const int nn = Bx.nlist_n[i];
-                    const int *row = Bx.nlist + i * (long long)Bx.maxn;
-                    for (int k = lane; k < nn; k += LANES) {
-                        const int j = row[k];
-                        const float4 pj = fin[j];
-                        const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
-                        const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
-                        const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
-                        const float sumr_f = 0.5f * (pi.w + pj.w);
-                        const float fr = sumr_f + rng_extra_f + SCREEN_MARGIN;
-                        const float d2f = fx * fx + fy * fy + fz * fz;
-                        if (!(d2f < fr * fr)) continue;
-                        // away from contact: the whole pair in FP32 from the float copies
-                        const float distf = sqrtf(d2f);
-                        if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
-                            if (!(distf < sumr_f + rng_extra_f)) continue;
-                            const float4 vj = vin[j], oj = oin[j];
-                            const float inv = 1.0f / distf;
-                            const float n[3] = {fx * inv, fy * inv, fz * inv};
-                            const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
-                            const float uj[3] = {vj.x, vj.y, vj.z};
-                            const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
-                            const float m_ij = vi.w * vj.w / (vi.w + vj.w);
-                            const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
-                            partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf,
-                                           nlim);
-                            continue;
-                        }
-                        // near contact: exact separation and forces in FP64
-                        near = true;
-                        pair64_out(Bx, xin, i, j, F, T, nlim);
+        const long long cap = Bx.cap;
+        // the trip count is uniform over the block, so every lane reaches the shuffles
+        for (long long base = tl.begin; base < tl.end; base += ngrp) {
+            const long long i = base + grp;
+            const bool act = i < tl.end;
+            double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+            float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};
+            unsigned nlim = 0;
+            bool near = false;  // this lane evaluated an FP64 pair
+            if (act) {
+                const float4 pi = fin[i], vi = vin[i], oi = oin[i];
+                const int nn = Bx.nlist_n[i];
+                const int *row = Bx.nlist + i * (long long)Bx.maxn;
+                for (int k = lane; k < nn; k += LANES) {
+                    const int j = row[k];
+                    const float4 pj = fin[j];
+                    const float fx = min_image_f(pj.x - pi.x, Lf[0], g.per[0]);
+                    const float fy = min_image_f(pj.y - pi.y, Lf[1], g.per[1]);
+                    const float fz = min_image_f(pj.z - pi.z, Lf[2], g.per[2]);
+                    const float sumr_f = 0.5f * (pi.w + pj.w);
+                    const float fr = sumr_f + rng_extra_f + SCREEN_MARGIN;
+                    const float d2f = fx * fx + fy * fy + fz * fz;
+                    if (!(d2f < fr * fr)) continue;
+                    // away from contact: the whole pair in FP32 from the float copies
+                    const float distf = sqrtf(d2f);
+                    if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
+                        if (!(distf < sumr_f + rng_extra_f)) continue;
+                        const float4 vj = vin[j], oj = oin[j];
+                        const float inv = 1.0f / distf;
+                        const float n[3] = {fx * inv, fy * inv, fz * inv};
+                        const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
+                        const float uj[3] = {vj.x, vj.y, vj.z};
+                        const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
+                        const float m_ij = vi.w * vj.w / (vi.w + vj.w);
+                        const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
+                        partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf, nlim);
+                        continue;
                     }
+                    // near contact: exact separation and forces in FP64
+                    near = true;
+                    pair64_out(Bx, xin, i, j, F, T, nlim);
                 }
-                if (LANES > 1) {
-                    // FP64 sums only when some lane of the warp met a pair near contact
-                    const bool red64 = __any_sync(0xffffffffu, near);
+            }
+            if (LANES > 1) {
+                // FP64 sums only when some lane of the warp met a pair near contact
+                const bool red64 = __any_sync(0xffffffffu, near);
 #pragma unroll
-                    for (int o = LANES / 2; o > 0; o >>= 1) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            if (red64) {
-                                F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
-                                T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
-                            }
-                            Ff[a] += __shfl_xor_sync(0xffffffffu, Ff[a], o);
-                            Tf[a] += __shfl_xor_sync(0xffffffffu, Tf[a], o);
-                        }
-                        nlim += __shfl_xor_sync(0xffffffffu, nlim, o);
-                    }
-                }
-                if (act && lane == 0) {
-                    const int s = (int)(i - cb);
+                for (int o = LANES / 2; o > 0; o >>= 1) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        sFT[a][s] = F[a] + (double)Ff[a];
-                        sFT[3 + a][s] = T[a] + (double)Tf[a];
+                        if (red64) {
+                            F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
+                            T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
+                        }
+                        Ff[a] += __shfl_xor_sync(0xffffffffu, Ff[a], o);
+                        Tf[a] += __shfl_xor_sync(0xffffffffu, Tf[a], o);
                     }
-                    sN[s] = nlim;
+                    nlim += __shfl_xor_sync(0xffffffffu, nlim, o);
                 }
             }
-            __syncthreads();
-            // phase B: walls and integration, one particle per thread
-            for (long long i = cb + threadIdx.x; i < ce; i += blockDim.x) {
-                const int s = (int)(i - cb);
-                double F[3] = {sFT[0][s], sFT[1][s], sFT[2][s]}, T[3] = {sFT[3][s], sFT[4][s], sFT[5][s]};
-                finish_particle<true>(Bx, pd, i, src_tmp, F, T, sN[s], key_out);
+            if (act && lane == 0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    Bx.psum[a * cap + i] = F[a] + (double)Ff[a];
+                    Bx.psum[(3 + a) * cap + i] = T[a] + (double)Tf[a];
+                }
+                if (nlim) atomicAdd(&Bx.counters[CNT_LUB_LIMITED], (unsigned long long)nlim);
             }
-            __syncthreads();
+        }
+    }
+}
+
+// walls and Eq. particle_motion of the mixed forms, one thread per particle
+template <bool WALLS>
+__global__ void __launch_bounds__(128) k_dem_integrate(const BoxDev *__restrict__ boxes,
+                                                                     const Tile *__restrict__ tiles, int ntiles,
+                                                                     int src_tmp, int key_out) {
+    DPS_FOR_TILES(tiles, ntiles, t) {
+        const Tile tl = tiles[t];
+        const BoxDev &Bx = boxes[tl.box];
+        const long long cap = Bx.cap;
+        const PairPar<double> pd = pair_par<double>(Bx.ph);
+        for (long long i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            double F[3], T[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                F[a] = Bx.psum[a * cap + i];
+                T[a] = Bx.psum[(3 + a) * cap + i];
+            }
+            finish_particle<WALLS>(Bx, pd, i, src_tmp, F, T, 0u, key_out);
         }
     }
 }
@@ -903,12 +905,16 @@ void launch_build_nlist(const BoxDev *boxes, const Tile *tiles, int ntiles, int 
 // cells and their counts for the sort that follows
 void launch_dem_substep(const BoxDev *boxes, const Tile *tiles, int ntiles, int src_tmp, int key_out, int mixed,
                         int lanes, int walls, int grid, int block, cudaStream_t s) {
-#define DPS_DEM(K, L) K<L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp, key_out)
+#define DPS_DEM(K, L) K<L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp)
     if (mixed) {
-        if (lanes >= 8) DPS_DEM(k_dem_substep_mixed, 8);
-        else if (lanes == 4) DPS_DEM(k_dem_substep_mixed, 4);
-        else if (lanes == 2) DPS_DEM(k_dem_substep_mixed, 2);
-        else DPS_DEM(k_dem_substep_mixed, 1);
+        if (lanes >= 8) DPS_DEM(k_dem_pairsum_mixed, 8);
+        else if (lanes == 4) DPS_DEM(k_dem_pairsum_mixed, 4);
+        else if (lanes == 2) DPS_DEM(k_dem_pairsum_mixed, 2);
+        else DPS_DEM(k_dem_pairsum_mixed, 1);
+        if (walls)
+            k_dem_integrate<true><<<grid, 128, 0, s>>>(boxes, tiles, ntiles, src_tmp, key_out);
+        else
+            k_dem_integrate<false><<<grid, 128, 0, s>>>(boxes, tiles, ntiles, src_tmp, key_out);
     } else {
 #define DPS_PAIRS(L) k_dem_pairs64<L><<<grid, block, 0, s>>>(boxes, tiles, ntiles, src_tmp)
         if (lanes >= 8) DPS_PAIRS(8);
