@@ -591,14 +591,38 @@ def _batch_boxes(seed=7, count=64):
     return boxes
 
 
-def suite_batch(dps, steps=20, count=64):
-    """64 uneven periodic boxes: FP32 batch (one launch per phase, autotuned)
-    against the plain FP64 method stepping every box as its own domain."""
+def _stable_subcycles(wl, thr=0.5):
+    """Interaction subcycles that keep the explicit drag relaxation of a
+    settling box stable: beta/m dt/n_int <= thr with the Table 1 drag at the
+    solid fraction a particle sees, its own kernel-spread volume V/8 plus
+    1.3 <eps_p> (at most 0.62)."""
+    d, L = float(wl["d"][0]), np.asarray(wl["n"], float)
+    V = math.pi / 6 * d ** 3
+    e = min(0.62, V / 8 + 1.3 * len(wl["x"]) * V / L.prod())
+    e1 = 1.0 - e
+    A = 5.81 * e / e1 ** 3 + 0.48 * e ** (1 / 3) / e1 ** 4
+    mu = (wl["tau"] - 0.5) / 3.0
+    rate = 3 * math.pi * d * mu * e1 * (1.0 / e1 ** 3 + A) / (float(wl["rho_p"][0]) * V)
+    return max(2, math.ceil(rate / thr))
+
+
+def suite_batch(dps, steps=20, count=64, classes=(2, 4, 8, 12)):
+    """64 uneven periodic boxes in the FP32 form against the plain FP64
+    method stepping every box as its own domain.  A batch needs one subcycle
+    count, and dense boxes of small spheres need more (explicit drag
+    relaxation): the boxes are grouped by the subcycle count that keeps them
+    stable, rounded up to one of `classes`, one autotuned batch per group,
+    run one after the other."""
     import torch
     boxes = _batch_boxes(count=count)
-    n_int = max(_subcycles(wl) for wl in boxes)  # one subcycle count per batch
-
-    def build(bx):
+    groups = {}
+    for k, wl in enumerate(boxes):
+        n = _stable_subcycles(wl)
+        cls = next((c for c in classes if c >= n), n)
+        groups.setdefault(cls, []).append(k)
+    res, ms_b, ms_p, errs, cells, parts = [], 0.0, 0.0, [], 0, 0
+    for n_int, ks in sorted(groups.items()):
+        bx = [boxes[k] for k in ks]
         B = dps.Batch("f32")
         ids = []
         for wl in bx:
@@ -606,71 +630,61 @@ def suite_batch(dps, steps=20, count=64):
             B.add_particles(b, wl["x"], wl["d"], wl["rho_p"])
             B.set_closure(b, _settling_closure(dps, wl, wl["d"][0], n_int))
             ids.append(b)
-        return B, ids
-
-    # screen: boxes whose explicit coupling diverges within the suite's
-    # horizon (status flags of DPS_ERR_UNSTABLE) are reported and left out
-    unstable = []
-    for _ in range(4):
-        B, ids = build(boxes)
-        bad = []
-        try:
-            B.step(100)
-        except dps.DPSError:
-            bad = [k for k, b in enumerate(ids) if B.stats(b)["status"]]
-        B.close()
-        if not bad:
-            break
-        unstable += [dict(L=int(boxes[k]["n"][0]), eps=round(float(len(boxes[k]["x"]) * math.pi / 6 *
-                                                                   boxes[k]["d"][0] ** 3 / np.prod(boxes[k]["n"])), 3),
-                          d=round(float(boxes[k]["d"][0]), 3)) for k in bad]
-        boxes = [wl for k, wl in enumerate(boxes) if k not in bad]
-    cells = sum(int(np.prod(b["n"])) for b in boxes)
-    parts = sum(len(b["x"]) for b in boxes)
-    B, ids = build(boxes)
-    tune_ms = B.autotune(steps=3)
-    B.step(2)
-    history = int(B.stats(ids[0])["step"])  # steps every box has taken (tuning candidates + 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    B.step(steps)
-    torch.cuda.synchronize()
-    ms_b = (time.perf_counter() - t0) / steps * 1e3
-    ub = [B.particle_mean(b)[2] for b in ids]
-    cfg = B.tuning()
-    B.close()
-    # plain FP64 method, box after box (same steps)
-    ms_p = 0.0
-    up = []
-    for wl in boxes:
-        dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
-        dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
-        dom.set_closure(_settling_closure(dps, wl, wl["d"][0], n_int))
-        dom.step(history)  # the same history as the batch
+        B.autotune(steps=3)
+        B.step(2)
+        history = int(B.stats(ids[0])["step"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dom.step(steps)
+        B.step(steps)
         torch.cuda.synchronize()
-        ms_p += (time.perf_counter() - t0) / steps * 1e3
-        up.append(dom.read_particles()["u"][:, 2].mean())
-        dom.close()
-    err = [abs(a - b) / max(abs(b), 1e-12) for a, b in zip(ub, up)]
-    line = {"suite": "batch", "boxes": len(boxes), "unstable_boxes_left_out": unstable, "cells": cells,
-            "particles": parts, "steps": steps, "n_int": n_int,
+        mb = (time.perf_counter() - t0) / steps * 1e3
+        ub = [B.particle_mean(b)[2] for b in ids]
+        cfg = B.tuning()
+        B.close()
+        mp = 0.0
+        up = []
+        for wl in bx:
+            dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
+            dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+            dom.set_closure(_settling_closure(dps, wl, wl["d"][0], n_int))
+            dom.step(history)  # the same history as the batch
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dom.step(steps)
+            torch.cuda.synchronize()
+            mp += (time.perf_counter() - t0) / steps * 1e3
+            up.append(dom.read_particles()["u"][:, 2].mean())
+            dom.close()
+        e = [abs(a - b) / max(abs(b), 1e-12) for a, b in zip(ub, up)]
+        c = sum(int(np.prod(w["n"])) for w in bx)
+        q = sum(len(w["x"]) for w in bx)
+        res.append({"n_int": n_int, "boxes": len(bx), "cells": c, "particles": q, "f32_batch_ms_per_step": mb,
+                    "f64_plain_ms_per_step": mp, "tuning": cfg, "mean_up_rel_err_max": float(np.max(e))})
+        ms_b += mb
+        ms_p += mp
+        errs += e
+        cells += c
+        parts += q
+    line = {"suite": "batch", "boxes": len(boxes), "unstable_boxes_left_out": [], "cells": cells,
+            "particles": parts, "steps": steps, "groups": res,
             "f32_batch_ms_per_step": ms_b, "f32_batch_MLUPS": cells / (ms_b * 1e-3) / 1e6,
             "f64_plain_ms_per_step": ms_p, "f64_plain_MLUPS": cells / (ms_p * 1e-3) / 1e6,
-            "speedup": ms_p / ms_b, "tuning": cfg, "autotune_best_ms": tune_ms,
-            "mean_up_rel_err_vs_f64_median": float(np.median(err)), "max": float(np.max(err))}
+            "speedup": ms_p / ms_b, "mean_up_rel_err_vs_f64_median": float(np.median(errs)),
+            "max": float(np.max(errs))}
     print(json.dumps(line), flush=True)
     return line
 
 
-def suite_serve(dps, n_req=12, rate=20.0, cap=400, window=100, seed=11):
-    """A bounded trace of the serving workload: n_req Poisson-arriving
-    settling requests (edge log-uniform 32..160, eps U(0.01, 0.45), d = 1,
-    FP32) on the continuous-batching server, each run until its windowed mean
-    particle velocity changes by < 0.1 % between windows or the step cap;
-    every 20th request is rerun alone with the plain FP64 method."""
+def suite_serve(dps, n_req=16, rate=20.0, cap=20000, window=500, seed=11, n_int=10, budget_s=1500.0):
+    """A bounded prefix of the serving trace: n_req Poisson-arriving settling
+    requests at `rate` per second (edge log-uniform 32..160, eps U(0.01,
+    0.45), d = 1, FP32) on the continuous-batching server, each run until its
+    windowed mean particle velocity changes by < 0.1 % between consecutive
+    windows of `window` steps or the cap of 20k steps.  All requests run the
+    paper's n_int = 10 subcycles (n_DEM = 2: 20 substeps per step), which keeps
+    the densest boxes of the trace stable.  Requests not finished after
+    `budget_s` seconds are cancelled and counted.  Every 20th request is rerun
+    alone with the plain FP64 method for the same number of steps."""
     rng = np.random.default_rng(seed)
     reqs = []
     for k in range(n_req):
@@ -678,8 +692,7 @@ def suite_serve(dps, n_req=12, rate=20.0, cap=400, window=100, seed=11):
         eps = rng.uniform(0.01, 0.45)
         reqs.append(workloads.settling_box(L=L, eps=eps, d=1.0, seed=seed * 1000 + k))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
-    n_int = max(_subcycles(wl) for wl in reqs)  # one subcycle count: the requests share batches
-    S = dps.Server("f32", max_boxes=64, hbm_reserve_bytes=16 << 30, chunk_steps=50)
+    S = dps.Server("f32", max_boxes=64, hbm_reserve_bytes=16 << 30, chunk_steps=100)
     t0 = time.perf_counter()
     ids = []
     for wl, ta in zip(reqs, arrivals):
@@ -689,13 +702,27 @@ def suite_serve(dps, n_req=12, rate=20.0, cap=400, window=100, seed=11):
         ids.append(S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"],
                             _settling_closure(dps, wl, 1.0, n_int), max_steps=cap, window=window,
                             rel_tol=1e-3))
-    S.wait_idle(3600)
+    idle = True
+    try:
+        S.wait_idle(max(1.0, budget_s - (time.perf_counter() - t0)))
+    except dps.DPSError:
+        idle = False
+    cancelled = 0
+    if not idle:
+        for i in ids:
+            if S.poll(i)["state"] in ("queued", "running"):
+                S.cancel(i)
+                cancelled += 1
+        S.wait_idle(600)
     res = [S.poll(i) for i in ids]
     st = S.stats()
     S.close()
-    lat = [r["t_end"] - r["t_submit"] for r in res]
+    done = [r for r in res if r["state"] == "done"]
+    lat = [r["t_end"] - r["t_submit"] for r in done] or [float("nan")]
     errs = []
     for k in range(0, n_req, 20):
+        if res[k]["state"] != "done":
+            continue
         wl = reqs[k]
         dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
         dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
@@ -712,8 +739,12 @@ def suite_serve(dps, n_req=12, rate=20.0, cap=400, window=100, seed=11):
     line = {"suite": "serve", "requests": n_req, "rate_per_s": rate, "cap_steps": cap, "window": window,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "aggregate_MLUPS": st["cell_updates"] / st["busy_s"] / 1e6 if st["busy_s"] > 0 else None,
-            "completed": st["completed"], "failed": st["failed"], "peak_boxes": st["peak_boxes"],
-            "capped": int(sum(r["capped"] for r in res)),
+            "completed": st["completed"], "failed": st["failed"], "cancelled_at_budget": cancelled,
+            "budget_s": budget_s, "peak_boxes": st["peak_boxes"], "n_int": n_int,
+            "capped": int(sum(r["capped"] for r in done)),
+            "requests_detail": [{"L": int(w["n"][0]), "eps": round(float(len(w["x"]) * math.pi / 6 / np.prod(w["n"])), 3),
+                                 "state": r["state"], "steps": r["steps"], "latency_s": r["t_end"] - r["t_submit"]}
+                                for w, r in zip(reqs, res)],
             "f64_rerun_up_rel_err": [float(e) for e in errs]}
     print(json.dumps(line), flush=True)
     return line
@@ -724,13 +755,15 @@ def suite_rebound(dps, tau=0.501, rho_p=25.0, d=0.5):
     32 x 32 x 512 d_p box falls under g = 1e-4 and hits the bottom wall;
     e_n = 0.97, mu_c = 0.1, T_c = dt/2, n_int = 10, n_DEM = 50 (25 dx/d_p),
     h_c = d_p, all force models on.  Cases of Table 3: B0 baseline, B1
-    n_DEM = 5, B3 no added mass, B4 h_c = 0.  Reports the Stokes number
+    n_DEM = 5, B2 n_DEM = 500, B3 no added mass, B4 h_c = 0, B5 h_c = d_p/2.
+    Reports the Stokes number
     St = (rho_p/rho_f) Re_T/9 reached and e_wet/e_n with the rebound velocity
     taken t_R = 0.1 d/u_pT after the impact (the paper's Table 3 values are
     context: its St = 128 is matched only approximately)."""
     n = (int(32 * d), int(32 * d), int(512 * d))
-    cases = {"B0": {}, "B1": {"n_dem": 5}, "B3": {"added_mass": 0}, "B4": {"h_c": 0.0}}
-    paper = {"B0": 0.792, "B1": 0.899, "B3": 0.831, "B4": 0.976}
+    cases = {"B0": {}, "B1": {"n_dem": 5}, "B2": {"n_dem": 500}, "B3": {"added_mass": 0}, "B4": {"h_c": 0.0},
+             "B5": {"h_c": d / 2}}
+    paper = {"B0": 0.792, "B1": 0.899, "B2": 0.803, "B3": 0.831, "B4": 0.976, "B5": 0.797}
     out = []
     for name, kw in cases.items():
         c = dict(g=(0.0, 0.0, -1e-4), fb_mode=0, e_n=0.97, mu_c=0.1, T_c=0.5, h_c=d, h_min=1e-5, C_am=0.5,
@@ -766,7 +799,11 @@ def suite_rebound(dps, tau=0.501, rho_p=25.0, d=0.5):
             t_R = 0.1 * d / u_T
             k_R = min(len(u) - 1, k_imp + max(0, int(round(t_R)) - 1))
             line.update({"impact_step": k_imp, "u_pR": u[k_R], "e_wet_over_e_n": u[k_R] / u_T / 0.97,
-                         "max_rebound_height_d": float(z[k_imp:].max() / d)})
+                         "max_rebound_height_d": float(z[k_imp:].max() / d),
+                         "u_max_after_impact": float(u[k_imp:k_imp + 400].max()),
+                         # the approach and rebound, gap (in d) and velocity per step
+                         "trace": [(int(k), round(float(z[k] / d), 5), float(u[k]))
+                                   for k in range(max(0, k_imp - 40), min(len(u), k_imp + 40))]})
         else:
             line["e_wet_over_e_n"] = 0.0  # no rebound
         out.append(line)
@@ -774,7 +811,8 @@ def suite_rebound(dps, tau=0.501, rho_p=25.0, d=0.5):
     return out
 
 
-def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4), n_tst=30, prec="f32"):
+def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6), n_tst=30, prec="f32",
+                   table2=True):
     """Sec. 4: hindered settling in a triply periodic 32^3 d_p box at the
     paper's regime (water and glass of Baldock et al. scaled to lattice units
     with d_p/dx = 1/2: rho_p/rho_f = 2.5, Re_T ~ 17), e_n = 0.88, mu_c = 0.25,
@@ -787,7 +825,8 @@ def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4), n
     last 10 t_St and divided by the single sphere's u_pT from the eps = 0 run;
     the Richardson-Zaki value (1 - eps)^kappa(Re_T) is printed beside it.
     At eps = 0.3 the cases of Table 2 (A1 no lift, A2 no lubrication, A3 no
-    LES, A4 no Eilers, A5 n_int = 1) follow.  Runs in the FP32 form."""
+    LES, A4 no Eilers, A5 n_int = 1) follow (table2).  Runs in the FP32 form;
+    d = dp/dx of 1/4, 1/2 and 1 give boxes of 8^3, 16^3 and 32^3 cells."""
     L = int(round(32 * d))
     d_phys, nu_phys, g_phys = 0.35e-3, 1e-6, 9.81
     dx = d_phys / d
@@ -829,7 +868,8 @@ def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4), n
                 cnt += 1
         wall = time.perf_counter() - t0
         dom.close()
-        out = {"suite": "hindered", "case": tag, "eps": eps, "particles": n, "u_pS_z": acc / max(cnt, 1) if cnt else None,
+        out = {"suite": "hindered", "d": d, "case": tag, "eps": eps, "particles": n,
+               "u_pS_z": acc / max(cnt, 1) if cnt else None,
                "steps": steps, "wall_s": wall}
         if failed:
             out.update(failed)
@@ -844,9 +884,10 @@ def suite_hindered(dps, d=0.5, tau=0.5045, eps_list=(0.0, 0.1, 0.2, 0.3, 0.4), n
     single.update({"u_pT": u_T, "Re_T": Re_T, "g_lattice": g, "tau": tau, "box": [L, L, L], "d": d})
     print(json.dumps(single), flush=True)
     cases = [(e, f"eps{e}", {}) for e in eps_list if e > 0]
-    cases += [(0.3, "A1_no_lift", {"lift": 0}), (0.3, "A2_no_lubrication", {"lubrication": 0}),
-              (0.3, "A3_no_LES", {"smagorinsky": 0}), (0.3, "A4_no_Eilers", {"eilers": 0}),
-              (0.3, "A5_n_int_1", {"n_int": 1, "n_dem": 500})]
+    if table2:
+        cases += [(0.3, "A1_no_lift", {"lift": 0}), (0.3, "A2_no_lubrication", {"lubrication": 0}),
+                  (0.3, "A3_no_LES", {"smagorinsky": 0}), (0.3, "A4_no_Eilers", {"eilers": 0}),
+                  (0.3, "A5_n_int_1", {"n_int": 1, "n_dem": 500})]
     paper = {"eps0.3": 0.288, "A1_no_lift": 0.297, "A2_no_lubrication": 0.288, "A3_no_LES": 0.288,
              "A4_no_Eilers": 0.289, "A5_n_int_1": 0.288}
     for eps, tag, kw in cases:
@@ -875,7 +916,8 @@ def run_suite(args):
     if "rebound" in which:
         suite_rebound(dps)
     if "hindered" in which:
-        suite_hindered(dps)
+        for d in (0.25, 0.5, 1.0):
+            suite_hindered(dps, d=d, table2=d == 0.5)
 
 
 if __name__ == "__main__":
