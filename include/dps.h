@@ -312,7 +312,7 @@ int dps_batch_state_size(dps_batch b, int box, size_t *bytes);
 int dps_batch_save_box(dps_batch b, int box, void *buf, size_t cap);
 int dps_batch_load_box(dps_batch b, int box, const void *buf, size_t size);
 /* launch shape: cfg = {cell threads/block, cells/tile, particle threads/block,
- * particles/tile, collide-stream variant 0 ... 5 (register budget and cells
+ * particles/tile, collide-stream variant 0 ... 7 (register budget and cells
  * per thread of the low-precision forms; ignored in FP64)} */
 int dps_batch_set_tuning(dps_batch b, const int cfg[5]);
 int dps_batch_get_tuning(dps_batch b, int cfg[5]);

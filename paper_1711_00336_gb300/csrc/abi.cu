@@ -106,7 +106,7 @@ enum { PH_MOM = 0, PH_FAM, PH_RAM, PH_FDRAG, PH_RDRAG, PH_DEM, PH_SORT, PH_EPS, 
 struct Tuning {
     int cell_block = 128, cell_tile = 1024;   // threads per block, cells per tile
     int part_block = 128, part_tile = 256;    // threads per block, particles per tile
-    int k1v = 3;                              // collide-stream variant (FP32/FP16: 2 cells per thread)
+    int k1v = 6;                              // collide-stream variant (FP32/FP16: vector cell pairs)
 };
 
 struct Batch {
@@ -783,9 +783,10 @@ static int run_steps(Batch *B, long long n) {
 // ---- boxes ------------------------------------------------------------------------------
 static int batch_init(Batch *B, int precision, void *stream, dps_alloc_fn a, dps_free_fn f, void *ctx) {
     B->prec = precision;
-    // collide-stream default: two cells per thread, 3 or 4 blocks per SM
-    // (measured at 256^3: 5.4 TB/s for FP32, 3.0 TB/s for FP16)
-    B->tune.k1v = precision == DPS_F16S ? 4 : 3;
+    // collide-stream default: adjacent cell pairs moved as two-element
+    // vectors, 4 blocks per SM (measured at 256^3: FP32 6.2 TB/s, FP16s
+    // 4.7 TB/s; two scalar cells per thread: 5.4 and 3.0 TB/s)
+    B->tune.k1v = 6;
     B->pdf_elem = precision == DPS_F64 ? 8 : (precision == DPS_F32 ? 4 : 2);
     B->fel = precision == DPS_F64 ? 8 : 4;
     B->alloc = a;
@@ -1889,7 +1890,7 @@ int dps_batch_set_tuning(dps_batch b, const int cfg[5]) {
         if (cfg[k] < 32 || cfg[k] > (1 << 20)) FAILB(&b->B, DPS_ERR_ARG, "invalid launch shape");
     if (cfg[0] > 256 || cfg[2] > 256 || (cfg[0] & 31) || (cfg[2] & 31))
         FAILB(&b->B, DPS_ERR_ARG, "threads per block must be a multiple of 32, at most 256");
-    if (cfg[4] < 0 || cfg[4] > 5) FAILB(&b->B, DPS_ERR_ARG, "collide-stream variant must be 0 ... 5");
+    if (cfg[4] < 0 || cfg[4] > 7) FAILB(&b->B, DPS_ERR_ARG, "collide-stream variant must be 0 ... 7");
     int rc = pull_state(&b->B);
     if (rc) return rc;
     b->B.tune = Tuning{cfg[0], cfg[1], cfg[2], cfg[3], cfg[4]};
@@ -1946,7 +1947,7 @@ static int autotune(Batch *B, int steps, double *best_ms) {
     }
     if (!rc && B->prec != DPS_F64) {
         const int v0 = best.k1v;  // timed with the launch shapes above
-        for (int v = 0; v < 6; ++v) {
+        for (int v = 0; v < 8; ++v) {
             if (v == v0) continue;
             Tuning t = best;
             t.k1v = v;

@@ -166,7 +166,10 @@ __device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T di
 // list is in lane-major row order whatever the launch shape.
 constexpr int NL_CACHE = 8;  // partners per lane kept between the two passes
 
-__global__ void __launch_bounds__(256) k_build_nlist(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
+#ifndef DPS_NLIST_MINB
+#define DPS_NLIST_MINB 4  // 256-thread blocks per SM the register budget is sized for (a latency-bound search)
+#endif
+__global__ void __launch_bounds__(256, DPS_NLIST_MINB) k_build_nlist(const BoxDev *__restrict__ boxes, const Tile *__restrict__ tiles,
                                                      int ntiles) {
     __shared__ int nl_cache[256][NL_CACHE];
     DPS_FOR_TILES(tiles, ntiles, t) {

@@ -159,6 +159,113 @@ __device__ __forceinline__ void collide_stream_cell2(ST *__restrict__ pdf, const
                                                        omega_box, kf_box, tau, vmode, status, mom2);
 }
 
+// two-element vectors of the stored type (low-precision forms): float2 or
+// half2, converted exactly to and from the FP32 arithmetic (the FP16 stores
+// round each element to nearest even, as the scalar stores do)
+template <typename ST> struct Vec2;
+template <> struct Vec2<float> {
+    __device__ static inline void load(const float *p, float &a, float &b) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static inline void store(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+};
+template <> struct Vec2<double> {  // for completeness: the FP64 form keeps the scalar variant
+    __device__ static inline void load(const double *p, double &a, double &b) {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static inline void store(double *p, double a, double b) {
+        *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+    }
+};
+template <> struct Vec2<__half> {
+    __device__ static inline void load(const __half *p, float &a, float &b) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static inline void store(__half *p, float a, float b) {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+    }
+};
+
+template <typename ST, typename CT, bool VISC, bool MOMIN>
+__device__ __forceinline__ void relax_cell(CT f[Q], CT e, CT fpx, CT fpy, CT fpz, CT fbx, CT fby, CT fbz,
+                                           CT omega_box, CT kf_box, CT tau, int vmode, bool flag, int *status,
+                                           const CT *mom);
+
+// two cells c, c+1 of one x row (c even, nx even: the plane offsets, the
+// pair and every y / z neighbour offset are even), both without a wall
+// neighbour: a population whose memory offset keeps the pair aligned (even
+// parity: every one; odd parity: those with c_x = 0) moves as one
+// two-element vector, half the load and store instructions of the scalar
+// path; the x-moving populations of the odd parity stay scalar.  A pair next
+// to a wall takes the scalar path cell by cell.  The relaxation is that of
+// the scalar path, so the results are the same bits.
+template <typename ST, typename FT, typename CT, int PAR, bool VISC>
+__device__ __forceinline__ void collide_stream_vec2(ST *__restrict__ pdf, const FT *__restrict__ eps,
+                                                    const FT *__restrict__ fpf, const Geom &g, long long c, CT fbx,
+                                                    CT fby, CT fbz, CT omega_box, CT kf_box, CT tau, int vmode,
+                                                    int *status) {
+    const long long N = g.ncell;
+    int ix, iy, iz;
+    cell_coords(g, c, ix, iy, iz);
+    const NbDelta D = neighbour_deltas(g, ix, iy, iz), D1 = neighbour_deltas(g, ix + 1, iy, iz);
+    if (!no_wall_neighbour(D) || !no_wall_neighbour(D1)) {
+        collide_stream_cell<ST, FT, CT, PAR, VISC, false>(pdf, eps, fpf, nullptr, nullptr, g, c, fbx, fby, fbz,
+                                                          omega_box, kf_box, tau, vmode, status);
+        collide_stream_cell<ST, FT, CT, PAR, VISC, false>(pdf, eps, fpf, nullptr, nullptr, g, c + 1, fbx, fby, fbz,
+                                                          omega_box, kf_box, tau, vmode, status);
+        return;
+    }
+    const unsigned Nu = (unsigned)N, cu = (unsigned)c;
+    CT f[Q], f1[Q];
+    Vec2<ST>::load(pdf + cu, f[0], f1[0]);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        if (PAR == 0) {
+            Vec2<ST>::load(pdf + ((unsigned)q * Nu + cu), f[q], f1[q]);
+        } else if (CX(q) == 0) {
+            Vec2<ST>::load(pdf + ((unsigned)OPP(q) * Nu + cu + wall_free_delta(D, 0, -CY(q), -CZ(q))), f[q], f1[q]);
+        } else {
+            f[q] = Store<ST>::load(pdf + ((unsigned)OPP(q) * Nu + cu + wall_free_delta(D, -CX(q), -CY(q), -CZ(q))));
+            f1[q] = Store<ST>::load(pdf + ((unsigned)OPP(q) * Nu + cu + 1u +
+                                           wall_free_delta(D1, -CX(q), -CY(q), -CZ(q))));
+        }
+    }
+    const CT e0 = (CT)eps[c], e1 = (CT)eps[c + 1];
+    CT a[3], b[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a[k] = (CT)fpf[k * N + c];
+        b[k] = (CT)fpf[k * N + c + 1];
+    }
+    relax_cell<ST, CT, VISC, false>(f, e0, a[0], a[1], a[2], fbx, fby, fbz, omega_box, kf_box, tau, vmode, true,
+                                    status, nullptr);
+    relax_cell<ST, CT, VISC, false>(f1, e1, b[0], b[1], b[2], fbx, fby, fbz, omega_box, kf_box, tau, vmode, true,
+                                    status, nullptr);
+    Vec2<ST>::store(pdf + cu, f[0], f1[0]);
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+        if (PAR == 0) {
+            Vec2<ST>::store(pdf + ((unsigned)(k + 9) * Nu + cu), f[k], f1[k]);
+            Vec2<ST>::store(pdf + ((unsigned)k * Nu + cu), f[k + 9], f1[k + 9]);
+        } else if (CX(k) == 0) {
+            // (the offsets are summed in 32-bit unsigned arithmetic, where a
+            // negative neighbour delta wraps, before they move the pointer)
+            Vec2<ST>::store(pdf + ((unsigned)k * Nu + cu + wall_free_delta(D, 0, CY(k), CZ(k))), f[k], f1[k]);
+            Vec2<ST>::store(pdf + ((unsigned)(k + 9) * Nu + cu + wall_free_delta(D, 0, -CY(k), -CZ(k))), f[k + 9],
+                            f1[k + 9]);
+        } else {
+            store_pair_wall_free<ST, CT>(pdf, Nu, cu, D, k, f[k], f[k + 9]);
+            store_pair_wall_free<ST, CT>(pdf, Nu, cu + 1u, D1, k, f1[k], f1[k + 9]);
+        }
+    }
+}
+
 // Correctly rounded single operations: the relaxation below spells out every
 // multiply, add and fused multiply-add, so each K1 variant (register budget,
 // cells per thread) rounds exactly alike and a box's result does not depend on
@@ -288,7 +395,12 @@ __global__ void __launch_bounds__(128, MINB) k_collide_stream(const BoxDev *__re
         const CT tau = (CT)B.ph.tau;
         const int vmode = VISC ? (B.ph.eilers ? 1 : 0) | (B.ph.smag ? 2 : 0) : 0;
         int *st = B.status;
-        if (CPT == 1) {
+        if (CPT == 3 && sizeof(ST) < 8 && !MOMIN && !(g.n[0] & 1) && !(tl.begin & 1)) {
+            // vector pairs (c even; nx even, so the tile ends are even too)
+            for (long long c = tl.begin + 2 * threadIdx.x; c < tl.end; c += 2 * blockDim.x)
+                collide_stream_vec2<ST, FT, CT, PAR, VISC>(pdf, eps, fpf, g, c, fbx, fby, fbz, omega, kf, tau, vmode,
+                                                           st);
+        } else if (CPT == 1 || CPT == 3) {
             for (long long c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x)
                 collide_stream_cell<ST, FT, CT, PAR, VISC, MOMIN>(pdf, eps, fpf, rho_m, j_m, g, c, fbx, fby, fbz,
                                                                   omega, kf, tau, vmode, st);
@@ -504,7 +616,8 @@ static int grid_for(long long n, int block) {
 }
 
 // variant: register budget of K1 (blocks of 128 threads per SM the compiler
-// must fit) and cells per thread (variants 3, 4: two); chosen by the batch
+// must fit) and cells per thread (variants 3, 4, 5: two; 6, 7: two adjacent
+// cells moved as two-element vectors); chosen by the batch
 // autotuner.  visc: some box of the batch
 // relaxes with a per-cell tau_e (one register budget for that variant).
 template <typename ST, typename FT, typename CT>
@@ -543,6 +656,10 @@ void launch_collide_stream(const BoxDev *boxes, const Tile *tiles, int ntiles, i
         DPS_K1(4, 2);
     else if (variant == 5)
         DPS_K1(2, 2);
+    else if (variant == 6)
+        DPS_K1(4, 3);
+    else if (variant == 7)
+        DPS_K1(3, 3);
     else
         DPS_K1(4, 1);
 #undef DPS_K1

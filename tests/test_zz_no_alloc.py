@@ -62,3 +62,39 @@ def test_noalloc_sort_rejects_sizes_beyond_its_scratch():
     ids = torch.zeros(1, dtype=torch.int32, device="cuda")
     rc, _, _ = _noalloc(torch, L, n, (1, 1, 1), x, ids)
     assert rc == -1  # DPS_ERR_ARG
+
+
+def _pool_used_high(torch):
+    """high-water mark of the device's default stream-ordered memory pool
+    (reset to zero by the call), through the CUDA runtime the library uses"""
+    rt = ctypes.CDLL("libcudart.so.13")
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0
+    used_high = 0x8  # cudaMemPoolAttrUsedMemHigh
+    v = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolGetAttribute(pool, used_high, ctypes.byref(v)) == 0
+    zero = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolSetAttribute(pool, used_high, ctypes.byref(zero)) == 0
+    return v.value
+
+
+def test_noalloc_sort_takes_nothing_from_the_stream_ordered_pool_and_handles_no_particles():
+    """The allocating sort draws its scratch from the stream-ordered pool (the
+    pool's high-water mark rises); the allocation-free one leaves it at zero.
+    With no particles it returns all-zero offsets."""
+    torch, dps, L = _setup()
+    from paper_1711_00336_gb300 import workloads
+    n, per = (20, 16, 12), (1, 1, 1)
+    pr = workloads.random_particles(n, per, 800, 3)
+    x = torch.tensor(pr["x"], dtype=torch.float64, device="cuda")
+    ids = torch.arange(800, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    _pool_used_high(torch)  # reset
+    dps.op_cell_sort(n, per, x, ids)
+    torch.cuda.synchronize()
+    assert _pool_used_high(torch) > 0
+    rc, cs, order = _noalloc(torch, L, n, per, x, ids)
+    assert rc == 0
+    assert _pool_used_high(torch) == 0
+    rc, cs0, _ = _noalloc(torch, L, n, per, x[:0], ids[:0])
+    assert rc == 0 and int(cs0.abs().sum()) == 0
