@@ -863,26 +863,40 @@ __global__ void __launch_bounds__(128, WALLS ? 1 : DPS_GATHER_MINB) k_dem_gather
             const double lev = 0.5 * pf[PD * cap + i];
             double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
             const int h0 = Bx.hoff[i], nh = Bx.hn[i];
-            for (int c = 0; c < nh; ++c) {
-                const long long sl = h0 + c;
-                if (!Bx.pflag[sl]) continue;
-                const double *r = Bx.pres + 6 * sl;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    F[a] += r[a];
-                    T[a] += lev * r[3 + a];
-                }
-            }
             const int nr = Bx.rn[i];
             const int *rr = Bx.rrow + i * (long long)Bx.maxn;
-            for (int c = 0; c < nr; ++c) {
-                const int sl = rr[c];
-                if (sl < 0 || !Bx.pflag[sl]) continue;
-                const double *r = Bx.pres + 6 * (long long)sl;
+            // the entries in chunks of GC: the slot indices, flags and results
+            // of a chunk are loaded before any is added (the loads, not the
+            // additions, bound this kernel), a screened-out pair adding zero;
+            // the additions keep the list order
+            constexpr int GC = 4;
+            for (int c0 = 0; c0 < nh + nr; c0 += GC) {
+                long long sl[GC];
+                bool on[GC];
+                double sg[GC];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    F[a] -= r[a];
-                    T[a] += lev * r[3 + a];
+                for (int u = 0; u < GC; ++u) {
+                    const int c = c0 + u;
+                    const int s = c < nh ? h0 + c : (c < nh + nr ? rr[c - nh] : -1);
+                    sl[u] = s < 0 ? 0 : s;
+                    on[u] = s >= 0;
+                    sg[u] = c < nh ? 1.0 : -1.0;  // the owner's force, or its opposite on the partner
+                }
+#pragma unroll
+                for (int u = 0; u < GC; ++u) on[u] = on[u] && Bx.pflag[sl[u]];
+                double v[GC][6];
+#pragma unroll
+                for (int u = 0; u < GC; ++u)
+#pragma unroll
+                    for (int a = 0; a < 6; ++a) v[u][a] = on[u] ? Bx.pres[6 * sl[u] + a] : 0.0;
+#pragma unroll
+                for (int u = 0; u < GC; ++u) {
+                    if (!on[u]) continue;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        F[a] += sg[u] * v[u][a];
+                        T[a] += lev * v[u][3 + a];
+                    }
                 }
             }
             finish_particle<WALLS>(Bx, pd, i, src_tmp, F, T, 0u, key_out);
