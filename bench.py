@@ -507,13 +507,13 @@ def _subcycles(wl):
     return max(2, math.ceil(rate / 0.8))
 
 
-def _settling_closure(dps, wl, d, n_int=None):
+def _settling_closure(dps, wl, d, n_int=None, pressure=1):
     """Sec. 4 settling closure; n_int from _subcycles unless given, and
     n_int n_DEM >= 20 DEM substeps per step (10 per collision time T_c = dt/2)."""
     n_int = n_int or _subcycles(wl)
     return dps.closure(g=wl["g"], h_c=d, e_n=0.88, mu_c=0.25, T_c=0.5, h_min=1e-5, C_am=0.5, n_int=n_int,
                        n_dem=max(1, math.ceil(20 / n_int)), lub_limiter=1, lub_cap=0.25, eps_min=0.05, skin=0.5,
-                       fb_mode=1)
+                       fb_mode=1, pressure=pressure)
 
 
 def suite_precision(dps, steps=5, warmup=2, L=256, d=1.5, eps_list=(0.05, 0.2, 0.4)):
@@ -675,16 +675,21 @@ def suite_batch(dps, steps=20, count=64, classes=(2, 4, 8, 12)):
     return line
 
 
-def suite_serve(dps, n_req=16, rate=20.0, cap=20000, window=500, seed=11, n_int=10, budget_s=1500.0):
+def suite_serve(dps, n_req=16, rate=20.0, cap=20000, window=500, seed=11, classes=(2, 4, 8, 12),
+                budget_s=1500.0):
     """A bounded prefix of the serving trace: n_req Poisson-arriving settling
     requests at `rate` per second (edge log-uniform 32..160, eps U(0.01,
     0.45), d = 1, FP32) on the continuous-batching server, each run until its
     windowed mean particle velocity changes by < 0.1 % between consecutive
-    windows of `window` steps or the cap of 20k steps.  All requests run the
-    paper's n_int = 10 subcycles (n_DEM = 2: 20 substeps per step), which keeps
-    the densest boxes of the trace stable.  Requests not finished after
-    `budget_s` seconds are cancelled and counted.  Every 20th request is rerun
-    alone with the plain FP64 method for the same number of steps."""
+    windows of `window` steps or the cap of 20k steps.  Each request runs the
+    subcycle count that keeps its drag relaxation stable, rounded up to one of
+    `classes` (n_DEM = ceil(20 / n_int)); the server runs one batch per class.
+    The pressure-gradient force is off: as printed it is not returned to the
+    fluid, so in a periodic box it adds momentum every step and the mean
+    particle velocity has no stationary value to converge to.  Requests not
+    finished after `budget_s` seconds are cancelled and counted.  Every 20th
+    request is rerun alone with the plain FP64 method for the same number of
+    steps."""
     rng = np.random.default_rng(seed)
     reqs = []
     for k in range(n_req):
@@ -692,15 +697,19 @@ def suite_serve(dps, n_req=16, rate=20.0, cap=20000, window=500, seed=11, n_int=
         eps = rng.uniform(0.01, 0.45)
         reqs.append(workloads.settling_box(L=L, eps=eps, d=1.0, seed=seed * 1000 + k))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    n_ints = []
+    for wl in reqs:
+        n = _stable_subcycles(wl)
+        n_ints.append(next((c for c in classes if c >= n), n))
     S = dps.Server("f32", max_boxes=64, hbm_reserve_bytes=16 << 30, chunk_steps=100)
     t0 = time.perf_counter()
     ids = []
-    for wl, ta in zip(reqs, arrivals):
+    for wl, ta, ni in zip(reqs, arrivals, n_ints):
         now = time.perf_counter() - t0
         if ta > now:
             time.sleep(ta - now)
         ids.append(S.submit(wl["n"], wl["periodic"], wl["tau"], wl["x"], wl["d"], wl["rho_p"],
-                            _settling_closure(dps, wl, 1.0, n_int), max_steps=cap, window=window,
+                            _settling_closure(dps, wl, 1.0, ni, pressure=0), max_steps=cap, window=window,
                             rel_tol=1e-3))
     idle = True
     try:
@@ -726,7 +735,7 @@ def suite_serve(dps, n_req=16, rate=20.0, cap=20000, window=500, seed=11, n_int=
         wl = reqs[k]
         dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
         dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
-        dom.set_closure(_settling_closure(dps, wl, 1.0, n_int))
+        dom.set_closure(_settling_closure(dps, wl, 1.0, n_ints[k], pressure=0))
         steps = res[k]["steps"]
         w, acc = window, np.zeros(3)
         dom.step(steps - w)
@@ -740,11 +749,12 @@ def suite_serve(dps, n_req=16, rate=20.0, cap=20000, window=500, seed=11, n_int=
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "aggregate_MLUPS": st["cell_updates"] / st["busy_s"] / 1e6 if st["busy_s"] > 0 else None,
             "completed": st["completed"], "failed": st["failed"], "cancelled_at_budget": cancelled,
-            "budget_s": budget_s, "peak_boxes": st["peak_boxes"], "n_int": n_int,
+            "budget_s": budget_s, "peak_boxes": st["peak_boxes"], "pressure_force": 0,
             "capped": int(sum(r["capped"] for r in done)),
             "requests_detail": [{"L": int(w["n"][0]), "eps": round(float(len(w["x"]) * math.pi / 6 / np.prod(w["n"])), 3),
-                                 "state": r["state"], "steps": r["steps"], "latency_s": r["t_end"] - r["t_submit"]}
-                                for w, r in zip(reqs, res)],
+                                 "n_int": ni, "state": r["state"], "steps": r["steps"],
+                                 "latency_s": r["t_end"] - r["t_submit"]}
+                                for w, r, ni in zip(reqs, res, n_ints)],
             "f64_rerun_up_rel_err": [float(e) for e in errs]}
     print(json.dumps(line), flush=True)
     return line

@@ -328,11 +328,13 @@ int dps_batch_launches_per_step(dps_batch b, int64_t *n);
 int dps_box_bytes(int precision, const int n[3], int64_t max_particles, size_t *bytes);
 
 /* ---- serving: continuous batching of settling-suspension runs ----------- */
-/* A server owns a batch and a worker thread.  Requests (one periodic or walled
- * box with its particles and closure) queue on submit; the worker admits a
- * queued request when a batch slot is free and cudaMemGetInfo shows room for
- * the box (dps_box_bytes) plus the reserve, steps all running boxes together
- * in chunks, samples each box's mean particle velocity every chunk and
+/* A server owns a worker thread and one batch per subcycle class (n_int,
+ * n_dem).  Requests (one periodic or walled box with its particles and
+ * closure) queue on submit; the worker admits queued requests first come
+ * first served, each into the batch of its class, while a slot (max_boxes
+ * over all classes) is free and cudaMemGetInfo shows room for the box
+ * (dps_box_bytes) plus the reserve, steps all running boxes in chunks (the
+ * class batches concurrently, each on its own stream), samples each box's mean particle velocity every chunk and
  * retires a box once the mean over its last `window` steps changed by less
  * than rel_tol (relative, along g) from the window before, or after max_steps.
  * A box's result does not depend on which other requests shared the GPU. */

@@ -1,13 +1,17 @@
 // serve.cu -- continuous batching of settling-suspension runs on one GPU.
 //
-// A worker thread owns one batch (include/dps.h batch API).  Between chunks of
-// steps it admits queued requests into the batch while a slot is free and the
-// device has room (cudaMemGetInfo against dps_box_bytes plus a reserve), so a
-// request arriving while others run joins the next chunk; it samples each
-// box's mean particle velocity once per chunk and retires boxes whose
-// windowed mean velocity converged (or hit the step cap), freeing their memory
-// for the queue.  Each box sees exactly the same step sequence as it would
-// alone, so its result does not depend on the mix.
+// A worker thread owns one batch (include/dps.h batch API) per subcycle class
+// (n_int, n_DEM): a batch advances all its boxes with one launch per phase,
+// and the boxes of a batch must share the subcycle counts.  Between chunks of
+// steps the worker admits queued requests, first come first served, into the
+// batch of their class while a slot is free and the device has room
+// (cudaMemGetInfo against dps_box_bytes plus a reserve), so a request arriving
+// while others run joins the next chunk; the class batches step concurrently
+// (each on its own stream); the worker samples each box's mean particle
+// velocity once per chunk and retires boxes whose windowed mean velocity
+// converged (or hit the step cap), freeing their memory for the queue.  Each
+// box sees exactly the same step sequence as it would alone, so its result
+// does not depend on the mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -30,6 +34,7 @@ struct Req {
     dps_request r{};
     std::vector<double> x, d, rho;
     dps_result res{};
+    dps_batch b = nullptr;  // the batch of its subcycle class
     int box = -1;
     bool cancel = false;
     double win_sum[3] = {0, 0, 0};
@@ -45,7 +50,7 @@ using clk = std::chrono::steady_clock;
 
 struct dps_server_s {
     dps_serve_desc desc{};
-    dps_batch batch = nullptr;
+    std::map<std::pair<int, int>, dps_batch> batches;  // (n_int, n_DEM) -> batch
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv;
@@ -65,10 +70,10 @@ struct dps_server_s {
         // final observables of the box, then release it
         if (state == DPS_REQ_DONE) {
             dps_stats s;
-            if (dps_batch_stats(batch, q->box, &s) == DPS_OK)
+            if (dps_batch_stats(q->b, q->box, &s) == DPS_OK)
                 for (int a = 0; a < 3; ++a) q->res.u_pS[a] = s.u_pS[a];
         }
-        dps_batch_remove_box(batch, q->box);
+        dps_batch_remove_box(q->b, q->box);
         std::lock_guard<std::mutex> lk(mu);
         q->res.state = state;
         q->res.status = status;
@@ -88,11 +93,6 @@ struct dps_server_s {
                 st.queued--;
                 continue;
             }
-            // every box of the batch runs the same subcycle counts: a request
-            // with other counts waits until the running boxes retire
-            if (!running.empty() && (q->r.closure.n_int != running[0]->r.closure.n_int ||
-                                     q->r.closure.n_dem != running[0]->r.closure.n_dem))
-                break;
             size_t need = 0, fre = 0, tot = 0;
             dps_box_bytes(desc.precision, q->r.n, q->r.np, &need);
             cudaMemGetInfo(&fre, &tot);
@@ -111,18 +111,31 @@ struct dps_server_s {
             st.queued--;
             admitting++;
             lk.unlock();
-            int box = -1;
-            int rc = dps_batch_add_box(batch, q->r.n, q->r.periodic, q->r.tau, q->r.rho_f, q->r.np, &box);
+            int box = -1, rc = DPS_OK;
+            // the batch of the request's subcycle class (created on first use)
+            const std::pair<int, int> cls(q->r.closure.n_int, q->r.closure.n_dem);
+            auto it = batches.find(cls);
+            if (it == batches.end()) {
+                dps_batch_desc bd{};
+                bd.precision = desc.precision;
+                dps_batch nb = nullptr;
+                rc = dps_batch_create(&bd, &nb);
+                if (rc == DPS_OK) it = batches.emplace(cls, nb).first;
+            }
+            if (rc == DPS_OK) {
+                q->b = it->second;
+                rc = dps_batch_add_box(q->b, q->r.n, q->r.periodic, q->r.tau, q->r.rho_f, q->r.np, &box);
+            }
             if (rc == DPS_OK && q->r.np)
-                rc = dps_batch_add_particles(batch, box, q->r.np, q->x.data(), nullptr, nullptr, q->d.data(),
+                rc = dps_batch_add_particles(q->b, box, q->r.np, q->x.data(), nullptr, nullptr, q->d.data(),
                                              q->rho.data());
-            if (rc == DPS_OK) rc = dps_batch_set_closure(batch, box, &q->r.closure);
+            if (rc == DPS_OK) rc = dps_batch_set_closure(q->b, box, &q->r.closure);
             lk.lock();
             admitting--;
             if (rc != DPS_OK) {
                 if (box >= 0) {
                     lk.unlock();
-                    dps_batch_remove_box(batch, box);
+                    dps_batch_remove_box(q->b, box);
                     lk.lock();
                 }
                 q->res.state = DPS_REQ_FAILED;
@@ -168,38 +181,62 @@ struct dps_server_s {
                 running.erase(std::find(running.begin(), running.end(), q));
             }
             if (running.empty()) continue;
-            double cells = 0;
-            for (Req *q : running) cells += (double)q->r.n[0] * q->r.n[1] * q->r.n[2];
-            int rc = dps_batch_step(batch, chunk);
+            // every class batch with running boxes advances one chunk; the
+            // batches run on their own streams, so their work overlaps
+            std::vector<dps_batch> active;
+            for (Req *q : running)
+                if (std::find(active.begin(), active.end(), q->b) == active.end()) active.push_back(q->b);
+            std::vector<int> brc(active.size(), DPS_OK);
+            for (size_t k = 0; k < active.size(); ++k) brc[k] = dps_batch_step_async(active[k], chunk);
+            for (size_t k = 0; k < active.size(); ++k)
+                if (brc[k] == DPS_OK) brc[k] = dps_batch_check(active[k]);
             std::vector<std::pair<Req *, int>> done;  // request, state
-            if (rc != DPS_OK) {
+            std::vector<dps_batch> failed_all;        // batches whose every box failed
+            double cells = 0;
+            for (size_t k = 0; k < active.size(); ++k) {
+                if (brc[k] == DPS_OK) {
+                    for (Req *q : running)
+                        if (q->b == active[k]) cells += (double)q->r.n[0] * q->r.n[1] * q->r.n[2];
+                    continue;
+                }
                 // boxes are independent: retire those whose status word flags
-                // the failure; if none does (a CUDA error), all of them
+                // the failure; if none does (a CUDA error), all boxes of the batch
                 int flagged = 0;
                 for (Req *q : running) {
                     dps_stats bs;
-                    if (rc == DPS_ERR_UNSTABLE && dps_batch_stats(batch, q->box, &bs) == DPS_OK && bs.status) {
+                    if (q->b == active[k] && brc[k] == DPS_ERR_UNSTABLE &&
+                        dps_batch_stats(q->b, q->box, &bs) == DPS_OK && bs.status) {
                         done.push_back({q, DPS_REQ_FAILED});
                         flagged++;
                     }
                 }
-                if (!flagged)
-                    for (Req *q : running) done.push_back({q, DPS_REQ_FAILED});
-                else
-                    rc = DPS_OK;  // the others completed the chunk
-            } else {
+                if (!flagged) {
+                    failed_all.push_back(active[k]);
+                    for (Req *q : running)
+                        if (q->b == active[k]) done.push_back({q, DPS_REQ_FAILED});
+                }
+            }
+            {
                 std::lock_guard<std::mutex> g(mu);
                 st.cell_updates += cells * chunk;
             }
-            if (rc == DPS_OK) {
+            // the error code of a box's batch (a flagged box of a batch that
+            // returned DPS_OK cannot occur)
+            auto batch_rc = [&](const Req *q) {
+                for (size_t k = 0; k < active.size(); ++k)
+                    if (active[k] == q->b) return brc[k];
+                return (int)DPS_OK;
+            };
+            {
                 for (Req *q : running) {
+                    if (std::find(failed_all.begin(), failed_all.end(), q->b) != failed_all.end()) continue;
                     if (std::find_if(done.begin(), done.end(), [&](const std::pair<Req *, int> &p) {
                             return p.first == q;
                         }) != done.end())
                         continue;
                     q->res.steps += chunk;
                     double u[3];
-                    dps_batch_particle_mean(batch, q->box, u);
+                    dps_batch_particle_mean(q->b, q->box, u);
                     for (int a = 0; a < 3; ++a) q->win_sum[a] += u[a];
                     q->win_n++;
                     if (q->res.steps % q->r.window == 0) {
@@ -229,9 +266,22 @@ struct dps_server_s {
                 }
             }
             for (auto &p : done) {
-                finish(p.first, p.second, p.second == DPS_REQ_FAILED ? (rc ? rc : DPS_ERR_UNSTABLE) : DPS_OK);
+                const int brq = batch_rc(p.first);
+                finish(p.first, p.second, p.second == DPS_REQ_FAILED ? (brq ? brq : DPS_ERR_UNSTABLE) : DPS_OK);
                 std::lock_guard<std::mutex> g(mu);
                 running.erase(std::find(running.begin(), running.end(), p.first));
+            }
+            // a class batch left without boxes is released (its streams,
+            // graphs and tile lists); the class's next request creates it anew
+            for (auto it = batches.begin(); it != batches.end();) {
+                bool used = false;
+                for (Req *q : running) used = used || q->b == it->second;
+                if (!used) {
+                    dps_batch_destroy(it->second);
+                    it = batches.erase(it);
+                } else {
+                    ++it;
+                }
             }
             cv.notify_all();
         }
@@ -251,13 +301,6 @@ int dps_serve_create(const dps_serve_desc *desc, dps_server *out) {
         cudaGetLastError();
         delete s;
         return DPS_ERR_CUDA;
-    }
-    dps_batch_desc bd{};
-    bd.precision = desc->precision;
-    int rc = dps_batch_create(&bd, &s->batch);
-    if (rc) {
-        delete s;
-        return rc;
     }
     s->t0 = clk::now();
     s->worker = std::thread([s] { s->loop(); });
@@ -346,7 +389,7 @@ int dps_serve_destroy(dps_server s) {
     }
     s->cv.notify_all();
     if (s->worker.joinable()) s->worker.join();
-    dps_batch_destroy(s->batch);
+    for (auto &p : s->batches) dps_batch_destroy(p.second);
     for (auto &p : s->all) delete p.second;
     delete s;
     return DPS_OK;

@@ -251,8 +251,9 @@ def test_serving_failing_request_leaves_the_others_running():
 
 
 def test_serving_groups_requests_by_subcycle_counts():
-    """Requests with other (n_int, n_DEM) wait until the running boxes retire
-    instead of sharing a batch; all of them complete."""
+    """Requests with other (n_int, n_DEM) run in the batch of their own class
+    beside the others (no box shares a batch with other subcycle counts); all
+    of them complete with the steps they asked for."""
     dps = _dps()
     kw = dict(max_steps=200, window=100, rel_tol=1e-9)
     wl, _ = _request(dps, 10, 0.1, 6)
