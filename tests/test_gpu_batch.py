@@ -266,6 +266,10 @@ def test_serving_groups_requests_by_subcycle_counts():
     S.close()
     assert all(r["state"] == "done" and r["steps"] == 200 for r in res), res
     assert st["failed"] == 0
+    assert st["peak_boxes"] == 3  # the classes ran side by side
+    # the same request in the same class gives the same result
+    assert np.array_equal(res[0]["up_mean"], res[2]["up_mean"])
+    assert not np.array_equal(res[0]["up_mean"], res[1]["up_mean"])
 
 
 def test_read_back_of_a_box_added_after_stepping():
