@@ -236,13 +236,12 @@ __device__ __forceinline__ void collide_stream_vec2(ST *__restrict__ pdf, const 
                                            wall_free_delta(D1, -CX(q), -CY(q), -CZ(q))));
         }
     }
-    const CT e0 = (CT)eps[c], e1 = (CT)eps[c + 1];
-    CT a[3], b[3];
+    // eps_f and f_pf of the pair as two-element vectors too (FT is float
+    // in the forms that take this path; c and N are even)
+    CT e0, e1, a[3], b[3];
+    Vec2<FT>::load(eps + cu, e0, e1);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        a[k] = (CT)fpf[k * N + c];
-        b[k] = (CT)fpf[k * N + c + 1];
-    }
+    for (int k = 0; k < 3; ++k) Vec2<FT>::load(fpf + ((unsigned)k * Nu + cu), a[k], b[k]);
     relax_cell<ST, CT, VISC, false>(f, e0, a[0], a[1], a[2], fbx, fby, fbz, omega_box, kf_box, tau, vmode, true,
                                     status, nullptr);
     relax_cell<ST, CT, VISC, false>(f1, e1, b[0], b[1], b[2], fbx, fby, fbz, omega_box, kf_box, tau, vmode, true,
