@@ -18,10 +18,11 @@
 // A particle that moves more than skin/2 before the next sort raises
 // DPS_ERR_UNSTABLE.  Candidate distances are screened in FP32 (a float
 // copy of the positions, refreshed every substep, with a margin far above its
-// rounding) and every pair that passes is evaluated exactly: in FP64 for the
-// FP64 form, and for the low-precision forms in FP32 except close to contact
-// (gap below 1e-3 dx or overlap), which stays FP64.  Positions, velocities and
-// the integration are FP64 in every form.  State is read from one buffer and
+// rounding) and every pair that passes is evaluated: in FP64 for the FP64
+// form, and in FP32 for the low-precision forms, where a pair close to
+// contact (gap below 1e-3 dx or overlap) takes its separation from the FP64
+// positions.  Positions, velocities and the integration are FP64 in every
+// form.  State is read from one buffer and
 // written to the other (ping-pong), so every pair sees the substep start.
 #include "box.cuh"
 
@@ -29,7 +30,7 @@ namespace dps {
 
 static constexpr double PI_D = 3.14159265358979323846;
 static constexpr float SCREEN_MARGIN = 1e-3f;  // >> FP32 rounding of positions < 2^16 cells
-static constexpr double H_NEAR = 1e-3;         // gaps below this use FP64 in the mixed forms
+static constexpr double H_NEAR = 1e-3;         // gaps below this: separation from the FP64 positions (mixed forms)
 
 // minimum image for |dx| < L (positions live in [0, L))
 __device__ __forceinline__ double min_image(double dx, int L, int per) {
@@ -143,13 +144,14 @@ __device__ __forceinline__ void lub_force(const PairPar<T> &ph, const T n[3], T 
 // given m_ij and <d>: contact while overlapping, lubrication on pairs that do
 // not overlap, 0 <= h < h_c (in contact the spring-dashpot acts alone, which
 // keeps the wet rebound of Sec. 5)
+// gap = |x_j - x_i| - (d_i + d_j)/2 (negative: the overlap).
 template <typename T>
-__device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T dist, T sumr, const T ui[3],
-                                        const T wi[3], T di, const T uj[3], const T wjh[3], T m_ij, T dmean, T F[3],
-                                        T Tq[3], unsigned &nlim) {
-    const T delta = sumr - dist;
+__device__ __forceinline__ void partner(const PairPar<T> &ph, const T n[3], T gap, const T ui[3], const T wi[3],
+                                        T di, const T uj[3], const T wjh[3], T m_ij, T dmean, T F[3], T Tq[3],
+                                        unsigned &nlim) {
+    const T delta = -gap;
     if (ph.contact && delta > T(0)) contact_force(ph, n, delta, ui, wi, di, uj, wjh, m_ij, T(0.5) * di, F, Tq);
-    const T h = dist - sumr;
+    const T h = gap;
     if (ph.lubrication && h >= T(0) && h < ph.h_c) {
         const T hh = m_max(h, ph.h_min);
         const T q = T(1) / (dmean * hh);  // r and 1/r from one division
@@ -376,24 +378,44 @@ __device__ __forceinline__ void pair64_body(const PairPar<double> &pd, const dou
         lub_force(pd, n, dmean, r, ir, cap, ui, uj, F, nlim);
     }
 }
-// the mixed forms' near-contact pair: loads the FP64 state of particle i itself
-__device__ __noinline__ void pair64_out(const BoxDev &Bx, const double *__restrict__ xin, long long i, long long j,
-                                        double F[3], double T[3], unsigned &nlim) {
+// the mixed forms' pair within H_NEAR of contact.  The float copies of the
+// positions carry absolute errors of up to ~3e-5 at x ~ 256, too coarse for
+// such gaps, so the separation comes from the FP64 positions: |dx|^2 - s^2
+// in FP64, divided by |dx| + s in FP32, a gap (or overlap) with FP32's
+// relative precision however small it is; the forces then run in FP32 like
+// every other pair.  Out of line, and returning its terms, so that the rare
+// call costs the FP32 pair loop no registers.
+struct NearTerms {
+    float F[3], T[3];
+    unsigned nlim;
+};
+__device__ __noinline__ NearTerms near_pair32(const BoxDev &Bx, const double *__restrict__ xin,
+                                              const float4 *__restrict__ vin, const float4 *__restrict__ oin,
+                                              const PairPar<float> &pfl, long long i, int j, float4 pi, float4 pj,
+                                              float4 vi, float4 oi, float rng_extra_f) {
+    NearTerms o = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, 0u};
     const double *pf = Bx.pf[Bx.cur];
     const long long cap = Bx.cap;
-    double xi[3], ui[3], wi[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        xi[a] = xin[a * cap + i];
-        ui[a] = xin[(3 + a) * cap + i];
-        wi[a] = xin[(6 + a) * cap + i];
-    }
-    const double di = pf[PD * cap + i];
-    const double mi = pf[PM * cap + i];
-    const double rng_extra = Bx.ph.lubrication ? fmax(Bx.ph.h_c, 0.0) : 0.0;
-    const PairPar<double> pd = pair_par<double>(Bx.ph);
     const Geom g = Bx.g;
-    pair64_body(pd, xin, pf, cap, g, j, xi, ui, wi, di, mi, rng_extra, 0.5 * di, F, T, nlim);
+    double dx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dx[a] = min_image(xin[a * cap + j] - xin[a * cap + i], g.n[a], g.per[a]);
+    const double d2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+    const double s = 0.5 * (pf[PD * cap + i] + pf[PD * cap + j]);
+    const float distf = sqrtf((float)d2);
+    if (!(distf > 0.f)) return o;
+    const float gap = (float)fma(-s, s, d2) / (distf + (float)s);
+    if (!(gap < rng_extra_f)) return o;
+    const float4 vj = vin[j], oj = oin[j];
+    const float inv = 1.0f / distf;
+    const float n[3] = {(float)dx[0] * inv, (float)dx[1] * inv, (float)dx[2] * inv};
+    const float uif[3] = {vi.x, vi.y, vi.z}, wif[3] = {oi.x, oi.y, oi.z};
+    const float uj[3] = {vj.x, vj.y, vj.z};
+    const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
+    const float m_ij = vi.w * vj.w / (vi.w + vj.w);
+    const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
+    partner<float>(pfl, n, gap, uif, wif, pi.w, uj, wjh, m_ij, dmean, o.F, o.T, o.nlim);
+    return o;
 }
 
 // one thread per particle: wall partners (WALLS; the FP64 form evaluates
@@ -433,7 +455,7 @@ __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<
             if (!(dist < range)) continue;
             double n[3] = {0, 0, 0};
             n[a] = side == 0 ? -1.0 : 1.0;
-            partner<double>(pd, n, dist, 0.5 * di, ui, wi, di, zero, zero, mi, 2.0 * di, F, T, nlim);
+            partner<double>(pd, n, dist - 0.5 * di, ui, wi, di, zero, zero, mi, 2.0 * di, F, T, nlim);
         }
     }
     // Eq. particle_motion, semi-implicit Euler with I = m d^2 / 10
@@ -480,8 +502,9 @@ __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<
 // src_tmp = 0: read x/u/w (and the float positions) from the current set,
 // write the ping-pong buffers; src_tmp = 1: the other way round.
 // k_dem_pairsum_mixed: lane groups of LANES lanes per particle walk its list;
-// pairs away from contact run in FP32 from the float copies, the rare pairs
-// near contact in FP64 (out of line); the group's sums (a fixed xor tree) go
+// pairs away from contact run in FP32 from the float copies, pairs near
+// contact in FP32 from an FP64 separation (out of line); the group's sums (a
+// fixed xor tree) go
 // to psum[6][cap] (force, torque) and the lubrication-cap count to the
 // counters.  k_dem_integrate then adds the walls and integrates, one thread
 // per particle.  Two kernels so that each has its own register budget: the
@@ -510,10 +533,8 @@ __global__ void __launch_bounds__(256, DPS_MIXED_MINB) k_dem_pairsum_mixed(const
         for (long long base = tl.begin; base < tl.end; base += ngrp) {
             const long long i = base + grp;
             const bool act = i < tl.end;
-            double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
             float Ff[3] = {0, 0, 0}, Tf[3] = {0, 0, 0};
             unsigned nlim = 0;
-            bool near = false;  // this lane evaluated an FP64 pair
             if (act) {
                 const float4 pi = fin[i], vi = vin[i], oi = oin[i];
                 const int nn = Bx.nlist_n[i];
@@ -528,9 +549,9 @@ __global__ void __launch_bounds__(256, DPS_MIXED_MINB) k_dem_pairsum_mixed(const
                     const float fr = sumr_f + rng_extra_f + SCREEN_MARGIN;
                     const float d2f = fx * fx + fy * fy + fz * fz;
                     if (!(d2f < fr * fr)) continue;
-                    // away from contact: the whole pair in FP32 from the float copies
                     const float distf = sqrtf(d2f);
                     if (distf - sumr_f > (float)H_NEAR + SCREEN_MARGIN) {
+                        // away from contact: the separation from the float copies
                         if (!(distf < sumr_f + rng_extra_f)) continue;
                         const float4 vj = vin[j], oj = oin[j];
                         const float inv = 1.0f / distf;
@@ -540,25 +561,24 @@ __global__ void __launch_bounds__(256, DPS_MIXED_MINB) k_dem_pairsum_mixed(const
                         const float wjh[3] = {0.5f * pj.w * oj.x, 0.5f * pj.w * oj.y, 0.5f * pj.w * oj.z};
                         const float m_ij = vi.w * vj.w / (vi.w + vj.w);
                         const float dmean = 2.0f * pi.w * pj.w / (pi.w + pj.w);
-                        partner<float>(pfl, n, distf, sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf, nlim);
+                        partner<float>(pfl, n, distf - sumr_f, uif, wif, pi.w, uj, wjh, m_ij, dmean, Ff, Tf, nlim);
                         continue;
                     }
-                    // near contact: exact separation and forces in FP64
-                    near = true;
-                    pair64_out(Bx, xin, i, j, F, T, nlim);
+                    // near contact: the separation from the FP64 positions
+                    const NearTerms o = near_pair32(Bx, xin, vin, oin, pfl, i, j, pi, pj, vi, oi, rng_extra_f);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Ff[a] += o.F[a];
+                        Tf[a] += o.T[a];
+                    }
+                    nlim += o.nlim;
                 }
             }
             if (LANES > 1) {
-                // FP64 sums only when some lane of the warp met a pair near contact
-                const bool red64 = __any_sync(0xffffffffu, near);
 #pragma unroll
                 for (int o = LANES / 2; o > 0; o >>= 1) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        if (red64) {
-                            F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
-                            T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
-                        }
                         Ff[a] += __shfl_xor_sync(0xffffffffu, Ff[a], o);
                         Tf[a] += __shfl_xor_sync(0xffffffffu, Tf[a], o);
                     }
@@ -568,8 +588,8 @@ __global__ void __launch_bounds__(256, DPS_MIXED_MINB) k_dem_pairsum_mixed(const
             if (act && lane == 0) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    Bx.psum[a * cap + i] = F[a] + (double)Ff[a];
-                    Bx.psum[(3 + a) * cap + i] = T[a] + (double)Tf[a];
+                    Bx.psum[a * cap + i] = (double)Ff[a];
+                    Bx.psum[(3 + a) * cap + i] = (double)Tf[a];
                 }
                 if (nlim) atomicAdd(&Bx.counters[CNT_LUB_LIMITED], (unsigned long long)nlim);
             }

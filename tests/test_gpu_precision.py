@@ -132,3 +132,48 @@ def test_collide_stream_forms_every_population_lands(prec, n, per, steps):
     tol = {"f32": 2e-7, "f16s": 2e-4}[prec]
     assert np.abs(got - ref[perm]).max() < tol
     dom.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16s"])
+def test_mixed_dem_pairs_near_contact_at_large_coordinates(prec):
+    """The low-precision forms take the separation of a pair near contact
+    (gap below 1e-3 dx, or overlapping) from the FP64 positions: sphere pairs
+    around x = 200, where the float copies of the positions are ~1.5e-5
+    coarse, with gaps from an overlap of 2e-3 to 1.5e-3, approaching one
+    another, follow the FP64 oracle through contact and lubrication
+    (hydrodynamic forces off) to 1e-5 of the largest velocity; the separation
+    from the float copies alone would be off by several per cent for these
+    gaps (4e-4 of the largest velocity).  Two pairs away from contact (gaps
+    0.05 and 0.3, separation from the float copies) sit near x = 20, where
+    the copies are fine enough for that bound."""
+    dps = _dps()
+    n, per = (224, 12, 12), (1, 1, 1)
+    gaps = [-2e-3, -5e-4, 0.0, 2e-4, 8e-4, 1.5e-3, 0.05, 0.3]
+    th = 0.3
+    x, u = [], []
+    for k, gp in enumerate(gaps):
+        y, z = 1.5 + 3.0 * (k % 4), 3.0 + 6.0 * (k // 4)
+        x0 = (200.37 if abs(gp) < 2e-3 else 20.37) + 0.113 * k
+        x.append([x0, y, z])
+        x.append([x0 + (1.0 + gp) * np.cos(th), y + (1.0 + gp) * np.sin(th), z])
+        u.append([1e-3, 0.0, 2e-4])
+        u.append([-1e-3, 1e-4, 0.0])
+    x, u = np.array(x), np.array(u)
+    w = np.random.default_rng(5).normal(0.0, 1e-3, x.shape)
+    npart = len(x)
+    kw = dict(e_n=0.9, mu_c=0.25, T_c=1.0, h_c=1.0, h_min=1e-5, C_am=0.5, n_int=1, n_dem=10, drag=0, pressure=0,
+              added_mass=0, lub_limiter=1, lub_cap=0.25, eps_min=0.05)
+    dom = dps.Domain(n, per, 0.6, prec, max_particles=npart)
+    dom.add_particles(x, np.ones(npart), np.full(npart, 2.5), u=u, w=w)
+    dom.set_closure(g=(0.0, 0.0, 0.0), fb_mode=0, skin=0.5, **kw)
+    dom.step(2)
+    got = dom.read_particles()
+    dom.close()
+    P = O.make_params(n, per, 0.6, **kw)
+    ref = O.Domain(P, x=x, u=u, w=w, d=np.ones(npart), rho_p=np.full(npart, 2.5))
+    ref.step(2)
+    r = ref.particles()
+    assert np.abs(got["u"] - r["u"]).max() < 1e-5 * np.abs(r["u"]).max()
+    assert np.abs(got["w"] - r["w"]).max() < 1e-5 * np.abs(r["w"]).max()
+    # the pairs in contact or within lubrication range changed velocity
+    assert np.abs(r["u"] - u)[:12].max() > 1e-4
