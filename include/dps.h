@@ -419,6 +419,17 @@ int dps_op_cell_sort(const int n[3], const int periodic[3], int B, int64_t np,
  * Errors: DPS_ERR_ARG (NULL), DPS_ERR_OOM, DPS_ERR_CUDA. */
 int dps_probe_fp64_peak(double *gflops);
 
+/* The natural logarithm of the FP64 lubrication term (Sec. 3.1.3, ln(<d>/2h))
+ * evaluated for checking: a table-driven method (Tang, ACM TOMS 16(4),
+ * 1990) whose error stays below one unit in the last place plus 2^-60.
+ * y[i] = that logarithm of x[i], y_lib[i] = the C / CUDA library log of x[i],
+ * for i < n (caller-owned host arrays).  device = 0: both computed on the
+ * host (the same source as the device path, with every operation rounded to
+ * nearest, so the two agree bit for bit); device != 0: on the current GPU
+ * (allocates 24 n bytes of device memory for the call, synchronous).
+ * Errors: DPS_ERR_ARG (n < 0 or a NULL array), DPS_ERR_OOM, DPS_ERR_CUDA. */
+int dps_check_tlog(const double *x, double *y, double *y_lib, int64_t n, int device);
+
 /* ---- allocation-free variant of the cell sort ---------------------------- */
 /* The paper has no counterpart: this entry point is a property of the
  * library, not of the method.  dps_op_cell_sort takes its scratch memory

@@ -346,7 +346,6 @@ __device__ __forceinline__ void pair64_body(const PairPar<double> &pd, const dou
         for (int a = 0; a < 3; ++a) {
             n[a] = dx[a] * inv;
             uj[a] = xin[(3 + a) * cap + j];
-            wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
         }
     } else {
         const int face = -1 - (int)j, ax = face >> 1, side = face & 1;
@@ -366,7 +365,14 @@ __device__ __forceinline__ void pair64_body(const PairPar<double> &pd, const dou
     const double A = wall ? mi : mi * mj, Bm = wall ? 1.0 : mi + mj;
     const double C = wall ? 2.0 * di : 2.0 * di * dj, D = wall ? 1.0 : di + dj;
     const double delta = sumr - dist;
-    if (pd.contact && delta > 0.0) contact_force(pd, n, delta, ui, wi, di, uj, wjh, A / Bm, lev, F, T);
+    if (pd.contact && delta > 0.0) {
+        // the partner's spin only matters in contact (the friction)
+        if (!wall) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) wjh[a] = 0.5 * dj * xin[(6 + a) * cap + j];
+        }
+        contact_force(pd, n, delta, ui, wi, di, uj, wjh, A / Bm, lev, F, T);
+    }
     const double h = dist - sumr;
     if (pd.lubrication && h >= 0.0 && h < pd.h_c) {
         const double hh = fmax(h, pd.h_min);

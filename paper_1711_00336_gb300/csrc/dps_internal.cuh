@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include "dps.h"
+#include "tlog.cuh"
 
 namespace dps {
 
@@ -168,7 +169,7 @@ struct Phys {
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
-__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ double m_log(double x) { return tlog(x); }  // tlog.cuh
 __device__ __forceinline__ float m_min(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double m_min(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ float m_max(float a, float b) { return fmaxf(a, b); }

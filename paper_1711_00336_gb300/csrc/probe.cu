@@ -1,10 +1,13 @@
 // probe.cu -- measured FP64 throughput of the GPU, the denominator of the
 // roofline of the FP64-bound kernels (the DEM pair chain, the FP64
 // collide-stream).  Not part of the method: a dense chain of independent
-// fused multiply-adds on every SM, timed with CUDA events.
+// fused multiply-adds on every SM, timed with CUDA events.  Also the check
+// entry of the lubrication term's logarithm (tlog.cuh) on the host or the
+// device, beside the library logarithm.
 #include <cuda_runtime.h>
 
 #include "dps.h"
+#include "tlog.cuh"
 
 namespace {
 
@@ -26,7 +29,45 @@ __global__ void __launch_bounds__(256) k_fma64(double seed, double *out) {
     if (s == 12345.678) out[0] = s;  // keeps the chains live; never true
 }
 
+__global__ void k_tlog_check(const double *x, double *y, double *y_lib, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        y[i] = dps::tlog(x[i]);
+        y_lib[i] = log(x[i]);
+    }
+}
+
 }  // namespace
+
+extern "C" int dps_check_tlog(const double *x, double *y, double *y_lib, int64_t n, int device) {
+    if (n < 0 || (n && (!x || !y || !y_lib))) return DPS_ERR_ARG;
+    if (!device) {
+        for (int64_t i = 0; i < n; ++i) {
+            y[i] = dps::tlog(x[i]);
+            y_lib[i] = std::log(x[i]);
+        }
+        return DPS_OK;
+    }
+    if (n == 0) return DPS_OK;
+    double *d = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)n;
+    if (cudaMalloc(&d, 3 * bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return DPS_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_tlog_check<<<256, 256>>>(d, d + n, d + 2 * n, (long long)n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(y, d + n, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(y_lib, d + 2 * n, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DPS_ERR_CUDA;
+    }
+    return DPS_OK;
+}
 
 extern "C" int dps_probe_fp64_peak(double *gflops) {
     if (!gflops) return DPS_ERR_ARG;

@@ -362,6 +362,20 @@ def probe_fp64_peak():
     return v.value
 
 
+def check_tlog(x, device=False):
+    """The lubrication term's logarithm and the library log of x (float64
+    array), evaluated on the host or on the current GPU: (y, y_lib)."""
+    L = lib()
+    L.dps_check_tlog.argtypes = [_DP, _DP, _DP, ctypes.c_int64, ctypes.c_int]
+    x = np.ascontiguousarray(np.asarray(x, np.float64).ravel())
+    y, yl = np.empty_like(x), np.empty_like(x)
+    rc = L.dps_check_tlog(x.ctypes.data_as(_DP), y.ctypes.data_as(_DP), yl.ctypes.data_as(_DP), len(x),
+                          int(bool(device)))
+    if rc != DPS_OK:
+        raise DPSError(rc, "dps_check_tlog failed")
+    return y, yl
+
+
 def op_cell_sort(n, periodic, x_dev, ids_dev, stream=None):
     """Linked-cell sort of device positions (torch float64 [np,3]) and ids
     (torch int32 [np]); returns device (cell_start[ncell+1], order[np])."""
