@@ -474,11 +474,15 @@ __device__ __forceinline__ void finish_particle(const BoxDev &Bx, const PairPar<
         const double wn = wi[a] + dt_I * T[a];
         double xn = xi[a] + ph.dt_dem * un;
         if (g.per[a]) {
-            const int L = g.n[a];
-            if (xn >= L) xn -= L;
-            else if (xn < 0.0) xn += L;
-            if (xn >= L || xn < 0.0) xn -= L * floor(xn / L);
-            if (xn >= L) xn -= L;
+            const double L = g.n[a];
+            // a particle that left the box folds back in (two comparisons
+            // for the rest, which stay put)
+            if (!(xn >= 0.0 && xn < L)) {
+                if (xn >= L) xn -= L;
+                else if (xn < 0.0) xn += L;
+                if (xn >= L || xn < 0.0) xn -= L * floor(xn / L);
+                if (xn >= L) xn -= L;
+            }
         }
         xn3[a] = xn;
         un3[a] = un;
