@@ -379,7 +379,7 @@ def main():
     ap.add_argument("--forms", default="f32,f16s", help="extra precision forms to time (comma list, '' for none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 64^3 wall-suspension line")
-    ap.add_argument("--suite", default="", help="precision,accuracy,batch,serve,rebound,hindered: measure the "
+    ap.add_argument("--suite", default="", help="precision,accuracy,batch,serve,latency,rebound,hindered: measure the "
                     "forms, the sphere-wall rebound or hindered settling instead")
     args = ap.parse_args()
     if args.suite:
@@ -756,8 +756,44 @@ def suite_serve(dps, n_req=16, rate=20.0, cap=20000, window=500, seed=11, classe
                                  "latency_s": r["t_end"] - r["t_submit"]}
                                 for w, r, ni in zip(reqs, res, n_ints)],
             "f64_rerun_up_rel_err": [float(e) for e in errs]}
+    # the arrival rate one GPU sustains: its cell updates per second over the
+    # mean cell updates a request needs to converge
+    cs = [float(np.prod(w["n"])) * r["steps"] for w, r in zip(reqs, res) if r["state"] == "done"]
+    if cs and st["busy_s"] > 0:
+        line["sustainable_rate_per_s"] = st["cell_updates"] / st["busy_s"] / float(np.mean(cs))
     print(json.dumps(line), flush=True)
     return line
+
+
+def suite_latency(dps, runs=20):
+    """p50 / p99 wall-clock latency of whole runs through the public API
+    (create the domain, upload the spheres, set the closure, step, read the
+    particles back, destroy), FP64, `runs` runs each after one untimed run:
+    the single settling sphere (32 x 32 x 64 with walls in z, 2000 steps) and
+    the 64^3 wall suspension (5000 spheres, 5000 steps)."""
+    import torch
+    out = []
+    for wl, steps in ((workloads.single_sphere(), 2000), (workloads.wall_suspension(), 5000)):
+        lat = []
+        for r in range(runs + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dom = dps.Domain(wl["n"], wl["periodic"], wl["tau"], "f64", max_particles=len(wl["x"]))
+            dom.add_particles(wl["x"], wl["d"], wl["rho_p"])
+            dom.set_closure(**closure_kw(wl))
+            dom.step(steps)
+            dom.read_particles()
+            dom.close()
+            torch.cuda.synchronize()
+            if r:
+                lat.append(time.perf_counter() - t0)
+        p50 = float(np.percentile(lat, 50))
+        line = {"suite": "latency", "workload": wl["name"], "steps": steps, "runs": runs, "precision": "f64",
+                "p50_s": p50, "p99_s": float(np.percentile(lat, 99)), "min_s": float(min(lat)),
+                "max_s": float(max(lat)), "MLUPS_at_p50": float(np.prod(wl["n"])) * steps / p50 / 1e6}
+        print(json.dumps(line), flush=True)
+        out.append(line)
+    return out
 
 
 def suite_rebound(dps, tau=0.501, rho_p=25.0, d=0.5):
@@ -923,6 +959,8 @@ def run_suite(args):
         suite_batch(dps)
     if "serve" in which:
         suite_serve(dps)
+    if "latency" in which:
+        suite_latency(dps)
     if "rebound" in which:
         suite_rebound(dps)
     if "hindered" in which:
