@@ -37,8 +37,9 @@ struct BoxDev {
     // partners j > i: hn[i] of them, in ascending j, at slots hoff[i] ...
     // (hj: the partner of a slot; slots are allocated per block from *ptop).
     // rn[i] / rrow[i*maxn + r]: the slots of the pairs (k, i), k < i, in
-    // ascending k.  pres[6 s ...]: force on the owner and n x F_t of slot s;
-    // pflag[s]: the pair passed the screen of this substep.
+    // ascending k.  pres[3 s ...]: force on the owner of slot s,
+    // pres[3 (pcap + s) ...]: its n x F_t; pflag[s]: 1 the pair passed the
+    // screen of this substep, 2 also n x F_t is nonzero (written).
     int *hj, *hoff, *hn, *rrow, *rn;
     double *pres;
     unsigned char *pflag;

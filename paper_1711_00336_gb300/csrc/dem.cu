@@ -853,11 +853,15 @@ __global__ void __launch_bounds__(256, DPS_PAIRS_MINB) k_dem_pairs64(const BoxDe
                     double Fq[3] = {0, 0, 0}, Cq[3] = {0, 0, 0};
                     pair64_body(pd, xin, pf, cap, g, qJ[q], xi, ui, wi, pf[PD * cap + ii], pf[PM * cap + ii],
                                 rng_extra, 1.0, Fq, Cq, nlim);
-                    double *r = Bx.pres + 6 * (long long)qS[q];
+                    // the force in the first plane; n x F_t, nonzero only for
+                    // pairs in contact with friction, in the second, flagged 2
+                    const long long sq = qS[q];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        r[a] = Fq[a];
-                        r[3 + a] = Cq[a];
+                    for (int a = 0; a < 3; ++a) Bx.pres[3 * sq + a] = Fq[a];
+                    if (Cq[0] != 0.0 || Cq[1] != 0.0 || Cq[2] != 0.0) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) Bx.pres[3 * (Bx.pcap + sq) + a] = Cq[a];
+                        Bx.pflag[sq] = 2;
                     }
                 }
                 __syncthreads();  // the next window overwrites the queue
@@ -876,6 +880,9 @@ __global__ void __launch_bounds__(256, DPS_PAIRS_MINB) k_dem_pairs64(const BoxDe
 // WALLS: some box of the batch has a wall axis (else the wall code is left
 // out: 128 registers instead of 168, more warps for a kernel that waits on
 // the scattered loads of the pair results)
+#ifndef DPS_GATHER_GC
+#define DPS_GATHER_GC 4  // entries whose loads are issued before any is added
+#endif
 #ifndef DPS_GATHER_MINB
 #define DPS_GATHER_MINB 4  // 128-thread blocks per SM the register budget is sized for
 #endif
@@ -899,7 +906,7 @@ __global__ void __launch_bounds__(128, WALLS ? 1 : DPS_GATHER_MINB) k_dem_gather
             // of a chunk are loaded before any is added (the loads, not the
             // additions, bound this kernel), a screened-out pair adding zero;
             // the additions keep the list order
-            constexpr int GC = 4;
+            constexpr int GC = DPS_GATHER_GC;
             for (int c0 = 0; c0 < nh + nr; c0 += GC) {
                 long long sl[GC];
                 bool on[GC];
@@ -912,13 +919,22 @@ __global__ void __launch_bounds__(128, WALLS ? 1 : DPS_GATHER_MINB) k_dem_gather
                     on[u] = s >= 0;
                     sg[u] = c < nh ? 1.0 : -1.0;  // the owner's force, or its opposite on the partner
                 }
+                int fl[GC];
 #pragma unroll
-                for (int u = 0; u < GC; ++u) on[u] = on[u] && Bx.pflag[sl[u]];
+                for (int u = 0; u < GC; ++u) {
+                    fl[u] = on[u] ? Bx.pflag[sl[u]] : 0;
+                    on[u] = fl[u] != 0;
+                }
+                // the force of every pair that passed; n x F_t only where the
+                // pair kernel flagged it (2): zero for all others
                 double v[GC][6];
 #pragma unroll
                 for (int u = 0; u < GC; ++u)
 #pragma unroll
-                    for (int a = 0; a < 6; ++a) v[u][a] = on[u] ? Bx.pres[6 * sl[u] + a] : 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        v[u][a] = on[u] ? Bx.pres[3 * sl[u] + a] : 0.0;
+                        v[u][3 + a] = fl[u] == 2 ? Bx.pres[3 * (Bx.pcap + sl[u]) + a] : 0.0;
+                    }
 #pragma unroll
                 for (int u = 0; u < GC; ++u) {
                     if (!on[u]) continue;
