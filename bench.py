@@ -87,7 +87,7 @@ DEM_FLOPS_PAIR = 75       # per interacting pair (once: F_ji = -F_ij): separatio
 # DRAM bytes (read + write) per particle-substep of the FP64 DEM pair and
 # gather kernels, from the ncu capture of profiles/dem_pairs_fp64_settling_64.md
 # (a 64^3 box of the headline eps and d; traffic grows with the particle count)
-DEM_TRAFFIC_PER_PARTICLE = 962.0  # (4.54 + 24.00) MB / 29,669 spheres, cold-cache capture
+DEM_TRAFFIC_PER_PARTICLE = 748.0  # (4.54 + 17.64) MB / 29,669 spheres, cold-cache capture
 
 
 def interacting_pairs(x, d, n, periodic, h_c, sample=20000, seed=0):
