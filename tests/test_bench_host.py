@@ -41,3 +41,27 @@ def test_interacting_pairs_by_hand():
     # walls on x: D and E are 7.5 apart; A (x - d/2 = 0.5) and E (-0.1)
     # reach the x = 0 face, D the x = 8 face (-0.4)
     assert bench.interacting_pairs(x, d, n, (0, 1, 1), h_c) == 1 + 3
+
+
+def test_stable_subcycles_by_hand():
+    """n_int keeps the explicit drag relaxation beta/m dt/n_int at or below
+    1/2: worked out for one box, and growing with the solid fraction and as
+    the spheres get smaller."""
+    import math
+    L, d, tau, rho_p = 32, 1.0, 0.55, 2.5
+    V = math.pi / 6 * d ** 3
+
+    def box(eps, dd=d):
+        n = int(round(eps * L ** 3 / (math.pi / 6 * dd ** 3)))
+        return dict(n=(L, L, L), d=np.full(n, dd), x=np.zeros((n, 3)), tau=tau, rho_p=np.full(n, rho_p))
+
+    # by hand at <eps_p> = 0.3: the solid fraction a sphere sees is V/8 + 1.3 * 0.3
+    wl = box(0.3)
+    e = V / 8 + 1.3 * len(wl["x"]) * V / L ** 3
+    A = 5.81 * e / (1 - e) ** 3 + 0.48 * e ** (1 / 3) / (1 - e) ** 4
+    rate = 3 * math.pi * d * (tau - 0.5) / 3 * (1 - e) * (1 / (1 - e) ** 3 + A) / (rho_p * V)
+    assert bench._stable_subcycles(wl) == max(2, math.ceil(rate / 0.5))
+    ns = [bench._stable_subcycles(box(eps)) for eps in (0.01, 0.1, 0.2, 0.3, 0.4, 0.45)]
+    assert ns == sorted(ns) and ns[0] == 2 and ns[-1] > ns[0]
+    # the same solid fraction in smaller spheres relaxes faster (rate ~ 1/d^2)
+    assert bench._stable_subcycles(box(0.3, 0.6)) > bench._stable_subcycles(wl)
